@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput benchmark: cloth node-steps/s on one GB300.
+
+Default workload (`plain_batch`): 64 square cloths with sides U{64..512}
+(5.97M nodes, seed 1002), k x U(0.8, 1.2), 1-4 pinned boundary nodes,
+pressure ~ N(0, 0.5) N/m^2 per cloth, FP32, every step one batched launch,
+replayed from captured CUDA graphs.  One bench step = one plain step of the
+whole batch.  The 306 MB double-buffered state is larger than the 129 MB L2,
+so no flush is needed between steps.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead
+(bounded sample, host cores); under torchrun only rank 0 runs it.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE_STEP = 48       # read u, v (24 B) + write u, v (24 B), FP32
+CLOCK_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+# ------------------------------------------------------------------ helpers
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40000)
+    p.add_argument("--warmup", type=int, default=400)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--graph-chunk", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def kernel_hash(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(name: str, src_files, units: float):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `units`
+    nodes; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"{name}.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("source_hash") != kernel_hash(src_files):
+            return None
+        return float(d["dram_bytes_per_node"]) * units
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms for one GPU."""
+
+    def __init__(self, device_index: int):
+        import torch
+        self.samples = []
+        self.proc = None
+        try:
+            pr = torch.cuda.get_device_properties(device_index)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+        except Exception:
+            bus = str(device_index)
+        self.bus = bus
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.bus], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0: float, t1: float) -> dict:
+        time.sleep(0.25)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+        sel = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25] or [p for (_, p) in self.samples]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in sel if num(p[1]) is not None]
+        smax = [num(p[2]) for p in sel if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in sel for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(sel)}
+
+
+def dist_setup(gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Largest value over all ranks (the slowest rank sets the job time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_cloth_steps(args):
+    spec, pins, x, v, steps = args
+    import oracle
+    t = time.perf_counter()
+    oracle.step(spec, x, v, pins=pins, steps=steps)
+    return time.perf_counter() - t
+
+
+def oracle_plain_rate(cfg, steps: int, cores: int):
+    """Node-steps/s of the FP64 oracle over all cloths of `cfg` for `steps`
+    steps, cloths spread over a spawn pool of `cores` processes."""
+    import oracle
+    oracle.build()
+    jobs = [(s, p, x, v, steps) for s, p, x, v in zip(cfg["specs"], cfg["pins"], cfg["x"], cfg["v"])]
+    jobs.sort(key=lambda j: -j[0]["rows"] * j[0]["cols"])
+    nodes = sum(s["rows"] * s["cols"] for s in cfg["specs"])
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_cloth_steps, jobs[:cores], chunksize=1)     # warm the workers
+        t = time.perf_counter()
+        pool.map(_oracle_cloth_steps, jobs, chunksize=1)
+        wall = time.perf_counter() - t
+    return nodes * steps / wall, wall
+
+
+# ------------------------------------------------------------------ runs
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2403_12820_gb300 import workloads as wl
+    cfg = wl.plain_batch()
+    cores = os.cpu_count() or 1
+    nodes = sum(s["rows"] * s["cols"] for s in cfg["specs"])
+    sample_steps = 1
+    # warm-up, then each timed bench step is one plain step of the whole batch
+    steps = max(1, min(args.steps, 10))
+    warm = max(0, min(args.warmup, 1))
+    if warm:
+        oracle_plain_rate(cfg, 1, cores)
+    rate, wall = oracle_plain_rate(cfg, steps * sample_steps, cores)
+    ms = wall / steps * 1e3
+    return {
+        "impl": "reference", "metric": "cloth node-steps/s (plain mass-spring step, batched cloths)",
+        "value": rate, "unit": "node-steps/s", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "plain_batch: 64 cloths, sides U{64..512} (5.97M nodes), FP64 oracle on host cores",
+                   "global_batch": 64, "nodes": nodes},
+        "cpu_baseline": {"value": rate, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"all 64 cloths x {steps} steps (bench steps capped at 10)"},
+        "e2e": {"value": rate, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_plain(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+
+    cfg = wl.plain_batch()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    x0 = pack(cfg["x"]).to(dev)
+    v0 = pack(cfg["v"]).to(dev)
+    cb.set_state(x0, v0)
+    nodes = cb.total_nodes
+    chunk = args.graph_chunk
+    stream = torch.cuda.current_stream()
+
+    cb.rollout(args.warmup, graph_chunk=chunk)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    w0 = time.time()
+    e0.record(stream)
+    cb.rollout(args.steps, graph_chunk=chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier(world)
+    clocks = sampler.stop(w0, w1)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    status = cb.status()
+    value = world * nodes * args.steps / (ms_max / 1e3)
+
+    hbm, _, peak_kind = peaks()
+    launch_s = ms / 1e3 / args.steps          # one plain-step kernel per step
+    achieved = BYTES_PER_NODE_STEP * nodes / launch_s / 1e9
+    traffic = ncu_traffic("plain_step_traffic", ["paper_2403_12820_gb300/csrc/plain_step.cu"], nodes)
+
+    out = {
+        "metric": "cloth node-steps/s (plain mass-spring step, batched cloths)",
+        "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plain_batch: 64 cloths, sides U{64..512} (seed 1002), 5.97M nodes, FP32, "
+                               f"CUDA graphs of {chunk} steps",
+                   "global_batch": 64 * world, "nodes_per_gpu": nodes,
+                   "l2": "inputs larger than L2 (306 MB double-buffered state vs 129 MB L2)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_kind": f"{peak_kind} (copy bandwidth)", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * nodes},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "status_word": status,
+    }
+
+    if not args.no_e2e:
+        # end to end through the public API: pinned host state -> device,
+        # a 100-step rollout, positions back to pinned host memory
+        per_call = 100
+        hx = torch.empty_like(x0, device="cpu").pin_memory()
+        hv = torch.empty_like(v0, device="cpu").pin_memory()
+        hx.copy_(x0); hv.copy_(v0)
+        hout = torch.empty_like(hx).pin_memory()
+        dx = torch.empty_like(x0); dv = torch.empty_like(v0)
+        calls = max(1, min(20, args.steps // per_call))
+        for _ in range(2):
+            dx.copy_(hx, non_blocking=True); dv.copy_(hv, non_blocking=True)
+            cb.set_state(dx, dv); cb.rollout(per_call, graph_chunk=per_call)
+            xo, _ = cb.get_state(); hout.copy_(xo, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            dx.copy_(hx, non_blocking=True); dv.copy_(hv, non_blocking=True)
+            cb.set_state(dx, dv)
+            cb.rollout(per_call, graph_chunk=per_call)
+            xo, _ = cb.get_state()
+            hout.copy_(xo, non_blocking=True)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        out["e2e"] = {"value": world * nodes * per_call * calls / el, "unit": "node-steps/s",
+                      "h2d_bytes_per_step": (hx.numel() + hv.numel()) * 4 / per_call,
+                      "d2h_bytes_per_step": hout.numel() * 4 / per_call,
+                      "steps_per_call": per_call, "calls": calls}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, wall = oracle_plain_rate(cfg, 2, cores)
+        out["cpu_baseline"] = {"value": rate, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                               "sample": f"all 64 cloths x 2 steps, FP64 oracle, {cores} processes ({wall:.1f} s)"}
+    cb.close()
+    return out
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        out = run_reference(args, rank, int(os.environ.get("WORLD_SIZE", "1")))
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return 0
+    rank, world, local = dist_setup(args.gpus)
+    out = run_plain(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

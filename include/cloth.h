@@ -1,0 +1,180 @@
+/*
+ * libcloth — GB300 (sm_103a) C ABI for the regular-grid mass-spring cloth
+ * and the physics-embedded CNN step of "A Physics-embedded Deep Learning
+ * Framework for Cloth Simulation" (Zhao, arXiv 2403.12820).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status: CLOTH_OK (0) or a negative
+ *    CLOTH_E* code; cloth_strerror() gives its text.  A CUDA failure returns
+ *    CLOTH_ECUDA and cloth_last_cuda_error() gives the cudaError_t value
+ *    (per calling thread).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that take a stream only enqueue work on it and return
+ *    without synchronising, unless they say otherwise.
+ *  - Pointers named d_* are device pointers, h_* host pointers.
+ *  - Ownership: the caller allocates every device buffer, including the
+ *    context workspace sized by cloth_workspace_size(); the library never
+ *    allocates device memory.  A context owns only its host-side struct, a
+ *    private capture stream and the CUDA graphs it caches; cloth_destroy()
+ *    releases those.  The caller keeps the workspace alive until then.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Errors found on the device (non-finite state, bad index in a debug
+ *    build) are OR-ed into a status word inside the workspace; read it with
+ *    cloth_status().
+ *
+ * State layout at the ABI: the cloths of a batch are packed one after the
+ * other; cloth b holds rows_b * cols_b nodes in row-major order, node
+ * (r, c) at index r * cols_b + c, and each node three consecutive floats
+ * (x, y, z).  Node (r, c) of cloth b rests at X = (c h_b, r h_b, 0).
+ */
+#ifndef CLOTH_H
+#define CLOTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CLOTH_OK = 0,
+    CLOTH_EINVAL = -1,       /* bad argument (NULL, size out of range, ...)   */
+    CLOTH_ENOMEM = -2,       /* caller's workspace smaller than required      */
+    CLOTH_ECUDA = -3,        /* a CUDA runtime call failed                    */
+    CLOTH_ENONFINITE = -4,   /* non-finite value found in the state           */
+    CLOTH_ETIMEOUT = -5,     /* a bounded device wait ran out                 */
+    CLOTH_EUNSUPPORTED = -6  /* valid request this build does not implement  */
+};
+
+/* Bits of the device status word (cloth_status). */
+enum {
+    CLOTH_STATUS_NONFINITE = 1,   /* a step produced a non-finite x or v */
+    CLOTH_STATUS_TIMEOUT = 2,     /* a bounded device wait ran out       */
+    CLOTH_STATUS_BOUNDS = 4       /* an index check failed (debug build) */
+};
+
+/* Lattice of one cloth: rows x cols nodes, spacing h (m), node mass m (kg).
+ * Sec. 3.1 (mass points joined by springs) and Sec. 4.1 (100 x 100 points). */
+typedef struct {
+    int32_t rows, cols;
+    float spacing, mass;
+} cloth_grid;
+
+/* Material and loads of one cloth.
+ *  k_struct, k_shear, k_bend: stiffness (N/m) of the springs to the 4
+ *    cardinal neighbours, the 4 diagonal neighbours and the 4 nodes two
+ *    apart in the cardinal directions — the 13-point stencil of Sec. 3.1,
+ *    elastic force Eq. 1 with rest lengths h, sqrt(2) h, 2 h.
+ *  mu_spring: spring-axis damping coefficient of Eq. 2.
+ *  drag: air drag d of Eq. 4 (force -d v).
+ *  pressure: p of Eq. 3, applied as (p/4) sum over the ordered cardinal
+ *    pairs (E,N),(N,W),(W,S),(S,E) of x_ij1 x x_ij2 (a flat interior node
+ *    receives p h^2 along +z).
+ *  gravity: acceleration g of Eq. 4 (force m g). */
+typedef struct {
+    float k_struct, k_shear, k_bend, mu_spring, drag, pressure;
+    float gravity[3];
+} cloth_params;
+
+/* Dirichlet nodes of one cloth (Sec. 3.1; the constraint operator C of
+ * Eq. 5 holds their velocity at zero).  `node` is a HOST array of `count`
+ * node indices r * cols + c, read during cloth_create only. */
+typedef struct {
+    int32_t count;
+    const int32_t* node;
+} cloth_pins;
+
+/* Sphere obstacle (cloth-object intersection elimination, Sec. 3.1): after
+ * each step a node inside the sphere is moved to the nearest point of its
+ * surface and its velocity is set to zero. */
+typedef struct {
+    float center[3];
+    float radius;
+    int32_t enabled;
+} cloth_sphere;
+
+typedef struct cloth_ctx cloth_ctx;
+
+/* Bytes of device workspace a context for these B cloths needs (state
+ * double buffer, descriptors, pin masks, work list, status word).
+ * Returns CLOTH_EINVAL if B < 1 or a grid has rows or cols < 1. */
+int cloth_workspace_size(int32_t B, const cloth_grid* grids, size_t* bytes);
+
+/* Create a context for B cloths on the current CUDA device.
+ *  grids, params: host arrays of B entries.  pins: host array of B entries
+ *  or NULL (no pins).  spheres: host array of B entries or NULL.
+ *  dt: time step of Eq. 5 (s).  d_workspace: device buffer of at least
+ *  cloth_workspace_size() bytes, 256-byte aligned.
+ * The workspace is initialised on `stream` (state zeroed: every cloth at
+ * rest, zero velocity).  Returns CLOTH_EINVAL for a bad pin index or a
+ * non-positive dt, spacing or mass; CLOTH_ENOMEM if `bytes` is too small. */
+int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const cloth_params* params,
+                 const cloth_pins* pins, const cloth_sphere* spheres, float dt,
+                 void* d_workspace, size_t bytes, void* stream);
+
+/* Load positions and velocities (packed ABI layout, device pointers, 3
+ * floats per node, total_nodes = sum rows_b * cols_b).  d_v may be NULL
+ * (zero velocity). */
+int cloth_set_state(cloth_ctx* ctx, const float* d_x, const float* d_v, void* stream);
+
+/* Store the current positions and velocities in the packed ABI layout.
+ * Either pointer may be NULL to skip it. */
+int cloth_get_state(cloth_ctx* ctx, float* d_x, float* d_v, void* stream);
+
+/* Total force on every node at the current state — Eq. 1 + 2 (springs),
+ * Eq. 3 (pressure) and Eq. 4 (gravity, drag) — packed like x. */
+int cloth_forces(cloth_ctx* ctx, float* d_f, void* stream);
+
+/* Advance every cloth `steps` plain steps (steps >= 0): the forces above,
+ * then the semi-implicit Euler update of Eq. 5, v <- C(v + dt f / m),
+ * x <- x + dt v, with pinned velocities held at zero, then sphere contact.
+ * One batched launch per step. */
+int cloth_step_plain(cloth_ctx* ctx, int32_t steps, void* stream);
+
+/* Rollout options.
+ *  steps: number of steps to run.
+ *  graph_chunk: steps per captured CUDA graph (rounded up to even; 0 =
+ *    no graph, one launch per step).  The graph is captured on the
+ *    context's private stream the first time a chunk size is used, cached
+ *    in the context and replayed on `stream`.
+ *  d_record / record_every: if d_record is not NULL, the positions after
+ *    every `record_every`-th step are written to d_record in the packed ABI
+ *    layout, one frame of 3 * total_nodes floats after another
+ *    (steps / record_every frames).  Recording disables graphs. */
+typedef struct {
+    int32_t steps;
+    int32_t graph_chunk;
+    float* d_record;
+    int32_t record_every;
+} cloth_rollout_opts;
+
+/* Plain-step rollout under the options above. */
+int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
+
+/* Topology as the step kernels see it: for every node of cloth b, bit s of
+ * d_mask[node] is set iff spring s exists (both ends in the grid), with s in
+ * the order E, N, W, S, NE, NW, SW, SE, 2E, 2N, 2W, 2S (offsets (dr, dc):
+ * (0,1) (1,0) (0,-1) (-1,0) (1,1) (1,-1) (-1,-1) (-1,1) (0,2) (2,0) (0,-2)
+ * (-2,0)).  Sec. 3.1, 13-point stencil. */
+int cloth_topology(cloth_ctx* ctx, int32_t b, uint16_t* d_mask, void* stream);
+
+/* Synchronise `stream`, then read and return (in *h_status) the device
+ * status word; with clear != 0 it is reset to 0 afterwards. */
+int cloth_status(cloth_ctx* ctx, int32_t* h_status, int32_t clear, void* stream);
+
+/* Number of cloths and total nodes of the context. */
+int cloth_info(const cloth_ctx* ctx, int32_t* B, int64_t* total_nodes);
+
+/* Release the context's host resources (graphs, capture stream). */
+void cloth_destroy(cloth_ctx* ctx);
+
+const char* cloth_strerror(int code);
+int cloth_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLOTH_H */

@@ -1,0 +1,157 @@
+"""Torch-facing wrapper of the cloth context (argument marshalling only).
+
+Torch supplies device memory and the stream; every step runs in libcloth's
+CUDA kernels.  A cloth is described by a dict with keys rows, cols, h, m,
+k_struct, k_shear, k_bend, mu, drag, p, g (3 floats), and optionally
+sphere = {center: (3 floats), radius}; the time step dt is shared by the
+batch.  States are float32 CUDA tensors of shape (total_nodes, 3), cloths
+packed back to back, node (r, c) of a cloth at row r * cols + c.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import ClothGrid, ClothParams, ClothPins, ClothSphere, RolloutOpts
+
+
+def _stream_handle(stream: torch.cuda.Stream | None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=torch.float32) -> torch.Tensor:
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    return t
+
+
+class ClothBatch:
+    """A batch of cloths of uneven sizes stepped by one launch per step."""
+
+    def __init__(self, specs: list[dict], pins: list[list[int]] | None = None, dt: float | None = None,
+                 device: str | torch.device = "cuda", stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("ClothBatch needs a CUDA device (libcloth has no CPU path)")
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.specs = list(specs)
+        B = len(specs)
+        self.B = B
+        dt = float(dt if dt is not None else specs[0]["dt"])
+        self.dt = dt
+        grids = (ClothGrid * B)()
+        params = (ClothParams * B)()
+        spheres = (ClothSphere * B)()
+        pin_arrs = []
+        pin_structs = (ClothPins * B)()
+        for b, s in enumerate(specs):
+            grids[b] = ClothGrid(int(s["rows"]), int(s["cols"]), float(s["h"]), float(s["m"]))
+            g = s.get("g", (0.0, 0.0, -9.81))
+            params[b] = ClothParams(float(s["k_struct"]), float(s["k_shear"]), float(s["k_bend"]),
+                                    float(s.get("mu", 0.0)), float(s.get("drag", 0.0)), float(s.get("p", 0.0)),
+                                    (ctypes.c_float * 3)(*[float(a) for a in g]))
+            sph = s.get("sphere")
+            if sph is not None:
+                spheres[b] = ClothSphere((ctypes.c_float * 3)(*[float(a) for a in sph["center"]]),
+                                         float(sph["radius"]), 1)
+            pl = list(pins[b]) if pins is not None else []
+            arr = (ctypes.c_int32 * max(1, len(pl)))(*pl)
+            pin_arrs.append(arr)
+            pin_structs[b] = ClothPins(len(pl), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)))
+        nbytes = ctypes.c_size_t()
+        _lib.check("cloth_workspace_size", self.lib.cloth_workspace_size(B, grids, ctypes.byref(nbytes)))
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            self.stream = stream
+            _lib.check("cloth_create", self.lib.cloth_create(
+                ctypes.byref(h), B, grids, params, pin_structs, spheres, ctypes.c_float(dt),
+                _ptr(self.workspace), nbytes, _stream_handle(stream)))
+        self.handle = h
+        nB, nn = ctypes.c_int32(), ctypes.c_int64()
+        _lib.check("cloth_info", self.lib.cloth_info(h, ctypes.byref(nB), ctypes.byref(nn)))
+        self.total_nodes = nn.value
+        offs = [0]
+        for s in specs:
+            offs.append(offs[-1] + int(s["rows"]) * int(s["cols"]))
+        self.node_offsets = offs
+
+    # ----------------------------------------------------------- state
+    def _s(self):
+        return _stream_handle(self.stream)
+
+    def set_state(self, x: torch.Tensor, v: torch.Tensor | None = None) -> None:
+        _require_cuda(x, "x")
+        if v is not None:
+            _require_cuda(v, "v")
+        if x.numel() != 3 * self.total_nodes or (v is not None and v.numel() != 3 * self.total_nodes):
+            raise ValueError("state tensors must hold 3 * total_nodes floats")
+        _lib.call("cloth_set_state", self.handle, _ptr(x), _ptr(v), self._s())
+
+    def get_state(self, x: torch.Tensor | None = None, v: torch.Tensor | None = None):
+        if x is None:
+            x = torch.empty(self.total_nodes, 3, dtype=torch.float32, device=self.device)
+        if v is None:
+            v = torch.empty(self.total_nodes, 3, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_get_state", self.handle, _ptr(x), _ptr(v), self._s())
+        return x, v
+
+    def forces(self) -> torch.Tensor:
+        f = torch.empty(self.total_nodes, 3, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_forces", self.handle, _ptr(f), self._s())
+        return f
+
+    def step(self, steps: int = 1) -> None:
+        _lib.call("cloth_step_plain", self.handle, int(steps), self._s())
+
+    def rollout(self, steps: int, graph_chunk: int = 0, record: torch.Tensor | None = None,
+                record_every: int = 1) -> None:
+        if record is not None:
+            _require_cuda(record, "record")
+            if record.numel() < (steps // record_every) * 3 * self.total_nodes:
+                raise ValueError("record buffer too small")
+        o = RolloutOpts(int(steps), int(graph_chunk), _ptr(record), int(record_every))
+        _lib.call("cloth_rollout_plain", self.handle, ctypes.byref(o), self._s())
+
+    def topology(self, b: int) -> torch.Tensor:
+        s = self.specs[b]
+        m = torch.empty(int(s["rows"]) * int(s["cols"]), dtype=torch.int16, device=self.device)
+        _lib.call("cloth_topology", self.handle, int(b), _ptr(m), self._s())
+        return m
+
+    def status(self, clear: bool = False) -> int:
+        st = ctypes.c_int32()
+        _lib.call("cloth_status", self.handle, ctypes.byref(st), int(clear), self._s())
+        return st.value
+
+    def split(self, t: torch.Tensor) -> list[torch.Tensor]:
+        """Per-cloth views (rows, cols, 3) of a packed (total_nodes, 3) tensor."""
+        out = []
+        for b, s in enumerate(self.specs):
+            a, e = self.node_offsets[b], self.node_offsets[b + 1]
+            out.append(t[a:e].view(int(s["rows"]), int(s["cols"]), 3))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            self.lib.cloth_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack(arrs) -> torch.Tensor:
+    """Concatenate per-cloth (rows, cols, 3) float32 arrays into (total_nodes, 3)."""
+    import numpy as np
+    return torch.from_numpy(np.concatenate([np.asarray(a, dtype=np.float32).reshape(-1, 3) for a in arrs]))

@@ -1,0 +1,406 @@
+// Host implementation of the cloth context entry points of include/cloth.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/cloth.h"
+#include "cloth_internal.cuh"
+
+using namespace cloth;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+constexpr int kMinSegRows = 4;       // smallest row segment the work list may use
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int64_t pitch_of(int cols) { return (int64_t)((cols + kPitchAlign - 1) / kPitchAlign) * kPitchAlign; }
+
+int64_t units_for(const cloth_grid* g, int B, int seg_rows)
+{
+    int64_t n = 0;
+    for (int b = 0; b < B; ++b)
+        n += (int64_t)((g[b].cols + kStrip - 1) / kStrip) * ((g[b].rows + seg_rows - 1) / seg_rows);
+    return n;
+}
+
+struct Layout {
+    size_t desc, units, pins, state[2], status, total;
+    int64_t state_floats, pin_words, max_units;
+};
+
+Layout make_layout(int B, const cloth_grid* g)
+{
+    Layout L{};
+    int64_t floats = 0, words = 0;
+    for (int b = 0; b < B; ++b) {
+        const int64_t pitch = pitch_of(g[b].cols);
+        floats += align_up((size_t)(6 * g[b].rows * pitch), kAlign / sizeof(float));
+        words += (int64_t)g[b].rows * ((pitch + 31) / 32);
+    }
+    L.state_floats = floats;
+    L.pin_words = words;
+    L.max_units = units_for(g, B, kMinSegRows);
+    size_t off = 0;
+    L.desc = off;     off = align_up(off + sizeof(ClothDesc) * B, kAlign);
+    L.units = off;    off = align_up(off + sizeof(WorkUnit) * L.max_units, kAlign);
+    L.pins = off;     off = align_up(off + sizeof(uint32_t) * words, kAlign);
+    L.state[0] = off; off = align_up(off + sizeof(float) * floats, kAlign);
+    L.state[1] = off; off = align_up(off + sizeof(float) * floats, kAlign);
+    L.status = off;   off = align_up(off + 64, kAlign);
+    L.total = off;
+    return L;
+}
+
+bool grids_ok(int32_t B, const cloth_grid* g)
+{
+    if (B < 1 || B > 65535 || !g) return false;
+    for (int b = 0; b < B; ++b)
+        if (g[b].rows < 1 || g[b].cols < 1 || g[b].rows > (1 << 20) || g[b].cols > (1 << 20)) return false;
+    return true;
+}
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return CLOTH_ECUDA;
+}
+
+#define CK(expr)                                 \
+    do {                                         \
+        cudaError_t e__ = (expr);                \
+        if (e__ != cudaSuccess) return cuda_fail(e__); \
+    } while (0)
+
+}  // namespace
+
+struct cloth_ctx {
+    int32_t B = 0;
+    int64_t total_nodes = 0, max_nodes = 0;
+    bool damp = false;
+    char* ws = nullptr;
+    Layout L{};
+    std::vector<ClothDesc> desc;
+    std::vector<cloth_grid> grids;
+    int cur = 0;                       // state buffer holding the current state
+    int seg_rows = 16;
+    int n_units = 0;
+    int grid = 0, block = 128;
+    int sm_count = 0;
+    cudaStream_t cap = nullptr;        // private stream for graph capture
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
+
+    ClothDesc* d_desc() const { return reinterpret_cast<ClothDesc*>(ws + L.desc); }
+    WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
+    uint32_t* d_pins() const { return reinterpret_cast<uint32_t*>(ws + L.pins); }
+    float* d_state(int k) const { return reinterpret_cast<float*>(ws + L.state[k]); }
+    int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
+};
+
+namespace {
+
+// Build and upload the work list for `seg_rows`-row segments; pick the grid
+// as a multiple of the SM count (persistent warps loop over the list).
+int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
+{
+    seg_rows = std::max(seg_rows, kMinSegRows);
+    std::vector<WorkUnit> u;
+    for (int b = 0; b < c->B; ++b) {
+        const int rows = c->grids[b].rows, cols = c->grids[b].cols;
+        for (int r0 = 0; r0 < rows; r0 += seg_rows)
+            for (int c0 = 0; c0 < cols; c0 += kStrip) u.push_back(WorkUnit{b, c0, r0, std::min(rows, r0 + seg_rows)});
+    }
+    // longest units first so the tail of the persistent loop is short
+    std::stable_sort(u.begin(), u.end(), [](const WorkUnit& a, const WorkUnit& b) { return (a.r1 - a.r0) > (b.r1 - b.r0); });
+    if ((int64_t)u.size() > c->L.max_units) return CLOTH_EINVAL;
+    CK(cudaMemcpyAsync(c->d_units(), u.data(), sizeof(WorkUnit) * u.size(), cudaMemcpyHostToDevice, s));
+    c->seg_rows = seg_rows;
+    c->n_units = (int)u.size();
+    const int warps_per_block = c->block / 32;
+    const int resident = c->sm_count * 12;      // warps that fit at once (~12 per SM)
+    const int want = std::min<int64_t>(c->n_units, resident);
+    c->grid = std::max(1, (want + warps_per_block - 1) / warps_per_block);
+    return CLOTH_OK;
+}
+
+int pick_seg_rows(const cloth_ctx* c)
+{
+    // enough units to cover every SM a few times over, but segments long
+    // enough that the 2 warm-up rows stay a small fraction
+    const int64_t target = (int64_t)c->sm_count * 12 * 2;
+    for (int R : {64, 32, 16, 8})
+        if (units_for(c->grids.data(), c->B, R) >= target) return R;
+    return 8;
+}
+
+int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s)
+{
+    StepArgs a;
+    a.desc = c->d_desc();
+    a.units = c->d_units();
+    a.n_units = c->n_units;
+    a.src = c->d_state(c->cur);
+    a.dst = c->d_state(c->cur ^ 1);
+    a.pinmask = c->d_pins();
+    a.force_out = force_out;
+    a.status = c->d_status();
+    CK(launch_plain_step(a, c->damp, forces_only, c->grid, c->block, s));
+    if (!forces_only) c->cur ^= 1;
+    return CLOTH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cloth_workspace_size(int32_t B, const cloth_grid* grids, size_t* bytes)
+{
+    if (!bytes || !grids_ok(B, grids)) return CLOTH_EINVAL;
+    *bytes = make_layout(B, grids).total;
+    return CLOTH_OK;
+}
+
+int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const cloth_params* params,
+                 const cloth_pins* pins, const cloth_sphere* spheres, float dt, void* d_workspace, size_t bytes,
+                 void* stream)
+{
+    if (!out || !params || !d_workspace || !grids_ok(B, grids) || !(dt > 0.f) || !std::isfinite(dt))
+        return CLOTH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign) return CLOTH_EINVAL;
+    for (int b = 0; b < B; ++b)
+        if (!(grids[b].spacing > 0.f) || !(grids[b].mass > 0.f)) return CLOTH_EINVAL;
+    const Layout L = make_layout(B, grids);
+    if (bytes < L.total) return CLOTH_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    cloth_ctx* c = new (std::nothrow) cloth_ctx;
+    if (!c) return CLOTH_ENOMEM;
+    c->B = B;
+    c->ws = static_cast<char*>(d_workspace);
+    c->L = L;
+    c->grids.assign(grids, grids + B);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e); }
+
+    std::vector<uint32_t> pinmask(L.pin_words, 0u);
+    int64_t floats = 0, words = 0, nodes = 0;
+    for (int b = 0; b < B; ++b) {
+        const cloth_grid& g = grids[b];
+        const cloth_params& p = params[b];
+        ClothDesc d{};
+        d.rows = g.rows;
+        d.cols = g.cols;
+        d.pitch = (int32_t)pitch_of(g.cols);
+        d.pin_wpr = (d.pitch + 31) / 32;
+        d.plane_off = floats;
+        d.plane_stride = (int64_t)g.rows * d.pitch;
+        d.pin_off = words;
+        d.abi_off = nodes;
+        d.h = g.spacing;
+        d.m = g.mass;
+        d.inv_m = 1.f / g.mass;
+        d.dt = dt;
+        d.k_struct = p.k_struct;
+        d.k_shear = p.k_shear;
+        d.k_bend = p.k_bend;
+        d.mu = p.mu_spring;
+        d.drag = p.drag;
+        d.p_quarter = 0.25f * p.pressure;
+        d.gx = p.gravity[0];
+        d.gy = p.gravity[1];
+        d.gz = p.gravity[2];
+        if (p.mu_spring != 0.f) c->damp = true;
+        if (spheres && spheres[b].enabled) {
+            d.sph_on = 1;
+            d.sph_cx = spheres[b].center[0];
+            d.sph_cy = spheres[b].center[1];
+            d.sph_cz = spheres[b].center[2];
+            d.sph_r = spheres[b].radius;
+            d.sph_r2 = spheres[b].radius * spheres[b].radius;
+        }
+        if (pins && pins[b].count > 0) {
+            if (!pins[b].node) { delete c; return CLOTH_EINVAL; }
+            for (int i = 0; i < pins[b].count; ++i) {
+                const int32_t n = pins[b].node[i];
+                if (n < 0 || (int64_t)n >= (int64_t)g.rows * g.cols) { delete c; return CLOTH_EINVAL; }
+                const int r = n / g.cols, col = n % g.cols;
+                pinmask[words + (int64_t)r * d.pin_wpr + col / 32] |= 1u << (col % 32);
+            }
+        }
+        c->desc.push_back(d);
+        floats += align_up((size_t)(6 * d.plane_stride), kAlign / sizeof(float));
+        words += (int64_t)g.rows * d.pin_wpr;
+        nodes += (int64_t)g.rows * g.cols;
+        c->max_nodes = std::max<int64_t>(c->max_nodes, (int64_t)g.rows * g.cols);
+    }
+    c->total_nodes = nodes;
+
+    int rc = CLOTH_OK;
+    e = cudaMemcpyAsync(c->d_desc(), c->desc.data(), sizeof(ClothDesc) * B, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && L.pin_words)
+        e = cudaMemcpyAsync(c->d_pins(), pinmask.data(), sizeof(uint32_t) * L.pin_words, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[0], 0, L.state[1] - L.state[0], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[1], 0, L.status - L.state[1], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.status, 0, 64, s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = cuda_fail(e);
+    if (rc == CLOTH_OK) rc = set_work(c, pick_seg_rows(c), s);
+    // the host copies above read pageable memory; wait so they are done
+    // before the host vectors go out of scope
+    if (rc == CLOTH_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e);
+    if (rc != CLOTH_OK) {
+        if (c->cap) cudaStreamDestroy(c->cap);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return CLOTH_OK;
+}
+
+int cloth_set_state(cloth_ctx* c, const float* d_x, const float* d_v, void* stream)
+{
+    if (!c || !d_x) return CLOTH_EINVAL;
+    CK(launch_set_state(c->d_desc(), c->B, c->max_nodes, nullptr, d_x, d_v, c->d_state(c->cur),
+                        static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
+int cloth_get_state(cloth_ctx* c, float* d_x, float* d_v, void* stream)
+{
+    if (!c) return CLOTH_EINVAL;
+    if (!d_x && !d_v) return CLOTH_OK;
+    CK(launch_get_state(c->d_desc(), c->B, c->max_nodes, nullptr, c->d_state(c->cur), d_x, d_v,
+                        static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
+int cloth_forces(cloth_ctx* c, float* d_f, void* stream)
+{
+    if (!c || !d_f) return CLOTH_EINVAL;
+    return launch_step(c, true, d_f, static_cast<cudaStream_t>(stream));
+}
+
+int cloth_step_plain(cloth_ctx* c, int32_t steps, void* stream)
+{
+    if (!c || steps < 0) return CLOTH_EINVAL;
+    for (int i = 0; i < steps; ++i) {
+        const int rc = launch_step(c, false, nullptr, static_cast<cudaStream_t>(stream));
+        if (rc) return rc;
+    }
+    return CLOTH_OK;
+}
+
+int cloth_rollout_plain(cloth_ctx* c, const cloth_rollout_opts* o, void* stream)
+{
+    if (!c || !o || o->steps < 0 || o->graph_chunk < 0) return CLOTH_EINVAL;
+    if (o->d_record && o->record_every < 1) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (o->d_record) {
+        int frame = 0;
+        for (int i = 1; i <= o->steps; ++i) {
+            int rc = launch_step(c, false, nullptr, s);
+            if (rc) return rc;
+            if (i % o->record_every == 0) {
+                rc = cloth_get_state(c, o->d_record + (int64_t)frame * 3 * c->total_nodes, nullptr, stream);
+                if (rc) return rc;
+                ++frame;
+            }
+        }
+        return CLOTH_OK;
+    }
+    int chunk = o->graph_chunk;
+    if (chunk & 1) ++chunk;
+    int done = 0;
+    if (chunk > 0 && o->steps >= chunk) {
+        const auto key = std::make_pair(chunk, c->cur);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            const int cur0 = c->cur;
+            int rc = CLOTH_OK;
+            for (int i = 0; i < chunk && rc == CLOTH_OK; ++i) rc = launch_step(c, false, nullptr, c->cap);
+            const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+            c->cur = cur0;   // capture only recorded the steps
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(e);
+            const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) return cuda_fail(e2);
+            it = c->graphs.emplace(key, ge).first;
+        }
+        while (o->steps - done >= chunk) {
+            CK(cudaGraphLaunch(it->second, s));
+            done += chunk;   // chunk is even: the current buffer is unchanged
+        }
+    }
+    for (; done < o->steps; ++done) {
+        const int rc = launch_step(c, false, nullptr, s);
+        if (rc) return rc;
+    }
+    return CLOTH_OK;
+}
+
+int cloth_topology(cloth_ctx* c, int32_t b, uint16_t* d_mask, void* stream)
+{
+    if (!c || !d_mask || b < 0 || b >= c->B) return CLOTH_EINVAL;
+    CK(launch_topology(c->d_desc(), b, c->grids[b].rows, c->grids[b].cols, d_mask, static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
+int cloth_status(cloth_ctx* c, int32_t* h_status, int32_t clear, void* stream)
+{
+    if (!c || !h_status) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(h_status, c->d_status(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (clear) {
+        CK(cudaMemsetAsync(c->d_status(), 0, sizeof(int32_t), s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return CLOTH_OK;
+}
+
+int cloth_info(const cloth_ctx* c, int32_t* B, int64_t* total_nodes)
+{
+    if (!c) return CLOTH_EINVAL;
+    if (B) *B = c->B;
+    if (total_nodes) *total_nodes = c->total_nodes;
+    return CLOTH_OK;
+}
+
+void cloth_destroy(cloth_ctx* c)
+{
+    if (!c) return;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+const char* cloth_strerror(int code)
+{
+    switch (code) {
+    case CLOTH_OK: return "ok";
+    case CLOTH_EINVAL: return "invalid argument";
+    case CLOTH_ENOMEM: return "workspace too small";
+    case CLOTH_ECUDA: return "CUDA runtime error";
+    case CLOTH_ENONFINITE: return "non-finite state";
+    case CLOTH_ETIMEOUT: return "device wait timed out";
+    case CLOTH_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+    }
+}
+
+int cloth_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

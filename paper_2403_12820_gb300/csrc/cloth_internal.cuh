@@ -1,0 +1,65 @@
+// Internal device-side structures of libcloth (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cloth {
+
+// The plain-step kernel maps one warp to a strip of STRIP output columns:
+// lane l holds the 4 consecutive columns c0 - 4 + 4 l .. c0 - 1 + 4 l, so
+// lanes 1..30 own the output columns c0 .. c0 + 119 and lanes 0 and 31 are
+// halo lanes that supply the springs reaching across the strip border.
+constexpr int kLaneCols = 4;
+constexpr int kStrip = 120;
+// Plane pitch (floats per row) is a multiple of this, so every float4 of a
+// lane is 16-byte aligned and lies wholly inside or outside [0, pitch).
+constexpr int kPitchAlign = 4;
+
+// Per-cloth descriptor in device memory (built on the host at create).
+struct __align__(16) ClothDesc {
+    int32_t rows, cols, pitch, pin_wpr;   // pin_wpr: 32-bit pin words per row
+    int64_t plane_off;                    // float offset of plane 0 in a state buffer
+    int64_t plane_stride;                 // rows * pitch (floats)
+    int64_t pin_off;                      // word offset of the pin bitmask
+    int64_t abi_off;                      // node offset in the packed ABI layout
+    float h, m, inv_m, dt;
+    float k_struct, k_shear, k_bend, mu;
+    float drag, p_quarter, gx, gy;
+    float gz, sph_cx, sph_cy, sph_cz;
+    float sph_r, sph_r2;
+    int32_t sph_on, pad0;
+};
+
+// One warp's work: cloth `b`, strip starting at output column c0, output
+// rows [r0, r1).
+struct __align__(16) WorkUnit {
+    int32_t b, c0, r0, r1;
+};
+
+// State buffer layout: for each cloth, 6 planes (u_x, u_y, u_z, v_x, v_y,
+// v_z) of rows x pitch floats at plane_off + k * plane_stride, where
+// u = x - X is the displacement from the rest lattice.
+
+struct StepArgs {
+    const ClothDesc* desc;
+    const WorkUnit* units;
+    int32_t n_units;
+    const float* src;
+    float* dst;
+    const uint32_t* pinmask;
+    float* force_out;     // forces-only mode: packed ABI layout
+    int32_t* status;
+};
+
+// Launchers (plain_step.cu, state.cu).
+cudaError_t launch_plain_step(const StepArgs& a, bool damp, bool forces_only, int grid, int block,
+                              cudaStream_t s);
+cudaError_t launch_set_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,
+                             const float* x, const float* v, float* state, cudaStream_t s);
+cudaError_t launch_get_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,
+                             const float* state, float* x, float* v, cudaStream_t s);
+cudaError_t launch_topology(const ClothDesc* desc, int32_t b, int32_t rows, int32_t cols, uint16_t* mask,
+                            cudaStream_t s);
+
+}  // namespace cloth

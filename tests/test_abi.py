@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (no GPU needed: only host-side calls are made)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2403_12820_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|size_t|int32_t|int64_t)\s*\*?\s*(\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cloth_create", "cloth_step_plain", "cloth_rollout_plain", "cloth_forces",
+                     "cloth_set_state", "cloth_get_state", "cloth_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_workspace_size_host_only():
+    lib = _lib.load()
+    g = (_lib.ClothGrid * 2)(_lib.ClothGrid(32, 32, 0.02, 1e-3), _lib.ClothGrid(5, 7, 0.02, 1e-3))
+    n = ctypes.c_size_t()
+    assert lib.cloth_workspace_size(2, g, ctypes.byref(n)) == 0
+    # two double-buffered copies of 6 float planes per node at least
+    assert n.value >= 2 * 6 * 4 * (32 * 32 + 5 * 7)
+    bad = (_lib.ClothGrid * 1)(_lib.ClothGrid(0, 7, 0.02, 1e-3))
+    assert lib.cloth_workspace_size(1, bad, ctypes.byref(n)) == -1
+    assert lib.cloth_workspace_size(0, g, ctypes.byref(n)) == -1
+
+
+def test_strerror_and_codes():
+    lib = _lib.load()
+    assert lib.cloth_strerror(0) == b"ok"
+    assert b"workspace" in lib.cloth_strerror(-2)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    lib = _lib.load()
+    g = (_lib.ClothGrid * 1)(_lib.ClothGrid(4, 4, 0.02, 1e-3))
+    p = (_lib.ClothParams * 1)()
+    h = ctypes.c_void_p()
+    # NULL workspace, non-positive dt, too-small workspace are refused on the host
+    assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(1e-4), None, 0, None) == -1
+    assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(0.0), ctypes.c_void_p(256), 1 << 20, None) == -1
+    assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(1e-4), ctypes.c_void_p(256), 16, None) == -2
