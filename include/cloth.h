@@ -153,6 +153,15 @@ typedef struct {
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
 
+/* Launch shape of the plain step: the work list is cut into row segments of
+ * `seg_rows` rows (>= 4; 0 keeps the current value) and the persistent grid
+ * holds `warps_per_sm` warps per SM (0 keeps the current value).  Changes
+ * only speed, never results.  Cached graphs are dropped. */
+int cloth_set_launch(cloth_ctx* ctx, int32_t seg_rows, int32_t warps_per_sm, void* stream);
+
+/* Current launch shape (seg_rows, warps_per_sm, number of work units). */
+int cloth_get_launch(const cloth_ctx* ctx, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units);
+
 /* Topology as the step kernels see it: for every node of cloth b, bit s of
  * d_mask[node] is set iff spring s exists (both ends in the grid), with s in
  * the order E, N, W, S, NE, NW, SW, SE, 2E, 2N, 2W, 2S (offsets (dr, dc):
@@ -166,6 +175,88 @@ int cloth_status(cloth_ctx* ctx, int32_t* h_status, int32_t clear, void* stream)
 
 /* Number of cloths and total nodes of the context. */
 int cloth_info(const cloth_ctx* ctx, int32_t* B, int64_t* total_nodes);
+
+/* ------------------------------------------------------------------------
+ * The physics-embedded CNN cell (Sec. 3.2, Eq. 6-7, Fig. 1) and the network
+ * step of the framework (Fig. 2).
+ *
+ * The cell maps the displacement u = x - X and velocity v of every node to
+ * an acceleration a (3 channels):
+ *   zu = in_scale[0:3] u,  zv = in_scale[3:6] v
+ *   phi1 = W1 (*) [zu; 0],  xi1 = W1 (*) [0; zv]       (Eq. 6, one kernel
+ *   phi  = W2 (*) phi1,     xi  = W2 (*) xi1            for x and v)
+ *   L = WL (*) phi + bL;  s = tanh(P phi);  N = WN s;  D = WD (xi . s)  (Eq. 7)
+ *   a = out_scale (L + N + D)
+ * with (*) a 3x3 cross-correlation with zero "same" padding, W1 6->32,
+ * W2 32->32, WL 32->3, P 32->32 (1x1), WN, WD 32->3 (1x1).
+ *
+ * Weight blob (floats, this order): W1[32][6][3][3], W2[32][32][3][3],
+ * WL[3][32][3][3], bL[3], P[32][32], WN[3][32], WD[3][32], in_scale[6],
+ * out_scale[3] — CLOTH_NET_BLOB floats; gradients cover the first
+ * CLOTH_NET_PARAMS (the scales are fixed).
+ * ---------------------------------------------------------------------- */
+#define CLOTH_NET_PARAMS 13027
+#define CLOTH_NET_BLOB 13036
+
+enum {
+    CLOTH_NET_FP32 = 0,   /* FP32 CUDA-core arithmetic throughout            */
+    CLOTH_NET_BF16 = 1    /* BF16 tensor-core channel contractions, FP32 accumulate */
+};
+
+typedef struct cloth_net cloth_net;
+
+/* Device workspace of a network: weights in FP32 and packed tensor-core
+ * forms, plus the per-block partial sums of net_backward. */
+int net_workspace_size(size_t* bytes);
+
+/* Create a network on the current device from a HOST weight blob of
+ * CLOTH_NET_BLOB floats.  precision: CLOTH_NET_FP32 or CLOTH_NET_BF16.
+ * d_workspace: net_workspace_size() bytes, 256-byte aligned, owned by the
+ * caller.  Returns CLOTH_EINVAL for a bad precision or a non-finite weight. */
+int net_create(cloth_net** out, int32_t precision, const float* h_blob, void* d_workspace, size_t bytes,
+               void* stream);
+
+/* Replace the weights from a DEVICE blob of CLOTH_NET_BLOB floats (for
+ * instance after an optimizer step); enqueued on `stream`. */
+int net_set_weights(cloth_net* net, const float* d_blob, void* stream);
+
+/* Copy the current weights (CLOTH_NET_BLOB floats) to a device buffer. */
+int net_get_weights(const cloth_net* net, float* d_blob, void* stream);
+
+/* Bytes of the activation buffer net_forward saves for net_backward, for
+ * N images of H x W nodes (260 floats per node). */
+int net_saved_size(int32_t N, int32_t H, int32_t W, size_t* bytes);
+
+/* Forward of the cell on N images of H x W nodes, NCHW FP32:
+ * d_z [N][6][H][W] (channels u_x u_y u_z v_x v_y v_z, u = x - X) ->
+ * d_a [N][3][H][W].  If d_saved is not NULL (net_saved_size() bytes) the
+ * activations needed by net_backward are stored there.  An FP32 network
+ * runs on CUDA cores; a BF16 network runs its channel contractions on the
+ * tensor cores (d_saved must then be NULL).  Sec. 3.2, Eq. 6-7. */
+int net_forward(cloth_net* net, const float* d_z, float* d_a, int32_t N, int32_t H, int32_t W, float* d_saved,
+                void* stream);
+
+/* Backward of the cell (FP32 networks): given d_grad_a [N][3][H][W] =
+ * dLoss/da at the forward's input d_z and its d_saved activations, ADDS
+ * dLoss/dw to d_grad_w [CLOTH_NET_PARAMS] and, if d_grad_z is not NULL,
+ * writes dLoss/dz [N][6][H][W].  d_saved is used as scratch and is no
+ * longer valid afterwards.  Weight gradients are reduced in a fixed order
+ * (bitwise reproducible).  Returns CLOTH_EUNSUPPORTED for a BF16 network. */
+int net_backward(cloth_net* net, const float* d_z, float* d_saved, const float* d_grad_a, float* d_grad_z,
+                 float* d_grad_w, int32_t N, int32_t H, int32_t W, void* stream);
+
+/* Release the network's host resources. */
+void net_destroy(cloth_net* net);
+
+/* Device workspace cloth_step_net needs for this context and network
+ * precision (per-step activations of every cloth). */
+int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* bytes);
+
+/* Advance every cloth `steps` network steps (Fig. 2): a = cell(u, v), then
+ * v <- C(v + dt (a + f_p / m)), x <- x + dt v with the pressure f_p of Eq. 3
+ * and the pins hard-encoded outside the network, then sphere contact.
+ * d_work: cloth_net_workspace_size() bytes. */
+int cloth_step_net(cloth_ctx* ctx, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream);
 
 /* Release the context's host resources (graphs, capture stream). */
 void cloth_destroy(cloth_ctx* ctx);

@@ -16,6 +16,8 @@ c_int32, c_int64, c_float, c_size_t, c_void_p = ctypes.c_int32, ctypes.c_int64, 
 P = ctypes.POINTER
 
 CLOTH_OK = 0
+NET_FP32, NET_BF16 = 0, 1
+NET_PARAMS, NET_BLOB = 13027, 13036
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
 STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_BOUNDS = 1, 2, 4
 
@@ -52,7 +54,20 @@ SIGNATURES = {
     "cloth_step_plain": (c_int32, [c_void_p, c_int32, c_void_p]),
     "cloth_rollout_plain": (c_int32, [c_void_p, P(RolloutOpts), c_void_p]),
     "cloth_topology": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    "cloth_set_launch": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    "cloth_get_launch": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int32)]),
     "cloth_status": (c_int32, [c_void_p, P(c_int32), c_int32, c_void_p]),
+    "net_workspace_size": (c_int32, [P(c_size_t)]),
+    "net_create": (c_int32, [P(c_void_p), c_int32, P(c_float), c_void_p, c_size_t, c_void_p]),
+    "net_set_weights": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "net_get_weights": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "net_saved_size": (c_int32, [c_int32, c_int32, c_int32, P(c_size_t)]),
+    "net_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "net_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                               c_void_p]),
+    "net_destroy": (None, [c_void_p]),
+    "cloth_net_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
+    "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_info": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
     "cloth_destroy": (None, [c_void_p]),
     "cloth_strerror": (ctypes.c_char_p, [c_int32]),

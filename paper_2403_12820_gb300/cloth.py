@@ -120,6 +120,28 @@ class ClothBatch:
         o = RolloutOpts(int(steps), int(graph_chunk), _ptr(record), int(record_every))
         _lib.call("cloth_rollout_plain", self.handle, ctypes.byref(o), self._s())
 
+    def set_launch(self, seg_rows: int = 0, warps_per_sm: int = 0) -> None:
+        _lib.call("cloth_set_launch", self.handle, int(seg_rows), int(warps_per_sm), self._s())
+
+    def get_launch(self) -> tuple[int, int, int]:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.call("cloth_get_launch", self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return a.value, b.value, c.value
+
+    def net_workspace(self, precision: int) -> torch.Tensor:
+        n = ctypes.c_size_t()
+        _lib.call("cloth_net_workspace_size", self.handle, int(precision), ctypes.byref(n))
+        ws = getattr(self, "_net_ws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._net_ws = ws
+        return ws
+
+    def step_net(self, net, steps: int = 1) -> None:
+        """`steps` network steps (Fig. 2) with the given Net."""
+        ws = self.net_workspace(net.precision)
+        _lib.call("cloth_step_net", self.handle, net.handle, int(steps), _ptr(ws), ws.numel(), self._s())
+
     def topology(self, b: int) -> torch.Tensor:
         s = self.specs[b]
         m = torch.empty(int(s["rows"]) * int(s["cols"]), dtype=torch.int16, device=self.device)

@@ -9,6 +9,7 @@
 
 #include "../../include/cloth.h"
 #include "cloth_internal.cuh"
+#include "net_internal.cuh"
 
 using namespace cloth;
 
@@ -73,6 +74,13 @@ int cuda_fail(cudaError_t e)
     return CLOTH_ECUDA;
 }
 
+// Cloths of one size, stepped by the network as one batch of images.
+struct NetGroup {
+    int H, W;
+    std::vector<int32_t> cloths;
+    size_t list_off;   // int32 offset of its cloth list in the step workspace
+};
+
 #define CK(expr)                                 \
     do {                                         \
         cudaError_t e__ = (expr);                \
@@ -93,9 +101,13 @@ struct cloth_ctx {
     int seg_rows = 16;
     int n_units = 0;
     int grid = 0, block = 128;
+    int warps_per_sm = 16;
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
+    std::vector<NetGroup> groups;      // network step: cloths grouped by size
+    int64_t group_max_nodes = 0;       // largest group's node count
+    const void* lists_written = nullptr;   // step workspace holding current cloth lists
 
     ClothDesc* d_desc() const { return reinterpret_cast<ClothDesc*>(ws + L.desc); }
     WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
@@ -124,7 +136,7 @@ int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
     c->seg_rows = seg_rows;
     c->n_units = (int)u.size();
     const int warps_per_block = c->block / 32;
-    const int resident = c->sm_count * 12;      // warps that fit at once (~12 per SM)
+    const int resident = c->sm_count * c->warps_per_sm;   // warps resident at once
     const int want = std::min<int64_t>(c->n_units, resident);
     c->grid = std::max(1, (want + warps_per_block - 1) / warps_per_block);
     return CLOTH_OK;
@@ -134,7 +146,7 @@ int pick_seg_rows(const cloth_ctx* c)
 {
     // enough units to cover every SM a few times over, but segments long
     // enough that the 2 warm-up rows stay a small fraction
-    const int64_t target = (int64_t)c->sm_count * 12 * 2;
+    const int64_t target = (int64_t)c->sm_count * 12;
     for (int R : {64, 32, 16, 8})
         if (units_for(c->grids.data(), c->B, R) >= target) return R;
     return 8;
@@ -151,14 +163,105 @@ int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s
     a.pinmask = c->d_pins();
     a.force_out = force_out;
     a.status = c->d_status();
-    CK(launch_plain_step(a, c->damp, forces_only, c->grid, c->block, s));
+    if (c->damp) CK(launch_plain_step_damp(a, forces_only, c->grid, c->block, s));
+    else CK(launch_plain_step(a, forces_only, c->grid, c->block, s));
     if (!forces_only) c->cur ^= 1;
     return CLOTH_OK;
+}
+
+void make_groups(cloth_ctx* c)
+{
+    if (!c->groups.empty()) return;
+    std::map<std::pair<int, int>, int> idx;
+    size_t off = 0;
+    for (int b = 0; b < c->B; ++b) {
+        const auto key = std::make_pair(c->grids[b].rows, c->grids[b].cols);
+        auto it = idx.find(key);
+        if (it == idx.end()) {
+            it = idx.emplace(key, (int)c->groups.size()).first;
+            c->groups.push_back(NetGroup{key.first, key.second, {}, 0});
+        }
+        c->groups[it->second].cloths.push_back(b);
+    }
+    for (auto& g : c->groups) {
+        g.list_off = off;
+        off += g.cloths.size();
+        c->group_max_nodes = std::max<int64_t>(c->group_max_nodes, (int64_t)g.cloths.size() * g.H * g.W);
+    }
+}
+
+// FP32 network-step workspace: cloth lists, then T1, T2 (64 channels each)
+// and the acceleration (3 channels) of the largest group.
+struct StepWs {
+    size_t lists, t1, t2, a, total;
+};
+StepWs step_ws(const cloth_ctx* c)
+{
+    StepWs w{};
+    size_t off = 0;
+    w.lists = off; off = align_up(off + sizeof(int32_t) * c->B, kAlign);
+    w.t1 = off;    off = align_up(off + sizeof(float) * 64 * c->group_max_nodes, kAlign);
+    w.t2 = off;    off = align_up(off + sizeof(float) * 64 * c->group_max_nodes, kAlign);
+    w.a = off;     off = align_up(off + sizeof(float) * 3 * c->group_max_nodes, kAlign);
+    w.total = off;
+    return w;
 }
 
 }  // namespace
 
 extern "C" {
+
+int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
+{
+    if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
+    make_groups(const_cast<cloth_ctx*>(c));
+    *bytes = step_ws(c).total;
+    return CLOTH_OK;
+}
+
+int cloth_step_net(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !net || !d_work || steps < 0) return CLOTH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
+    make_groups(c);
+    const StepWs w = step_ws(c);
+    if (bytes < w.total) return CLOTH_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_work);
+    int32_t* lists = reinterpret_cast<int32_t*>(ws + w.lists);
+    if (c->lists_written != d_work) {
+        std::vector<int32_t> all;
+        for (const auto& g : c->groups) all.insert(all.end(), g.cloths.begin(), g.cloths.end());
+        CK(cudaMemcpyAsync(lists, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        c->lists_written = d_work;
+    }
+    float* t1 = reinterpret_cast<float*>(ws + w.t1);
+    float* t2 = reinterpret_cast<float*>(ws + w.t2);
+    float* a = reinterpret_cast<float*>(ws + w.a);
+    for (int st = 0; st < steps; ++st) {
+        for (const auto& g : c->groups) {
+            NetFwdArgs f{};
+            f.src.desc = c->d_desc();
+            f.src.cloth_of = lists + g.list_off;
+            f.src.state = c->d_state(c->cur);
+            f.w = net->d_w();
+            f.t1 = t1;
+            f.t2 = t2;
+            f.s = nullptr;
+            f.a = a;
+            f.N = (int)g.cloths.size();
+            f.H = g.H;
+            f.W = g.W;
+            CK(launch_net_forward_simt(f, s));
+            CK(launch_net_update(c->d_desc(), lists + g.list_off, f.N, g.H, g.W, a, c->d_state(c->cur),
+                                 c->d_state(c->cur ^ 1), c->d_pins(), c->d_status(), s));
+        }
+        c->cur ^= 1;
+    }
+    return CLOTH_OK;
+}
 
 int cloth_workspace_size(int32_t B, const cloth_grid* grids, size_t* bytes)
 {
@@ -351,6 +454,28 @@ int cloth_rollout_plain(cloth_ctx* c, const cloth_rollout_opts* o, void* stream)
     return CLOTH_OK;
 }
 
+int cloth_set_launch(cloth_ctx* c, int32_t seg_rows, int32_t warps_per_sm, void* stream)
+{
+    if (!c || seg_rows < 0 || (seg_rows > 0 && seg_rows < kMinSegRows) || warps_per_sm < 0 || warps_per_sm > 64)
+        return CLOTH_EINVAL;
+    if (warps_per_sm > 0) c->warps_per_sm = warps_per_sm;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    const int rc = set_work(c, seg_rows > 0 ? seg_rows : c->seg_rows, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
+int cloth_get_launch(const cloth_ctx* c, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units)
+{
+    if (!c) return CLOTH_EINVAL;
+    if (seg_rows) *seg_rows = c->seg_rows;
+    if (warps_per_sm) *warps_per_sm = c->warps_per_sm;
+    if (n_units) *n_units = c->n_units;
+    return CLOTH_OK;
+}
+
 int cloth_topology(cloth_ctx* c, int32_t b, uint16_t* d_mask, void* stream)
 {
     if (!c || !d_mask || b < 0 || b >= c->B) return CLOTH_EINVAL;
@@ -401,6 +526,10 @@ const char* cloth_strerror(int code)
     }
 }
 
-int cloth_last_cuda_error(void) { return g_last_cuda; }
+int cloth_last_cuda_error(void)
+{
+    const int n = cloth::net_last_cuda_error();
+    return g_last_cuda ? g_last_cuda : n;
+}
 
 }  // extern "C"

@@ -39,7 +39,12 @@ struct __align__(16) WorkUnit {
 
 // State buffer layout: for each cloth, 6 planes (u_x, u_y, u_z, v_x, v_y,
 // v_z) of rows x pitch floats at plane_off + k * plane_stride, where
-// u = x - X is the displacement from the rest lattice.
+// u = x - X is the displacement from the rest lattice.  Inside every
+// aligned group of 4 columns the floats are stored in the order
+// c0, c2, c1, c3, so that one float4 load hands a lane its column pairs
+// (c0, c2) and (c1, c3) as two float2 registers for paired FP32 arithmetic.
+__host__ __device__ constexpr int col_slot(int j) { return j == 1 ? 2 : (j == 2 ? 1 : j); }
+__host__ __device__ constexpr int col_pos(int c) { return (c & ~3) + col_slot(c & 3); }
 
 struct StepArgs {
     const ClothDesc* desc;
@@ -53,8 +58,8 @@ struct StepArgs {
 };
 
 // Launchers (plain_step.cu, state.cu).
-cudaError_t launch_plain_step(const StepArgs& a, bool damp, bool forces_only, int grid, int block,
-                              cudaStream_t s);
+cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
+cudaError_t launch_plain_step_damp(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
 cudaError_t launch_set_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,
                              const float* x, const float* v, float* state, cudaStream_t s);
 cudaError_t launch_get_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,

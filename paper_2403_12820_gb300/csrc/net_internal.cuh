@@ -1,0 +1,93 @@
+// Internal structures of the CNN cell (Sec. 3.2, Eq. 6-7) in libcloth.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cloth_internal.cuh"
+
+namespace cloth {
+
+// Weight blob offsets (floats): W1[32][6][3][3], W2[32][32][3][3],
+// WL[3][32][3][3], bL[3], P[32][32], WN[3][32], WD[3][32], in_scale[6],
+// out_scale[3].
+constexpr int kC = 32;
+constexpr int kOffW1 = 0;
+constexpr int kOffW2 = kOffW1 + kC * 6 * 9;
+constexpr int kOffWL = kOffW2 + kC * kC * 9;
+constexpr int kOffBL = kOffWL + 3 * kC * 9;
+constexpr int kOffP = kOffBL + 3;
+constexpr int kOffWN = kOffP + kC * kC;
+constexpr int kOffWD = kOffWN + 3 * kC;
+constexpr int kParams = kOffWD + 3 * kC;   // 13027 trainable
+constexpr int kOffIns = kParams;
+constexpr int kOffOuts = kOffIns + 6;
+constexpr int kBlob = kOffOuts + 3;        // 13036
+
+// Blocks of the weight-gradient kernels; each writes one partial row of
+// kParams floats that a fixed-order reduction sums.
+constexpr int kWgradBlocks = 512;
+
+// Saved activations of net_forward for net_backward, per node (floats), as
+// NCHW regions of the N images:
+//   T1 [N][2][32] (phi1, xi1)   T2 [N][2][32] (phi, xi)   S [N][32] (s)
+//   G2 [N][2][32] (d phi, d xi) GT [N][32] (d t)          GY [N][3] (d y)
+// net_backward writes d phi1, d xi1 over T2 once T2 is no longer needed.
+constexpr int64_t kSavT1 = 0, kSavT2 = 64, kSavS = 128, kSavG2 = 160, kSavGT = 224, kSavGY = 256;
+constexpr int64_t kSavedPerNode = 260;
+
+// Where the cell reads its 6 input channels from.
+struct NetSrc {
+    // NCHW input z [N][6][H][W] (net_forward) ...
+    const float* z;
+    // ... or the cloth state planes (cloth_step_net): image n is cloth
+    // cloth_of[n]; u = planes 0-2, v = planes 3-5, permuted column order
+    const ClothDesc* desc;
+    const int32_t* cloth_of;
+    const float* state;
+};
+
+struct NetFwdArgs {
+    NetSrc src;
+    const float* w;     // FP32 weight blob (device)
+    float* t1;          // [N][2][32][H][W]
+    float* t2;          // [N][2][32][H][W]
+    float* s;           // [N][32][H][W] or nullptr
+    float* a;           // [N][3][H][W]
+    int N, H, W;
+};
+
+cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s);
+cudaError_t launch_net_backward_simt(const float* w, const float* z, float* saved, const float* ga, float* gz,
+                                     float* partials, float* gw, int N, int H, int W, cudaStream_t s);
+// Network step update: v <- C(v + dt (a + f_p / m)), u <- u + dt v, sphere.
+cudaError_t launch_net_update(const ClothDesc* desc, const int32_t* cloth_of, int n, int H, int W, const float* a,
+                              const float* src, float* dst, const uint32_t* pinmask, int32_t* status, cudaStream_t s);
+cudaError_t net_simt_init();
+int net_last_cuda_error();
+
+
+// Host side of a network handle (include/cloth.h: cloth_net).
+struct NetLayout {
+    size_t blob, part, total;
+};
+inline NetLayout net_layout()
+{
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    NetLayout L{};
+    size_t off = 0;
+    L.blob = off; off = al(off + sizeof(float) * kBlob);
+    L.part = off; off = al(off + sizeof(float) * (size_t)kWgradBlocks * kParams);
+    L.total = off;
+    return L;
+}
+
+}  // namespace cloth
+
+struct cloth_net {
+    int32_t precision = 0;
+    char* ws = nullptr;
+    cloth::NetLayout L{};
+    float* d_w() const { return reinterpret_cast<float*>(ws + L.blob); }
+    float* d_part() const { return reinterpret_cast<float*>(ws + L.part); }
+};

@@ -1,0 +1,560 @@
+// CNN cell (Sec. 3.2, Eq. 6-7) in FP32 on CUDA cores: forward with saved
+// activations, hand-written backward, and the network-step update (Fig. 2).
+//
+// Layer by layer, NCHW FP32 activations, every 3x3 convolution a tiled
+// kernel: a block of 128 threads computes a 32 x 8 tile of nodes for all
+// output channels (each thread 2 nodes, rows ty and ty + 4), with the input
+// tile plus its 1-node halo and the weights staged in shared memory.  Weight
+// gradients are per-block partial sums over a fixed assignment of tiles,
+// reduced in a fixed order, so results are bitwise reproducible.
+#include "net_internal.cuh"
+
+namespace cloth {
+namespace {
+
+constexpr int TW = 32, TH = 8, NT = 128;
+
+// ----------------------------------------------------------------- views
+// Cell input, field f of image n: f = 0 -> in_scale[0:3] u, f = 1 ->
+// in_scale[3:6] v.  Image index img = 2 n + f.
+struct InZ {
+    NetSrc src;
+    const float* w;
+    int H, W;
+    __device__ float operator()(int img, int c, int y, int x) const
+    {
+        const int n = img >> 1, f = img & 1;
+        const float sc = w[kOffIns + 3 * f + c];
+        if (src.z) return sc * src.z[(((int64_t)n * 6 + 3 * f + c) * H + y) * W + x];
+        const ClothDesc& D = src.desc[src.cloth_of[n]];
+        return sc * src.state[D.plane_off + (3 * f + c) * D.plane_stride + (int64_t)y * D.pitch + col_pos(x)];
+    }
+};
+
+// Plain NCHW tensor: image i at p + (i * img_mul + img_add) * img_stride.
+struct View {
+    const float* p;
+    int64_t img_stride, HW;
+    int W, img_mul, img_add;
+    __device__ float operator()(int i, int c, int y, int x) const
+    {
+        return p[(int64_t)(i * img_mul + img_add) * img_stride + c * HW + (int64_t)y * W + x];
+    }
+};
+
+struct ProdView {   // elementwise product of two views (xi . s)
+    View a, b;
+    __device__ float operator()(int i, int c, int y, int x) const { return a(i, c, y, x) * b(i, c, y, x); }
+};
+
+struct Ones {
+    __device__ float operator()(int, int, int, int) const { return 1.f; }
+};
+
+// Field f of the scaled cell input of image n: in_scale[3f + c] z[n][3f + c].
+struct ZView {
+    const float* z;
+    const float* w;
+    int64_t HW;
+    int W, f;
+    __device__ float operator()(int n, int c, int y, int x) const
+    {
+        return w[kOffIns + 3 * f + c] * z[((int64_t)n * 6 + 3 * f + c) * HW + (int64_t)y * W + x];
+    }
+};
+
+struct OutView {
+    float* p;
+    int64_t img_stride, HW;
+    int W;
+    __device__ void operator()(int i, int c, int y, int x, float v) const
+    {
+        p[(int64_t)i * img_stride + c * HW + (int64_t)y * W + x] = v;
+    }
+};
+
+// d z output of field f = img & 1 into channels 3 f .. 3 f + 2, times in_scale.
+struct OutGz {
+    float* gz;
+    const float* w;
+    int H, W;
+    __device__ void operator()(int img, int c, int y, int x, float v) const
+    {
+        const int n = img >> 1, f = img & 1;
+        gz[(((int64_t)n * 6 + 3 * f + c) * H + y) * W + x] = w[kOffIns + 3 * f + c] * v;
+    }
+};
+
+// ----------------------------------------------------------------- weights
+// W(o, i, tap) of the convolution computed: o = output, i = input channel.
+struct WtW1 {   // phi1 / xi1 = W1 (*) [zu; 0] / [0; zv]: field f uses W1[:, 3f:3f+3]
+    const float* w;
+    __device__ float operator()(int img, int o, int i, int tap) const
+    {
+        return w[kOffW1 + (o * 6 + 3 * (img & 1) + i) * 9 + tap];
+    }
+};
+struct WtW2 {
+    const float* w;
+    __device__ float operator()(int, int o, int i, int tap) const { return w[kOffW2 + (o * kC + i) * 9 + tap]; }
+};
+// Transposed convolutions (adjoint wrt the input): swap the channel roles
+// and flip the taps.
+struct WtW2T {
+    const float* w;
+    __device__ float operator()(int, int o, int i, int tap) const { return w[kOffW2 + (i * kC + o) * 9 + (8 - tap)]; }
+};
+struct WtW1T {
+    const float* w;
+    __device__ float operator()(int img, int o, int i, int tap) const
+    {
+        return w[kOffW1 + (i * 6 + 3 * (img & 1) + o) * 9 + (8 - tap)];
+    }
+};
+
+// ----------------------------------------------------------------- conv
+// out(img, o, y, x) = sum_{i, ky, kx} W(o, i, ky, kx) in(img, i, y+ky-1, x+kx-1)
+// with zero outside [0, H) x [0, W).  Grid: (tiles_x, tiles_y, images).
+template <int CIN, int COUT, class In, class Wt, class Out>
+__global__ void __launch_bounds__(NT) conv3x3_kernel(In in, Wt wt, Out out, int H, int W)
+{
+    constexpr int COUTP = (COUT + 3) / 4 * 4;
+    extern __shared__ float4 smem4[];
+    float* s_w = reinterpret_cast<float*>(smem4);          // [9][CIN][COUTP]
+    float* s_in = s_w + 9 * CIN * COUTP;                   // [CIN][TH+2][TW+2]
+    const int img = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 9 * CIN * COUTP; e += NT) {
+        const int tap = e / (CIN * COUTP), rem = e % (CIN * COUTP), i = rem / COUTP, o = rem % COUTP;
+        s_w[e] = o < COUT ? wt(img, o, i, tap) : 0.f;
+    }
+    for (int e = tid; e < CIN * (TH + 2) * (TW + 2); e += NT) {
+        const int i = e / ((TH + 2) * (TW + 2)), rem = e % ((TH + 2) * (TW + 2));
+        const int y = y0 + rem / (TW + 2) - 1, x = x0 + rem % (TW + 2) - 1;
+        s_in[e] = (y >= 0 && y < H && x >= 0 && x < W) ? in(img, i, y, x) : 0.f;
+    }
+    __syncthreads();
+    const int tx = tid & 31, ty = tid >> 5;
+    float acc0[COUTP], acc1[COUTP];
+#pragma unroll
+    for (int o = 0; o < COUTP; ++o) acc0[o] = acc1[o] = 0.f;
+    for (int i = 0; i < CIN; ++i) {
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const float* si = s_in + (i * (TH + 2) + ty + ky) * (TW + 2) + tx + kx;
+                const float a0 = si[0], a1 = si[4 * (TW + 2)];
+                const float4* w4 = reinterpret_cast<const float4*>(s_w + ((ky * 3 + kx) * CIN + i) * COUTP);
+#pragma unroll
+                for (int q = 0; q < COUTP / 4; ++q) {
+                    const float4 w = w4[q];
+                    acc0[4 * q + 0] = fmaf(w.x, a0, acc0[4 * q + 0]); acc1[4 * q + 0] = fmaf(w.x, a1, acc1[4 * q + 0]);
+                    acc0[4 * q + 1] = fmaf(w.y, a0, acc0[4 * q + 1]); acc1[4 * q + 1] = fmaf(w.y, a1, acc1[4 * q + 1]);
+                    acc0[4 * q + 2] = fmaf(w.z, a0, acc0[4 * q + 2]); acc1[4 * q + 2] = fmaf(w.z, a1, acc1[4 * q + 2]);
+                    acc0[4 * q + 3] = fmaf(w.w, a0, acc0[4 * q + 3]); acc1[4 * q + 3] = fmaf(w.w, a1, acc1[4 * q + 3]);
+                }
+            }
+    }
+    const int x = x0 + tx;
+    if (x < W) {
+        if (y0 + ty < H)
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) out(img, o, y0 + ty, x, acc0[o]);
+        if (y0 + ty + 4 < H)
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) out(img, o, y0 + ty + 4, x, acc1[o]);
+    }
+}
+
+template <int CIN, int COUT>
+constexpr int conv_smem() { return (9 * CIN * ((COUT + 3) / 4 * 4) + CIN * (TH + 2) * (TW + 2)) * 4; }
+
+template <int CIN, int COUT, class In, class Wt, class Out>
+cudaError_t conv3x3(In in, Wt wt, Out out, int H, int W, int images, cudaStream_t s)
+{
+    if (images <= 0 || H <= 0 || W <= 0) return cudaSuccess;
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, images);
+    conv3x3_kernel<CIN, COUT, In, Wt, Out><<<grid, NT, conv_smem<CIN, COUT>(), s>>>(in, wt, out, H, W);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- branches
+// Eq. 7 on the trunk output t2 = (phi, xi): L = WL (*) phi + bL,
+// s = tanh(P phi), N = WN s, D = WD (xi . s), a = out_scale (L + N + D).
+constexpr int kBranchSmem = (3 * kC * 9 + kC * kC + 6 * kC + 8 + kC * (TH + 2) * (TW + 2)) * 4;
+
+__global__ void __launch_bounds__(NT) branch_fwd_kernel(const float* __restrict__ w, const float* __restrict__ t2,
+                                                        float* __restrict__ s_out, float* __restrict__ a, int H, int W)
+{
+    extern __shared__ float4 smem4[];
+    float* sWL = reinterpret_cast<float*>(smem4);     // [3][32][9]
+    float* sP = sWL + 3 * kC * 9;                     // [32][32]
+    float* sWN = sP + kC * kC;                        // [3][32]
+    float* sWD = sWN + 3 * kC;                        // [3][32]
+    float* sB = sWD + 3 * kC;                         // bL[3], out_scale[3]
+    float* sPhi = sB + 8;                             // [32][TH+2][TW+2]
+    const int n = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, tid = threadIdx.x;
+    const int64_t HW = (int64_t)H * W;
+    for (int e = tid; e < 3 * kC * 9; e += NT) sWL[e] = w[kOffWL + e];
+    for (int e = tid; e < kC * kC; e += NT) sP[e] = w[kOffP + e];
+    for (int e = tid; e < 3 * kC; e += NT) { sWN[e] = w[kOffWN + e]; sWD[e] = w[kOffWD + e]; }
+    if (tid < 3) { sB[tid] = w[kOffBL + tid]; sB[3 + tid] = w[kOffOuts + tid]; }
+    const float* phi = t2 + (int64_t)n * 2 * kC * HW;
+    const float* xi = phi + kC * HW;
+    for (int e = tid; e < kC * (TH + 2) * (TW + 2); e += NT) {
+        const int i = e / ((TH + 2) * (TW + 2)), rem = e % ((TH + 2) * (TW + 2));
+        const int y = y0 + rem / (TW + 2) - 1, x = x0 + rem % (TW + 2) - 1;
+        sPhi[e] = (y >= 0 && y < H && x >= 0 && x < W) ? phi[i * HW + (int64_t)y * W + x] : 0.f;
+    }
+    __syncthreads();
+    const int tx = tid & 31, x = x0 + tx;
+    for (int half = 0; half < 2; ++half) {
+        const int ly = (tid >> 5) + 4 * half, y = y0 + ly;
+        if (x >= W || y >= H) continue;
+        float L[3] = {sB[0], sB[1], sB[2]};
+        for (int i = 0; i < kC; ++i)
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx) {
+                    const float v = sPhi[(i * (TH + 2) + ly + ky) * (TW + 2) + tx + kx];
+#pragma unroll
+                    for (int o = 0; o < 3; ++o) L[o] = fmaf(sWL[(o * kC + i) * 9 + ky * 3 + kx], v, L[o]);
+                }
+        float pc[kC];
+#pragma unroll
+        for (int i = 0; i < kC; ++i) pc[i] = sPhi[(i * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
+        float Nn[3] = {0.f, 0.f, 0.f}, Dd[3] = {0.f, 0.f, 0.f};
+        const int64_t p = (int64_t)y * W + x;
+        for (int c = 0; c < kC; ++c) {
+            float t = 0.f;
+            const float4* pr = reinterpret_cast<const float4*>(sP + c * kC);
+#pragma unroll
+            for (int q = 0; q < kC / 4; ++q) {
+                const float4 pw = pr[q];
+                t = fmaf(pw.x, pc[4 * q], fmaf(pw.y, pc[4 * q + 1], fmaf(pw.z, pc[4 * q + 2], fmaf(pw.w, pc[4 * q + 3], t))));
+            }
+            const float sv = tanhf(t);
+            const float xs = xi[c * HW + p] * sv;
+            if (s_out) s_out[((int64_t)n * kC + c) * HW + p] = sv;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                Nn[o] = fmaf(sWN[o * kC + c], sv, Nn[o]);
+                Dd[o] = fmaf(sWD[o * kC + c], xs, Dd[o]);
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 3; ++o) a[((int64_t)n * 3 + o) * HW + p] = sB[3 + o] * (L[o] + Nn[o] + Dd[o]);
+    }
+}
+
+// Backward through Eq. 7 at every node: from d a to d y = out_scale d a,
+// d xi, d t = d s (1 - s^2) and d phi = P^T d t + WL^T (*) d y.
+__global__ void __launch_bounds__(NT) branch_bwd_kernel(const float* __restrict__ w, const float* __restrict__ ga,
+                                                        float* __restrict__ saved, int H, int W)
+{
+    extern __shared__ float4 smem4[];
+    float* sWL = reinterpret_cast<float*>(smem4);     // [3][32][9]
+    float* sP = sWL + 3 * kC * 9;                     // [32][32]
+    float* sWN = sP + kC * kC;
+    float* sWD = sWN + 3 * kC;
+    float* sB = sWD + 3 * kC;                         // out_scale[3]
+    float* sGy = sB + 8;                              // [3][TH+2][TW+2]
+    const int n = blockIdx.z, N = gridDim.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, tid = threadIdx.x;
+    const int64_t HW = (int64_t)H * W, NHW = (int64_t)N * HW;
+    for (int e = tid; e < 3 * kC * 9; e += NT) sWL[e] = w[kOffWL + e];
+    for (int e = tid; e < kC * kC; e += NT) sP[e] = w[kOffP + e];
+    for (int e = tid; e < 3 * kC; e += NT) { sWN[e] = w[kOffWN + e]; sWD[e] = w[kOffWD + e]; }
+    if (tid < 3) sB[tid] = w[kOffOuts + tid];
+    __syncthreads();
+    for (int e = tid; e < 3 * (TH + 2) * (TW + 2); e += NT) {
+        const int o = e / ((TH + 2) * (TW + 2)), rem = e % ((TH + 2) * (TW + 2));
+        const int y = y0 + rem / (TW + 2) - 1, x = x0 + rem % (TW + 2) - 1;
+        sGy[e] = (y >= 0 && y < H && x >= 0 && x < W) ? sB[o] * ga[((int64_t)n * 3 + o) * HW + (int64_t)y * W + x] : 0.f;
+    }
+    __syncthreads();
+    const float* xi = saved + kSavT2 * NHW + ((int64_t)n * 2 + 1) * kC * HW;
+    const float* sv = saved + kSavS * NHW + (int64_t)n * kC * HW;
+    float* gphi = saved + kSavG2 * NHW + (int64_t)n * 2 * kC * HW;
+    float* gxi = gphi + kC * HW;
+    float* gt = saved + kSavGT * NHW + (int64_t)n * kC * HW;
+    float* gy = saved + kSavGY * NHW + (int64_t)n * 3 * HW;
+    const int tx = tid & 31, x = x0 + tx;
+    for (int half = 0; half < 2; ++half) {
+        const int ly = (tid >> 5) + 4 * half, y = y0 + ly;
+        if (x >= W || y >= H) continue;
+        const int64_t p = (int64_t)y * W + x;
+        float g[3];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            g[o] = sGy[(o * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
+            gy[o * HW + p] = g[o];
+        }
+        float gtl[kC];
+        for (int c = 0; c < kC; ++c) {
+            const float s = sv[c * HW + p], xv = xi[c * HW + p];
+            float gxs = 0.f, gs = 0.f;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                gxs = fmaf(sWD[o * kC + c], g[o], gxs);
+                gs = fmaf(sWN[o * kC + c], g[o], gs);
+            }
+            gs = fmaf(gxs, xv, gs);
+            gxi[c * HW + p] = gxs * s;
+            gtl[c] = gs * (1.f - s * s);
+            gt[c * HW + p] = gtl[c];
+        }
+        for (int i = 0; i < kC; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c = 0; c < kC; ++c) acc = fmaf(sP[c * kC + i], gtl[c], acc);
+            // WL^T (*) d y: d phi_i(p) += sum_o,ky,kx WL[o][i][ky][kx] d y_o(p - (ky-1, kx-1))
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                    for (int o = 0; o < 3; ++o)
+                        acc = fmaf(sWL[(o * kC + i) * 9 + ky * 3 + kx],
+                                   sGy[(o * (TH + 2) + ly + 2 - ky) * (TW + 2) + tx + 2 - kx], acc);
+            gphi[i * HW + p] = acc;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- wgrad
+// Partial weight gradients: for the tiles t = blockIdx.x, + gridDim.x, ...
+// (tile = 32 x 8 nodes of image i), out[(a * BSTRIDE + b) * TAPS + tap] +=
+// sum_pixels A(i, a, y, x) B(i, b, y + dy, x + dx) with B zero outside the
+// image.  Thread (ab, b) owns a in [ab*ABLK, ab*ABLK+ABLK) and one b.
+template <int CA, int CB, int TAPS, int ABLK, class AV, class BV>
+__global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, int bstride, int H, int W, int n_img)
+{
+    constexpr int HB = TAPS == 9 ? 1 : 0;   // halo of the B tile
+    extern __shared__ float4 smem4[];
+    float* sA = reinterpret_cast<float*>(smem4);          // [CA][TH][TW]
+    float* sB = sA + CA * TH * TW;                          // [CB][TH+2HB][TW+2HB] (+1 pad)
+    constexpr int BW = TW + 2 * HB, BH = TH + 2 * HB, BPL = BH * BW + 1;
+    const int tid = threadIdx.x;
+    const int ab = tid / CB, b = tid % CB;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int n_tiles = tiles_x * tiles_y * n_img;
+    float acc[ABLK][TAPS];
+#pragma unroll
+    for (int j = 0; j < ABLK; ++j)
+#pragma unroll
+        for (int t = 0; t < TAPS; ++t) acc[j][t] = 0.f;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int i = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
+        const int y0 = (rem / tiles_x) * TH, x0 = (rem % tiles_x) * TW;
+        __syncthreads();
+        for (int e = tid; e < CA * TH * TW; e += blockDim.x) {
+            const int a = e / (TH * TW), r2 = e % (TH * TW), y = y0 + r2 / TW, x = x0 + r2 % TW;
+            sA[e] = (y < H && x < W) ? A(i, a, y, x) : 0.f;
+        }
+        for (int e = tid; e < CB * BH * BW; e += blockDim.x) {
+            const int bb = e / (BH * BW), r2 = e % (BH * BW);
+            const int y = y0 + r2 / BW - HB, x = x0 + r2 % BW - HB;
+            sB[bb * BPL + r2] = (y >= 0 && y < H && x >= 0 && x < W) ? B(i, bb, y, x) : 0.f;
+        }
+        __syncthreads();
+        if (ab < CA / ABLK) {
+            for (int py = 0; py < TH; ++py)
+                for (int px = 0; px < TW; ++px) {
+                    float av[ABLK];
+#pragma unroll
+                    for (int j = 0; j < ABLK; ++j) av[j] = sA[((ab * ABLK + j) * TH + py) * TW + px];
+#pragma unroll
+                    for (int t = 0; t < TAPS; ++t) {
+                        const int dy = TAPS == 9 ? t / 3 : 0, dx = TAPS == 9 ? t % 3 : 0;
+                        const float bv = sB[b * BPL + (py + dy) * BW + px + dx];
+#pragma unroll
+                        for (int j = 0; j < ABLK; ++j) acc[j][t] = fmaf(av[j], bv, acc[j][t]);
+                    }
+                }
+        }
+    }
+    if (ab < CA / ABLK) {
+        float* out = part + (int64_t)blockIdx.x * kParams + out_off;
+#pragma unroll
+        for (int j = 0; j < ABLK; ++j)
+#pragma unroll
+            for (int t = 0; t < TAPS; ++t) out[((ab * ABLK + j) * bstride + b) * TAPS + t] = acc[j][t];
+    }
+}
+
+template <int CA, int CB, int TAPS, int ABLK, class AV, class BV>
+cudaError_t wgrad(AV A, BV B, float* part, int out_off, int bstride, int H, int W, int n_img, cudaStream_t s)
+{
+    constexpr int NTH = (CA / ABLK) * CB;
+    constexpr int HB = TAPS == 9 ? 1 : 0;
+    constexpr int smem = (CA * TH * TW + CB * ((TH + 2 * HB) * (TW + 2 * HB) + 1)) * 4;
+    wgrad_kernel<CA, CB, TAPS, ABLK, AV, BV><<<kWgradBlocks, NTH < 32 ? 32 : NTH, smem, s>>>(A, B, part, out_off, bstride,
+                                                                                        H, W, n_img);
+    return cudaGetLastError();
+}
+
+// gw[j] += sum over blocks g (in order) of part[g][j]
+__global__ void reduce_partials_kernel(const float* __restrict__ part, float* __restrict__ gw)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kParams) return;
+    float s = 0.f;
+    for (int g = 0; g < kWgradBlocks; ++g) s += part[(int64_t)g * kParams + j];
+    gw[j] += s;
+}
+
+// ----------------------------------------------------------------- update
+// v <- C(v + dt (a + f_p / m)), u <- u + dt v, sphere contact; f_p by
+// Eq. 3 (1/4 reading) as (d'_E - d'_W) x (d'_N - d'_S).
+__global__ void net_update_kernel(const ClothDesc* __restrict__ desc, const int32_t* __restrict__ cloth_of, int H,
+                                  int W, const float* __restrict__ a, const float* __restrict__ src,
+                                  float* __restrict__ dst, const uint32_t* __restrict__ pinmask,
+                                  int32_t* __restrict__ status)
+{
+    const int n = blockIdx.z;
+    const ClothDesc& D = desc[cloth_of[n]];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const int64_t HW = (int64_t)H * W;
+    const float* S = src + D.plane_off;
+    auto at = [&](int plane, int yy, int xx) { return S[plane * D.plane_stride + (int64_t)yy * D.pitch + col_pos(xx)]; };
+    float u[3], v[3], acc[3];
+    for (int c = 0; c < 3; ++c) {
+        u[c] = at(c, y, x);
+        v[c] = at(3 + c, y, x);
+        acc[c] = a[((int64_t)n * 3 + c) * HW + (int64_t)y * W + x];
+    }
+    if (D.p_quarter != 0.f) {
+        const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
+        float e[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
+        for (int c = 0; c < 3; ++c) {
+            if (bE) e[c] += at(c, y, x + 1) - u[c] + (c == 0 ? D.h : 0.f);
+            if (bW) e[c] -= at(c, y, x - 1) - u[c] - (c == 0 ? D.h : 0.f);
+            if (bN) nn[c] += at(c, y + 1, x) - u[c] + (c == 1 ? D.h : 0.f);
+            if (bS) nn[c] -= at(c, y - 1, x) - u[c] - (c == 1 ? D.h : 0.f);
+        }
+        const float sc = D.p_quarter * D.inv_m;
+        acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
+        acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
+        acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
+    }
+    const bool pinned = (pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
+    float vn[3], un[3];
+    for (int c = 0; c < 3; ++c) {
+        vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], v[c]);
+        un[c] = fmaf(D.dt, vn[c], u[c]);
+    }
+    if (D.sph_on) {
+        const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0], ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
+        const float rz = un[2] - D.sph_cz;
+        const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        if (dd < D.sph_r2 && dd > 0.f) {
+            const float sc = D.sph_r * rsqrtf(dd);
+            un[0] = fmaf(sc, rx, un[0] - rx);
+            un[1] = fmaf(sc, ry, un[1] - ry);
+            un[2] = fmaf(sc, rz, un[2] - rz);
+            vn[0] = vn[1] = vn[2] = 0.f;
+        }
+    }
+    if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(status, 1);
+    float* O = dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
+    for (int c = 0; c < 3; ++c) {
+        O[c * D.plane_stride] = un[c];
+        O[(3 + c) * D.plane_stride] = vn[c];
+    }
+}
+
+}  // namespace
+
+cudaError_t net_simt_init()
+{
+    cudaError_t e;
+#define SET_SMEM(kern, bytes)                                                                   \
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) \
+        return e;
+    SET_SMEM((conv3x3_kernel<3, kC, InZ, WtW1, OutView>), (conv_smem<3, kC>()));
+    SET_SMEM((conv3x3_kernel<kC, kC, View, WtW2, OutView>), (conv_smem<kC, kC>()));
+    SET_SMEM((conv3x3_kernel<kC, kC, View, WtW2T, OutView>), (conv_smem<kC, kC>()));
+    SET_SMEM((conv3x3_kernel<kC, 3, View, WtW1T, OutGz>), (conv_smem<kC, 3>()));
+    SET_SMEM(branch_fwd_kernel, kBranchSmem);
+    SET_SMEM(branch_bwd_kernel, kBranchSmem);
+    SET_SMEM((wgrad_kernel<kC, kC, 9, 4, View, View>), ((kC * TH * TW + kC * ((TH + 2) * (TW + 2) + 1)) * 4));
+    SET_SMEM((wgrad_kernel<kC, kC, 1, 4, View, View>), ((kC * TH * TW + kC * (TH * TW + 1)) * 4));
+#undef SET_SMEM
+    return cudaSuccess;
+}
+
+cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s)
+{
+    const int H = f.H, W = f.W, N = f.N;
+    const int64_t HW = (int64_t)H * W;
+    cudaError_t e;
+    // Eq. 6: phi1 = W1 (*) [zu; 0], xi1 = W1 (*) [0; zv] (images 2n + field)
+    e = conv3x3<3, kC>(InZ{f.src, f.w, H, W}, WtW1{f.w}, OutView{f.t1, kC * HW, HW, W}, H, W, 2 * N, s);
+    if (e != cudaSuccess) return e;
+    // phi = W2 (*) phi1, xi = W2 (*) xi1
+    e = conv3x3<kC, kC>(View{f.t1, kC * HW, HW, W, 1, 0}, WtW2{f.w}, OutView{f.t2, kC * HW, HW, W}, H, W, 2 * N, s);
+    if (e != cudaSuccess) return e;
+    // Eq. 7
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, N);
+    branch_fwd_kernel<<<grid, NT, kBranchSmem, s>>>(f.w, f.t2, f.s, f.a, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_backward_simt(const float* w, const float* z, float* saved, const float* ga, float* gz,
+                                     float* part, float* gw, int N, int H, int W, cudaStream_t s)
+{
+    const int64_t HW = (int64_t)H * W, NHW = (int64_t)N * HW;
+    float* T1 = saved + kSavT1 * NHW;
+    float* T2 = saved + kSavT2 * NHW;
+    float* Sv = saved + kSavS * NHW;
+    float* G2 = saved + kSavG2 * NHW;
+    float* GT = saved + kSavGT * NHW;
+    float* GY = saved + kSavGY * NHW;
+    cudaError_t e;
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, N);
+    branch_bwd_kernel<<<grid, NT, kBranchSmem, s>>>(w, ga, saved, H, W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const View gy{GY, 3 * HW, HW, W, 1, 0};
+    const View phi{T2, 2 * kC * HW, HW, W, 1, 0};          // image n -> T2[n][0]
+    const View xi{T2 + kC * HW, 2 * kC * HW, HW, W, 1, 0};  // image n -> T2[n][1]
+    const View sv{Sv, kC * HW, HW, W, 1, 0};
+    const View gt{GT, kC * HW, HW, W, 1, 0};
+    // weight gradients of Eq. 7: WL, bL, P, WN, WD
+    if ((e = wgrad<3, kC, 9, 3>(gy, phi, part, kOffWL, kC, H, W, N, s)) != cudaSuccess) return e;
+    if ((e = wgrad<3, 1, 1, 3>(gy, Ones{}, part, kOffBL, 1, H, W, N, s)) != cudaSuccess) return e;
+    if ((e = wgrad<kC, kC, 1, 4>(gt, phi, part, kOffP, kC, H, W, N, s)) != cudaSuccess) return e;
+    if ((e = wgrad<3, kC, 1, 3>(gy, sv, part, kOffWN, kC, H, W, N, s)) != cudaSuccess) return e;
+    if ((e = wgrad<3, kC, 1, 3>(gy, ProdView{xi, sv}, part, kOffWD, kC, H, W, N, s)) != cudaSuccess) return e;
+    // W2: d phi1 = W2^T (*) d phi (into the T2 region, now free), d W2
+    float* G1 = T2;
+    if ((e = wgrad<kC, kC, 9, 4>(View{G2, kC * HW, HW, W, 1, 0}, View{T1, kC * HW, HW, W, 1, 0}, part, kOffW2, kC, H, W,
+                                 2 * N, s)) != cudaSuccess)
+        return e;
+    if ((e = conv3x3<kC, kC>(View{G2, kC * HW, HW, W, 1, 0}, WtW2T{w}, OutView{G1, kC * HW, HW, W}, H, W, 2 * N, s)) !=
+        cudaSuccess)
+        return e;
+    // W1: per field, d W1[:, 3f:3f+3] from d phi1 / d xi1 and the scaled input
+    for (int f = 0; f < 2; ++f) {
+        if ((e = wgrad<kC, 3, 9, 4>(View{G1, kC * HW, HW, W, 2, f}, ZView{z, w, HW, W, f}, part, kOffW1 + 27 * f, 6, H, W,
+                                    N, s)) != cudaSuccess)
+            return e;
+    }
+    reduce_partials_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(part, gw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (gz)
+        return conv3x3<kC, 3>(View{G1, kC * HW, HW, W, 1, 0}, WtW1T{w}, OutGz{gz, w, H, W}, H, W, 2 * N, s);
+    return cudaSuccess;
+}
+
+cudaError_t launch_net_update(const ClothDesc* desc, const int32_t* cloth_of, int n, int H, int W, const float* a,
+                              const float* src, float* dst, const uint32_t* pinmask, int32_t* status, cudaStream_t s)
+{
+    dim3 grid((W + 127) / 128, H, n);
+    net_update_kernel<<<grid, 128, 0, s>>>(desc, cloth_of, H, W, a, src, dst, pinmask, status);
+    return cudaGetLastError();
+}
+
+}  // namespace cloth

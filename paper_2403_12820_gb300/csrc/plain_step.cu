@@ -1,134 +1,128 @@
 // Plain mass-spring step (Sec. 3.1, Eq. 1-5) for a batch of cloths of
-// uneven sizes in one launch.
+// uneven sizes in one launch, in paired FP32 (f32x2) arithmetic.  Serves
+// every batch without spring-axis damping (mu = 0; plain_step_damp.cu
+// handles mu != 0).
 //
 // Mapping: one warp per work unit (cloth b, strip of kStrip = 120 output
 // columns, output rows [r0, r1)).  Lane l holds the 4 consecutive columns
-// c0 - 4 + 4l .. c0 - 1 + 4l as float4 loads of the SoA planes.  The warp
-// marches down the rows with a register window of 4 position rows
-// (r-1 .. r+2).  At row r every node evaluates its 6 "forward" springs
-// (E, 2E, N, 2N, NE, NW); the reaction -F goes to the partner's accumulator
-// either in registers (same lane, rows r..r+2) or through one warp shuffle
-// (neighbour lane).  After row r's springs, its force accumulator holds all
-// 12 springs (the backward ones arrived from rows r-2, r-1 and from the left
-// lane), so the node is finished: pressure (Eq. 3), gravity and drag
-// (Eq. 4), the semi-implicit Euler update with pins (Eq. 5) and sphere
-// contact, then the float4 store.  Each spring is evaluated once, with
-// 1 rsqrt and 1 fast division.
+// c = c4 .. c4 + 3 (c4 = c0 - 4 + 4 l) as the column pairs A = (c0, c2) and
+// B = (c1, c3); lanes 1..30 own the output columns, lanes 0 and 31 are halo
+// lanes.  The warp marches down the rows with a register window of the
+// position rows r .. r+2 (r+3 in flight).  At row r each node evaluates its
+// 6 "forward" springs (E, 2E, N, 2N, NE, NW) once, as 12 spring pairs of
+// one type on (c0, c2) or (c1, c3); the reaction -F lands in the partner's
+// accumulator, in registers (same lane, rows r .. r+2) or through one warp
+// shuffle (neighbour lane).  After row r its accumulator holds all 12
+// springs, and the node is finished: gravity and drag (Eq. 4), the
+// semi-implicit Euler update with pins (Eq. 5), sphere contact, float4
+// stores.  Pressure (Eq. 3) of row r+1 is added while rows r .. r+2 are in
+// the window.
 //
 // Precision: positions are stored as u = x - X (displacement from the rest
-// lattice).  A spring's vector is d = l + du with l the exact lattice
-// offset (multiples of h) and du = u_j - u_i, and its stretch uses
-// |d|^2 - L^2 = du . (2 l + du) (since |l| = L), so (|d| - L) / |d| =
-// (|d|^2 - L^2) / (|d| (|d| + L)) carries no cancellation in FP32.
+// lattice).  A spring's vector is d = l + du with l the lattice offset and
+// du = u_j - u_i, and its stretch uses |d|^2 - L^2 = du . (2 l + du) (since
+// |l| = L), so (|d| - L) / |d| = (|d|^2 - L^2) / (|d| (|d| + L)) carries no
+// cancellation in FP32.
 #include "cloth_internal.cuh"
+
+// Resident blocks of 128 threads per SM the register budget is sized for.
+#ifndef CLOTH_PLAIN_MINB
+#define CLOTH_PLAIN_MINB 3
+#endif
 
 namespace cloth {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+using f2 = float2;
 
-template <int NC>
-struct Row {
-    float c[NC][4];  // [component][column]
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }   // a - b, one rounding
+
+// One row of a lane: the column pairs A = (c0, c2) and B = (c1, c3) of the
+// three components.
+struct Row2 {
+    f2 A[3], B[3];
 };
 
-template <int NC>
-struct Node {
-    float c[NC];
-};
-
-template <int NC>
-__device__ __forceinline__ void zero(Row<NC>& r)
+__device__ __forceinline__ void zero(Row2& r)
 {
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) r.c[c][k] = 0.f;
+    for (int c = 0; c < 3; ++c) r.A[c] = r.B[c] = F2(0.f);
 }
 
-// Load NC planes (starting at plane `plane0`) of one row of 4 columns.
-template <int NC>
-__device__ __forceinline__ void load_row(Row<NC>& r, const float* base, int64_t stride, int plane0, bool ok)
+// Planes plane0 .. plane0+2 of one row; memory order c0 c2 c1 c3.
+__device__ __forceinline__ void load2(Row2& r, const float* base, int64_t stride, int plane0, bool ok)
 {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < 3; ++c) {
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ok) t = __ldg(reinterpret_cast<const float4*>(base + (int64_t)(plane0 + c) * stride));
-        r.c[c][0] = t.x; r.c[c][1] = t.y; r.c[c][2] = t.z; r.c[c][3] = t.w;
+        r.A[c] = make_float2(t.x, t.y);
+        r.B[c] = make_float2(t.z, t.w);
     }
 }
 
-template <int NC>
-__device__ __forceinline__ Node<NC> at(const Row<NC>& r, int k)
+// Lattice offset S h along one axis as a pair (S in {-1, 1, 2}).
+template <int S>
+__device__ __forceinline__ f2 lat(f2 h, f2 h2, f2 nh)
 {
-    Node<NC> n;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) n.c[c] = r.c[c][k];
-    return n;
+    static_assert(S == 1 || S == 2 || S == -1, "lattice offset");
+    return S == 1 ? h : (S == 2 ? h2 : nh);
 }
 
-// Column k of the neighbour lane (delta = +1: lane + 1, delta = -1: lane - 1).
-template <int NC>
-__device__ __forceinline__ Node<NC> from_lane(const Row<NC>& r, int k, int delta)
+// Spring pair of lattice offset (SX, SY) h: returns s with f_i = s d and
+// f_j = -s d, d = x_j - x_i (written to d).  Eq. 1 with x_ij = x_i - x_j
+// gives s = k (|d| - L) / |d| = k (|d|^2 - L^2) / (|d| (|d| + L)).  A half
+// whose spring does not exist gets s = 0.
+template <int SX, int SY>
+__device__ __forceinline__ f2 spring2(const f2 (&ui)[3], const f2 (&uj)[3], f2 h, f2 h2, f2 nh, f2 L, f2 L2, f2 k,
+                                      bool ok0, bool ok1, f2 (&d)[3])
 {
-    Node<NC> n;
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-        n.c[c] = delta > 0 ? __shfl_down_sync(kFull, r.c[c][k], 1) : __shfl_up_sync(kFull, r.c[c][k], 1);
-    return n;
-}
-
-// Force on node i from the spring (i, j) with lattice offset (lx, ly, 0) =
-// X_j - X_i and rest length L: Eq. 1 with x_ij = x_i - x_j gives
-// f_i = k (|d| - L) d / |d|, d = x_j - x_i; Eq. 2 adds mu ((v_j - v_i) . d) d / |d|^2.
-template <int NC>
-__device__ __forceinline__ float3 spring(float lx, float ly, float L, float k, float mu, const Node<NC>& i,
-                                         const Node<NC>& j, bool ok)
-{
-    const float dux = j.c[0] - i.c[0], duy = j.c[1] - i.c[1], duz = j.c[2] - i.c[2];
-    const float dx = lx + dux, dy = ly + duy, dz = duz;
-    const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float num = fmaf(dux, dx + lx, fmaf(duy, dy + ly, duz * dz));   // |d|^2 - L^2
-    const float rq = rsqrtf(q);
-    float s = __fdividef(k * num * rq, fmaf(q, rq, L));
-    if constexpr (NC == 6) {
-        const float dvx = j.c[3] - i.c[3], dvy = j.c[4] - i.c[4], dvz = j.c[5] - i.c[5];
-        s = fmaf(mu * fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz)), rq * rq, s);
+    const f2 dux = sub2(uj[0], ui[0]), duy = sub2(uj[1], ui[1]), duz = sub2(uj[2], ui[2]);
+    f2 num;
+    if constexpr (SX != 0) {
+        const f2 lx = lat<SX>(h, h2, nh);
+        d[0] = add2(lx, dux);
+        num = mul2(dux, add2(d[0], lx));
+    } else {
+        d[0] = dux;
+        num = mul2(dux, dux);
     }
-    s = ok ? s : 0.f;
-    return make_float3(s * dx, s * dy, s * dz);
+    if constexpr (SY != 0) {
+        const f2 ly = lat<SY>(h, h2, nh);
+        d[1] = add2(ly, duy);
+        num = fma2(duy, add2(d[1], ly), num);
+    } else {
+        d[1] = duy;
+        num = fma2(duy, duy, num);
+    }
+    d[2] = duz;
+    num = fma2(duz, duz, num);                       // |d|^2 - L^2
+    const f2 q = add2(num, L2);                      // |d|^2
+    const f2 rq = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+    const f2 den = fma2(q, rq, L);                   // |d| + L
+    const f2 t = mul2(mul2(k, num), rq);
+    f2 s = mul2(t, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)));
+    s.x = ok0 ? s.x : 0.f;
+    s.y = ok1 ? s.y : 0.f;
+    return s;
 }
 
-__device__ __forceinline__ void add3(float (&a)[3][4], int k, float3 f)
+__device__ __forceinline__ void acc2(f2 (&a)[3], f2 s, const f2 (&d)[3])
 {
-    a[0][k] += f.x; a[1][k] += f.y; a[2][k] += f.z;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] = fma2(s, d[c], a[c]);
 }
-__device__ __forceinline__ void sub3(float (&a)[3][4], int k, float3 f)
-{
-    a[0][k] -= f.x; a[1][k] -= f.y; a[2][k] -= f.z;
-}
-__device__ __forceinline__ float3 shfl3_up(float3 f)
-{
-    return make_float3(__shfl_up_sync(kFull, f.x, 1), __shfl_up_sync(kFull, f.y, 1), __shfl_up_sync(kFull, f.z, 1));
-}
-__device__ __forceinline__ float3 shfl3_down(float3 f)
-{
-    return make_float3(__shfl_down_sync(kFull, f.x, 1), __shfl_down_sync(kFull, f.y, 1),
-                       __shfl_down_sync(kFull, f.z, 1));
-}
-__device__ __forceinline__ float3 cross3(float3 a, float3 b)
-{
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float3 fma3(float s, float3 a, float3 b)
-{
-    return make_float3(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z));
-}
+__device__ __forceinline__ float shup(float v) { return __shfl_up_sync(kFull, v, 1); }
+__device__ __forceinline__ float shdn(float v) { return __shfl_down_sync(kFull, v, 1); }
 
-template <bool DAMP, bool FORCES>
-__global__ void __launch_bounds__(128, 3) plain_step_kernel(StepArgs a)
+template <bool FORCES>
+__global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepArgs a)
 {
-    constexpr int NC = DAMP ? 6 : 3;
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -139,8 +133,6 @@ __global__ void __launch_bounds__(128, 3) plain_step_kernel(StepArgs a)
         const ClothDesc& D = a.desc[wu.b];
         const int rows = D.rows, cols = D.cols, pitch = D.pitch;
         const int64_t stride = D.plane_stride;
-        const float h = D.h, h2 = 2.f * D.h, hd = 1.41421356237309515f * D.h;
-        const float ks = D.k_struct, ksh = D.k_shear, kb = D.k_bend, mu = D.mu;
         const int c4 = wu.c0 - 4 + 4 * lane;
         const bool lane_in = c4 >= 0 && c4 < pitch;
         // bit j of cm: column c4 - 1 + j exists (j = 0..6)
@@ -150,197 +142,276 @@ __global__ void __launch_bounds__(128, 3) plain_step_kernel(StepArgs a)
             const int col = c4 - 1 + j;
             cm |= (col >= 0 && col < cols) ? (1u << j) : 0u;
         }
+        auto bit = [&](int j) { return ((cm >> j) & 1u) != 0u; };
+        // column part of each spring pair's existence: own node and partner
+        const bool oA0 = bit(1), oA1 = bit(3), oB0 = bit(2), oB1 = bit(4);
+        const bool eA0 = oA0 && bit(2), eA1 = oA1 && bit(4);      // E, NE of A: partners c1, c3
+        const bool tA0 = oA0 && bit(3), tA1 = oA1 && bit(5);      // 2E of A: c2, c4
+        const bool wA0 = oA0 && bit(0), wA1 = oA1 && bit(2);      // NW of A: c-1, c1
+        const bool eB0 = oB0 && bit(3), eB1 = oB1 && bit(5);      // E, NE of B: c2, c4
+        const bool tB0 = oB0 && bit(4), tB1 = oB1 && bit(6);      // 2E of B: c3, c5
+        const bool wB0 = oB0 && bit(1), wB1 = oB1 && bit(3);      // NW of B: c0, c2
+        // pressure masks: the E neighbour of each half exists (mE) / the W
+        // neighbour exists (mW, stored negated)
+        const f2 mEA = make_float2(bit(2) ? 1.f : 0.f, bit(4) ? 1.f : 0.f);
+        const f2 mWA = make_float2(bit(0) ? -1.f : 0.f, bit(2) ? -1.f : 0.f);
+        const f2 mEB = make_float2(bit(3) ? 1.f : 0.f, bit(5) ? 1.f : 0.f);
+        const f2 mWB = make_float2(bit(1) ? -1.f : 0.f, bit(3) ? -1.f : 0.f);
+
+        const float hs = D.h;
+        const f2 h = F2(hs), h2 = F2(2.f * hs), nh = F2(-hs);
+        const f2 Ls = F2(hs), Ls2 = F2(hs * hs), Lb = F2(2.f * hs), Lb2 = F2(4.f * hs * hs);
+        const f2 Ld = F2(1.41421356237309515f * hs), Ld2 = F2(2.f * hs * hs);
+        const f2 ks = F2(D.k_struct), ksh = F2(D.k_shear), kb = F2(D.k_bend);
+        const f2 hxA = mul2(sub2(mEA, mWA), h), hxB = mul2(sub2(mEB, mWB), h);   // (mE + |mW|) h
+        const float pq = D.p_quarter;
         const int64_t lane_off = D.plane_off + (lane_in ? c4 : 0);
         const float* src = a.src + lane_off;
         auto rok = [&](int q) { return (unsigned)q < (unsigned)rows; };
         auto rowp = [&](int q) { return src + (int64_t)(rok(q) ? q : 0) * pitch; };
 
         const int rb = wu.r0 - 2;
-        Row<NC> P1, P2, P3;  // rows r, r+1, r+2 (u, and v when DAMP)
-        load_row(P1, rowp(rb), stride, 0, lane_in && rok(rb));
-        load_row(P2, rowp(rb + 1), stride, 0, lane_in && rok(rb + 1));
-        load_row(P3, rowp(rb + 2), stride, 0, lane_in && rok(rb + 2));
-        // own velocity of row r (needed for the update; in P1 when DAMP)
-        Row<3> VC, VN;
-        if constexpr (!DAMP) load_row(VC, rowp(rb), stride, 3, lane_in && rok(rb));
-        float A1[3][4], A2[3][4], A3[3][4];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) A1[c][k] = A2[c][k] = A3[c][k] = 0.f;
+        Row2 P0, P1, P2, F0, F1, Fq;   // rows r, r+1, r+2; forces of r, r+1, r+2
+        load2(P0, rowp(rb), stride, 0, lane_in && rok(rb));
+        load2(P1, rowp(rb + 1), stride, 0, lane_in && rok(rb + 1));
+        load2(P2, rowp(rb + 2), stride, 0, lane_in && rok(rb + 2));
+        zero(F0); zero(F1); zero(Fq);
 
         for (int r = rb; r < wu.r1; ++r) {
-            // prefetch row r+3 and (no damping) the velocity of row r+1
-            Row<NC> P4;
-            load_row(P4, rowp(r + 3), stride, 0, lane_in && rok(r + 3));
-            if constexpr (!DAMP) load_row(VN, rowp(r + 1), stride, 3, lane_in && rok(r + 1));
+            // positions of row r+3 are needed next row; the velocity of row r
+            // only at the end of this one: both loads have a row of work to land
+            Row2 PN, V0;
+            load2(PN, rowp(r + 3), stride, 0, lane_in && rok(r + 3));
+            const bool vout = r >= wu.r0 && rok(r) && out_lane;
+            load2(V0, rowp(r), stride, 3, lane_in && vout);
 
             const bool ok_r = rok(r), ok_r1 = rok(r + 1), ok_r2 = rok(r + 2);
-            // neighbour-lane columns: lane+1's columns 0, 1 of row r, column 0
-            // of row r+1; lane-1's column 3 of row r+1
-            const Node<NC> Ra1 = from_lane(P1, 0, +1), Rb1 = from_lane(P1, 1, +1);
-            const Node<NC> Ra2 = from_lane(P2, 0, +1), L2 = from_lane(P2, 3, -1);
-            float3 sendA_r = make_float3(0.f, 0.f, 0.f), sendB_r = sendA_r, sendA_r1 = sendA_r, sendD_r1 = sendA_r;
+            const bool okN = ok_r && ok_r1, ok2N = ok_r && ok_r2;
+            // assembled partner pairs (per component):
+            //   X0 = (c2, c4) of row r, Y0 = (c3, c5) of row r,
+            //   X1 = (c2, c4) of row r+1, Z1 = (c-1, c1) of row r+1
+            f2 X0[3], Y0[3], X1[3], Z1[3];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const Node<NC> ni = at(P1, k);
-                const bool own = ok_r && ((cm >> (k + 1)) & 1u);
-                const bool cE = (cm >> (k + 2)) & 1u, c2E = (cm >> (k + 3)) & 1u, cW = (cm >> k) & 1u;
-                const Node<NC> pE = k < 3 ? at(P1, k < 3 ? k + 1 : 0) : Ra1;
-                const Node<NC> p2E = k < 2 ? at(P1, k < 2 ? k + 2 : 0) : (k == 2 ? Ra1 : Rb1);
-                const Node<NC> pN = at(P2, k), p2N = at(P3, k);
-                const Node<NC> pNE = k < 3 ? at(P2, k < 3 ? k + 1 : 0) : Ra2;
-                const Node<NC> pNW = k > 0 ? at(P2, k > 0 ? k - 1 : 0) : L2;
-                const float3 fE = spring(h, 0.f, h, ks, mu, ni, pE, own && cE);
-                const float3 f2E = spring(h2, 0.f, h2, kb, mu, ni, p2E, own && c2E);
-                const float3 fN = spring(0.f, h, h, ks, mu, ni, pN, own && ok_r1);
-                const float3 f2N = spring(0.f, h2, h2, kb, mu, ni, p2N, own && ok_r2);
-                const float3 fNE = spring(h, h, hd, ksh, mu, ni, pNE, own && ok_r1 && cE);
-                const float3 fNW = spring(-h, h, hd, ksh, mu, ni, pNW, own && ok_r1 && cW);
-                add3(A1, k, make_float3(fE.x + f2E.x + fN.x + f2N.x + fNE.x + fNW.x,
-                                        fE.y + f2E.y + fN.y + f2N.y + fNE.y + fNW.y,
-                                        fE.z + f2E.z + fN.z + f2N.z + fNE.z + fNW.z));
-                sub3(A2, k, fN);
-                sub3(A3, k, f2N);
-                if (k < 3) sub3(A1, k < 3 ? k + 1 : 0, fE);
-                else sendA_r = make_float3(sendA_r.x + fE.x, sendA_r.y + fE.y, sendA_r.z + fE.z);
-                if (k < 2) sub3(A1, k < 2 ? k + 2 : 0, f2E);
-                else if (k == 2) sendA_r = make_float3(sendA_r.x + f2E.x, sendA_r.y + f2E.y, sendA_r.z + f2E.z);
-                else sendB_r = f2E;
-                if (k < 3) sub3(A2, k < 3 ? k + 1 : 0, fNE);
-                else sendA_r1 = fNE;
-                if (k > 0) sub3(A2, k > 0 ? k - 1 : 0, fNW);
-                else sendD_r1 = fNW;
+            for (int c = 0; c < 3; ++c) {
+                X0[c] = make_float2(P0.A[c].y, shdn(P0.A[c].x));
+                Y0[c] = make_float2(P0.B[c].y, shdn(P0.B[c].x));
+                X1[c] = make_float2(P1.A[c].y, shdn(P1.A[c].x));
+                Z1[c] = make_float2(shup(P1.B[c].y), P1.B[c].x);
             }
-            sub3(A1, 0, shfl3_up(sendA_r));
-            sub3(A1, 1, shfl3_up(sendB_r));
-            sub3(A2, 0, shfl3_up(sendA_r1));
-            sub3(A2, 3, shfl3_down(sendD_r1));
+            f2 d[3], s;
+            float sR0r[3] = {0.f, 0.f, 0.f}, sR1r[3] = {0.f, 0.f, 0.f};
+            float sR0r1[3] = {0.f, 0.f, 0.f}, sL3r1[3] = {0.f, 0.f, 0.f};
 
-            // pressure (Eq. 3) of row r+1, whose 4 cardinal neighbours are in
-            // rows r .. r+2 of the window, goes into its accumulator
-            if (D.p_quarter != 0.f && ok_r1) {
-                const float pq = D.p_quarter;
+            // ---- springs of the A pair (c0, c2)
+            s = spring2<1, 0>(P0.A, P0.B, h, h2, nh, Ls, Ls2, ks, ok_r && eA0, ok_r && eA1, d);      // E -> (c1, c3)
+            acc2(F0.A, s, d);
+            acc2(F0.B, mul2(s, F2(-1.f)), d);
+            s = spring2<2, 0>(P0.A, X0, h, h2, nh, Lb, Lb2, kb, ok_r && tA0, ok_r && tA1, d);        // 2E -> (c2, c4)
+            acc2(F0.A, s, d);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const Node<NC> ni = at(P2, k);
-                    const Node<NC> nE = k < 3 ? at(P2, k < 3 ? k + 1 : 0) : Ra2;
-                    const Node<NC> nW = k > 0 ? at(P2, k > 0 ? k - 1 : 0) : L2;
-                    const Node<NC> nN = at(P3, k), nS = at(P1, k);
-                    const bool bE = (cm >> (k + 2)) & 1u, bW = (cm >> k) & 1u;
-                    const float3 dE = make_float3(h + nE.c[0] - ni.c[0], nE.c[1] - ni.c[1], nE.c[2] - ni.c[2]);
-                    const float3 dW = make_float3(-h + nW.c[0] - ni.c[0], nW.c[1] - ni.c[1], nW.c[2] - ni.c[2]);
-                    const float3 dN = make_float3(nN.c[0] - ni.c[0], h + nN.c[1] - ni.c[1], nN.c[2] - ni.c[2]);
-                    const float3 dS = make_float3(nS.c[0] - ni.c[0], -h + nS.c[1] - ni.c[1], nS.c[2] - ni.c[2]);
-                    float3 T = make_float3(0.f, 0.f, 0.f);
-                    T = fma3((bE && ok_r2) ? 1.f : 0.f, cross3(dE, dN), T);
-                    T = fma3((ok_r2 && bW) ? 1.f : 0.f, cross3(dN, dW), T);
-                    T = fma3((bW && ok_r) ? 1.f : 0.f, cross3(dW, dS), T);
-                    T = fma3((ok_r && bE) ? 1.f : 0.f, cross3(dS, dE), T);
-                    add3(A2, k, make_float3(pq * T.x, pq * T.y, pq * T.z));
+            for (int c = 0; c < 3; ++c) {
+                const f2 f = mul2(s, d[c]);
+                F0.A[c].y -= f.x;
+                sR0r[c] += f.y;
+            }
+            s = spring2<0, 1>(P0.A, P1.A, h, h2, nh, Ls, Ls2, ks, okN && oA0, okN && oA1, d);        // N
+            acc2(F0.A, s, d);
+            acc2(F1.A, mul2(s, F2(-1.f)), d);
+            s = spring2<0, 2>(P0.A, P2.A, h, h2, nh, Lb, Lb2, kb, ok2N && oA0, ok2N && oA1, d);      // 2N
+            acc2(F0.A, s, d);
+            acc2(Fq.A, mul2(s, F2(-1.f)), d);
+            s = spring2<1, 1>(P0.A, P1.B, h, h2, nh, Ld, Ld2, ksh, okN && eA0, okN && eA1, d);       // NE -> (c1, c3)
+            acc2(F0.A, s, d);
+            acc2(F1.B, mul2(s, F2(-1.f)), d);
+            s = spring2<-1, 1>(P0.A, Z1, h, h2, nh, Ld, Ld2, ksh, okN && wA0, okN && wA1, d);        // NW -> (c-1, c1)
+            acc2(F0.A, s, d);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 f = mul2(s, d[c]);
+                sL3r1[c] += f.x;
+                F1.B[c].x -= f.y;
+            }
+            // ---- springs of the B pair (c1, c3)
+            s = spring2<1, 0>(P0.B, X0, h, h2, nh, Ls, Ls2, ks, ok_r && eB0, ok_r && eB1, d);        // E -> (c2, c4)
+            acc2(F0.B, s, d);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 f = mul2(s, d[c]);
+                F0.A[c].y -= f.x;
+                sR0r[c] += f.y;
+            }
+            s = spring2<2, 0>(P0.B, Y0, h, h2, nh, Lb, Lb2, kb, ok_r && tB0, ok_r && tB1, d);        // 2E -> (c3, c5)
+            acc2(F0.B, s, d);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 f = mul2(s, d[c]);
+                F0.B[c].y -= f.x;
+                sR1r[c] += f.y;
+            }
+            s = spring2<0, 1>(P0.B, P1.B, h, h2, nh, Ls, Ls2, ks, okN && oB0, okN && oB1, d);        // N
+            acc2(F0.B, s, d);
+            acc2(F1.B, mul2(s, F2(-1.f)), d);
+            s = spring2<0, 2>(P0.B, P2.B, h, h2, nh, Lb, Lb2, kb, ok2N && oB0, ok2N && oB1, d);      // 2N
+            acc2(F0.B, s, d);
+            acc2(Fq.B, mul2(s, F2(-1.f)), d);
+            s = spring2<1, 1>(P0.B, X1, h, h2, nh, Ld, Ld2, ksh, okN && eB0, okN && eB1, d);         // NE -> (c2, c4)
+            acc2(F0.B, s, d);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const f2 f = mul2(s, d[c]);
+                F1.A[c].y -= f.x;
+                sR0r1[c] += f.y;
+            }
+            s = spring2<-1, 1>(P0.B, P1.A, h, h2, nh, Ld, Ld2, ksh, okN && wB0, okN && wB1, d);      // NW -> (c0, c2)
+            acc2(F0.B, s, d);
+            acc2(F1.A, mul2(s, F2(-1.f)), d);
+
+            // ---- reactions that cross to the neighbour lanes
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F0.A[c].x -= shup(sR0r[c]);
+                F0.B[c].x -= shup(sR1r[c]);
+                F1.A[c].x -= shup(sR0r1[c]);
+                F1.B[c].y -= shdn(sL3r1[c]);
+            }
+
+            // ---- pressure (Eq. 3) of row r+1, whose 4 cardinal neighbours lie
+            // in rows r .. r+2.  With d'_n = (neighbour n exists)(x_n - x_i),
+            // the sum over the ordered pairs of d'_E x d'_N + d'_N x d'_W +
+            // d'_W x d'_S + d'_S x d'_E equals (d'_E - d'_W) x (d'_N - d'_S).
+            if (pq != 0.f && ok_r1) {
+                const f2 bN = F2(ok_r2 ? 1.f : 0.f), bSn = F2(ok_r ? -1.f : 0.f);
+                const f2 hy = mul2(sub2(bN, bSn), h);
+                const f2 pq2 = F2(pq);
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const f2* ui = half == 0 ? P1.A : P1.B;
+                    const f2* uE = half == 0 ? P1.B : X1;
+                    const f2* uW = half == 0 ? Z1 : P1.A;
+                    const f2* uN = half == 0 ? P2.A : P2.B;
+                    const f2* uS = half == 0 ? P0.A : P0.B;
+                    const f2 mE = half == 0 ? mEA : mEB, mW = half == 0 ? mWA : mWB;
+                    const f2 hx = half == 0 ? hxA : hxB;
+                    const f2 ex = fma2(mE, sub2(uE[0], ui[0]), fma2(mW, sub2(uW[0], ui[0]), hx));
+                    const f2 ey = fma2(mE, sub2(uE[1], ui[1]), mul2(mW, sub2(uW[1], ui[1])));
+                    const f2 ez = fma2(mE, sub2(uE[2], ui[2]), mul2(mW, sub2(uW[2], ui[2])));
+                    const f2 nx = fma2(bN, sub2(uN[0], ui[0]), mul2(bSn, sub2(uS[0], ui[0])));
+                    const f2 ny = fma2(bN, sub2(uN[1], ui[1]), fma2(bSn, sub2(uS[1], ui[1]), hy));
+                    const f2 nz = fma2(bN, sub2(uN[2], ui[2]), mul2(bSn, sub2(uS[2], ui[2])));
+                    f2* Fh = half == 0 ? F1.A : F1.B;
+                    Fh[0] = fma2(pq2, sub2(mul2(ey, nz), mul2(ez, ny)), Fh[0]);
+                    Fh[1] = fma2(pq2, sub2(mul2(ez, nx), mul2(ex, nz)), Fh[1]);
+                    Fh[2] = fma2(pq2, sub2(mul2(ex, ny), mul2(ey, nx)), Fh[2]);
                 }
             }
 
-            // row r is complete: gravity and drag, update, store
-            if (r >= wu.r0 && ok_r && out_lane && ((cm >> 1) & 1u)) {
-                const ClothDesc& Dd = D;
-                float vx[4], vy[4], vz[4];
+            // ---- row r is complete: gravity and drag (Eq. 4), update (Eq. 5)
+            if (r >= wu.r0 && ok_r && out_lane && oA0) {
+                const f2 ndrag = F2(-D.drag);
+                const f2 mg[3] = {F2(D.m * D.gx), F2(D.m * D.gy), F2(D.m * D.gz)};
+                Row2 f;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if constexpr (DAMP) { vx[k] = P1.c[3][k]; vy[k] = P1.c[4][k]; vz[k] = P1.c[5][k]; }
-                    else { vx[k] = VC.c[0][k]; vy[k] = VC.c[1][k]; vz[k] = VC.c[2][k]; }
-                }
-                float fx[4], fy[4], fz[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    fx[k] = A1[0][k] + fmaf(-Dd.drag, vx[k], Dd.m * Dd.gx);
-                    fy[k] = A1[1][k] + fmaf(-Dd.drag, vy[k], Dd.m * Dd.gy);
-                    fz[k] = A1[2][k] + fmaf(-Dd.drag, vz[k], Dd.m * Dd.gz);
+                for (int c = 0; c < 3; ++c) {
+                    f.A[c] = add2(F0.A[c], fma2(ndrag, V0.A[c], mg[c]));
+                    f.B[c] = add2(F0.B[c], fma2(ndrag, V0.B[c], mg[c]));
                 }
                 if constexpr (FORCES) {
+                    float* o = a.force_out + (D.abi_off + (int64_t)r * cols + c4) * 3;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int col = c4 + k;
-                        if (col < cols) {
-                            float* o = a.force_out + (Dd.abi_off + (int64_t)r * cols + col) * 3;
-                            o[0] = fx[k]; o[1] = fy[k]; o[2] = fz[k];
-                        }
+                    for (int c = 0; c < 3; ++c) {
+                        o[0 * 3 + c] = f.A[c].x;
+                        if (c4 + 1 < cols) o[1 * 3 + c] = f.B[c].x;
+                        if (c4 + 2 < cols) o[2 * 3 + c] = f.A[c].y;
+                        if (c4 + 3 < cols) o[3 * 3 + c] = f.B[c].y;
                     }
                 } else {
-                    const uint32_t pw = __ldg(a.pinmask + Dd.pin_off + (int64_t)r * Dd.pin_wpr + (c4 >> 5));
-                    const unsigned pbits = (pw >> (c4 & 31)) & 0xfu;
-                    const float dt = Dd.dt, dtm = Dd.dt * Dd.inv_m;
-                    float un[3][4], vn[3][4];
-                    bool finite = true;
+                    const f2 dt = F2(D.dt), dtm = F2(D.dt * D.inv_m);
+                    Row2 un, vn;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const bool pinned = (pbits >> k) & 1u;
-                        float nvx = fmaf(dtm, fx[k], vx[k]), nvy = fmaf(dtm, fy[k], vy[k]), nvz = fmaf(dtm, fz[k], vz[k]);
-                        if (pinned) nvx = nvy = nvz = 0.f;
-                        float nux = fmaf(dt, nvx, P1.c[0][k]), nuy = fmaf(dt, nvy, P1.c[1][k]), nuz = fmaf(dt, nvz, P1.c[2][k]);
-                        if (Dd.sph_on) {
-                            // position relative to the centre: (X - c) + u
-                            const float rx = fmaf((float)(c4 + k), h, -Dd.sph_cx) + nux;
-                            const float ry = fmaf((float)r, h, -Dd.sph_cy) + nuy;
-                            const float rz = nuz - Dd.sph_cz;
+                    for (int c = 0; c < 3; ++c) {
+                        vn.A[c] = fma2(dtm, f.A[c], V0.A[c]);
+                        vn.B[c] = fma2(dtm, f.B[c], V0.B[c]);
+                    }
+                    const uint32_t pw = __ldg(a.pinmask + D.pin_off + (int64_t)r * D.pin_wpr + (c4 >> 5));
+                    const unsigned pb = (pw >> (c4 & 31)) & 0xfu;
+                    if (pb) {   // Dirichlet nodes: C holds their velocity at zero
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if (pb & 1u) vn.A[c].x = 0.f;
+                            if (pb & 4u) vn.A[c].y = 0.f;
+                            if (pb & 2u) vn.B[c].x = 0.f;
+                            if (pb & 8u) vn.B[c].y = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        un.A[c] = fma2(dt, vn.A[c], P0.A[c]);
+                        un.B[c] = fma2(dt, vn.B[c], P0.B[c]);
+                    }
+                    if (D.sph_on) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            // column c4 + k sits in pair A (k even) or B (k odd), half k / 2
+                            f2* U = (k & 1) ? un.B : un.A;
+                            f2* Vv = (k & 1) ? vn.B : vn.A;
+                            float& ux = (k >> 1) ? U[0].y : U[0].x;
+                            float& uy = (k >> 1) ? U[1].y : U[1].x;
+                            float& uz = (k >> 1) ? U[2].y : U[2].x;
+                            const float rx = fmaf((float)(c4 + k), hs, -D.sph_cx) + ux;
+                            const float ry = fmaf((float)r, hs, -D.sph_cy) + uy;
+                            const float rz = uz - D.sph_cz;
                             const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                            if (dd < Dd.sph_r2 && dd > 0.f) {
-                                const float s = Dd.sph_r * rsqrtf(dd);
-                                nux = fmaf(s, rx, nux - rx);
-                                nuy = fmaf(s, ry, nuy - ry);
-                                nuz = fmaf(s, rz, nuz - rz);
-                                nvx = nvy = nvz = 0.f;
+                            if (dd < D.sph_r2 && dd > 0.f) {
+                                const float sc = D.sph_r * rsqrtf(dd);
+                                ux = fmaf(sc, rx, ux - rx);
+                                uy = fmaf(sc, ry, uy - ry);
+                                uz = fmaf(sc, rz, uz - rz);
+                                if (k >> 1) { Vv[0].y = 0.f; Vv[1].y = 0.f; Vv[2].y = 0.f; }
+                                else { Vv[0].x = 0.f; Vv[1].x = 0.f; Vv[2].x = 0.f; }
                             }
                         }
-                        un[0][k] = nux; un[1][k] = nuy; un[2][k] = nuz;
-                        vn[0][k] = nvx; vn[1][k] = nvy; vn[2][k] = nvz;
-                        if ((cm >> (k + 1)) & 1u)
-                            finite = finite && isfinite(nux + nuy + nuz + nvx + nvy + nvz);
                     }
-                    if (!finite) atomicOr(a.status, 1);
+                    // non-finite check over the 4 nodes (columns beyond the
+                    // grid hold finite values: their springs are all zero)
+                    f2 chk = add2(add2(un.A[0], un.A[1]), add2(un.A[2], vn.A[0]));
+                    chk = add2(chk, add2(add2(vn.A[1], vn.A[2]), add2(un.B[0], un.B[1])));
+                    chk = add2(chk, add2(add2(un.B[2], vn.B[0]), add2(vn.B[1], vn.B[2])));
+                    if (!isfinite(chk.x + chk.y)) atomicOr(a.status, 1);
                     float* dst = a.dst + lane_off + (int64_t)r * pitch;
                     if (c4 + 3 < cols) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            *reinterpret_cast<float4*>(dst + c * stride) = make_float4(un[c][0], un[c][1], un[c][2], un[c][3]);
-                            *reinterpret_cast<float4*>(dst + (c + 3) * stride) = make_float4(vn[c][0], vn[c][1], vn[c][2], vn[c][3]);
+                            *reinterpret_cast<float4*>(dst + c * stride) =
+                                make_float4(un.A[c].x, un.A[c].y, un.B[c].x, un.B[c].y);
+                            *reinterpret_cast<float4*>(dst + (c + 3) * stride) =
+                                make_float4(vn.A[c].x, vn.A[c].y, vn.B[c].x, vn.B[c].y);
                         }
                     } else {
+                        // ragged strip end: memory slots c0 -> 0, c2 -> 1, c1 -> 2, c3 -> 3
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if (c4 + k < cols) {
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) {
-                                    dst[c * stride + k] = un[c][k];
-                                    dst[(c + 3) * stride + k] = vn[c][k];
-                                }
-                            }
+                        for (int c = 0; c < 3; ++c) {
+                            dst[c * stride + 0] = un.A[c].x;
+                            dst[(c + 3) * stride + 0] = vn.A[c].x;
+                            if (c4 + 1 < cols) { dst[c * stride + 2] = un.B[c].x; dst[(c + 3) * stride + 2] = vn.B[c].x; }
+                            if (c4 + 2 < cols) { dst[c * stride + 1] = un.A[c].y; dst[(c + 3) * stride + 1] = vn.A[c].y; }
+                        }
                     }
                 }
             }
 
             // slide the window down one row
-            P1 = P2; P2 = P3; P3 = P4;
-            if constexpr (!DAMP) VC = VN;
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { A1[c][k] = A2[c][k]; A2[c][k] = A3[c][k]; A3[c][k] = 0.f; }
+            P0 = P1; P1 = P2; P2 = PN;
+            F0 = F1; F1 = Fq; zero(Fq);
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_plain_step(const StepArgs& a, bool damp, bool forces_only, int grid, int block, cudaStream_t s)
+cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s)
 {
-    if (damp) {
-        if (forces_only) plain_step_kernel<true, true><<<grid, block, 0, s>>>(a);
-        else plain_step_kernel<true, false><<<grid, block, 0, s>>>(a);
-    } else {
-        if (forces_only) plain_step_kernel<false, true><<<grid, block, 0, s>>>(a);
-        else plain_step_kernel<false, false><<<grid, block, 0, s>>>(a);
-    }
+    if (forces_only) plain_step_kernel<true><<<grid, block, 0, s>>>(a);
+    else plain_step_kernel<false><<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

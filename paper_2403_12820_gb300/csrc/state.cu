@@ -18,7 +18,7 @@ __global__ void set_state_kernel(const ClothDesc* __restrict__ desc, const float
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / D.cols), c = (int)(i % D.cols);
         const int64_t src = (D.abi_off + i) * 3;
-        const int64_t dst = D.plane_off + (int64_t)r * D.pitch + c;
+        const int64_t dst = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
         const double X = (double)c * (double)D.h, Y = (double)r * (double)D.h;
         state[dst] = (float)((double)x[src + 0] - X);
         state[dst + D.plane_stride] = (float)((double)x[src + 1] - Y);
@@ -35,7 +35,7 @@ __global__ void get_state_kernel(const ClothDesc* __restrict__ desc, const float
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / D.cols), c = (int)(i % D.cols);
         const int64_t dst = (D.abi_off + i) * 3;
-        const int64_t src = D.plane_off + (int64_t)r * D.pitch + c;
+        const int64_t src = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
         if (x) {
             x[dst + 0] = (float)((double)c * (double)D.h + (double)state[src]);
             x[dst + 1] = (float)((double)r * (double)D.h + (double)state[src + D.plane_stride]);
