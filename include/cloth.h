@@ -245,6 +245,25 @@ int net_forward(cloth_net* net, const float* d_z, float* d_a, int32_t N, int32_t
 int net_backward(cloth_net* net, const float* d_z, float* d_saved, const float* d_grad_a, float* d_grad_z,
                  float* d_grad_w, int32_t N, int32_t H, int32_t W, void* stream);
 
+/* net_forward_static — the FP32 cell forward for callers that cannot
+ * allocate device memory on demand (for example a plug-in inside a host
+ * application that reserves the GPU memory budget at start-up, or a
+ * real-time frame loop where an allocation could stall a frame).  The paper
+ * has no counterpart: this is a deployment variant of net_forward.
+ *  d_blob: DEVICE weight blob of CLOTH_NET_BLOB floats (read only; no
+ *    network handle needed).  d_z [N][6][H][W] in, d_a [N][3][H][W] out, as
+ *    for net_forward.
+ * The trunk's layer outputs live in one static device array inside the
+ * library (CLOTH_NET_STATIC_MAX_NODES nodes, 8 MiB, held by every GPU that
+ * loads the library until exit); nothing is allocated.  Returns
+ * CLOTH_EINVAL when N * H * W exceeds CLOTH_NET_STATIC_MAX_NODES.  The first
+ * call on a device looks up the array's device address and sets kernel
+ * attributes; make that first call before any stream capture.  All calls on
+ * a device share the array: calls whose work overlaps on the GPU race. */
+#define CLOTH_NET_STATIC_MAX_NODES 16384
+int net_forward_static(const float* d_blob, const float* d_z, float* d_a, int32_t N, int32_t H, int32_t W,
+                       void* stream);
+
 /* Release the network's host resources. */
 void net_destroy(cloth_net* net);
 

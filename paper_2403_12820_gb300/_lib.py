@@ -66,6 +66,7 @@ SIGNATURES = {
     "net_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32,
                                c_void_p]),
     "net_destroy": (None, [c_void_p]),
+    "net_forward_static": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
     "cloth_net_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
     "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_info": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
