@@ -46,6 +46,8 @@ def parse_args(argv=None):
     p.add_argument("--graph-chunk", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cnn", action="store_true")
+    p.add_argument("--cnn-steps", type=int, default=200)
     return p.parse_args(argv)
 
 
@@ -317,13 +319,83 @@ def run_plain(args, rank, world, local):
                       "d2h_bytes_per_step": hout.numel() * 4 / per_call,
                       "steps_per_call": per_call, "calls": calls}
 
+    if not args.no_cnn:
+        out["cnn"] = run_cnn(args, dev)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        rate, wall = oracle_plain_rate(cfg, 2, cores)
+        rate, wall = oracle_plain_rate(cfg, 24, cores)
         out["cpu_baseline"] = {"value": rate, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-                               "sample": f"all 64 cloths x 2 steps, FP64 oracle, {cores} processes ({wall:.1f} s)"}
+                               "sample": f"all 64 cloths x 24 steps (143M node-steps), FP64 oracle, "
+                                         f"{cores} processes, {wall:.1f} s wall"}
     cb.close()
     return out
+
+
+CNN_FLOP_PER_NODE = 44480     # 22,240 MAC of the cell per node
+
+
+def cnn_blob(h: float):
+    from paper_2403_12820_gb300 import workloads as wl
+    return wl.kaiming_blob(2003, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
+
+
+def run_cnn(args, dev):
+    """Network step (Fig. 2) on 32 cloths of 128 x 128: node-steps/s, the
+    ratio to the plain step on the same cloths, and the mean node-position
+    error relative to cloth width after 100 steps (Table 2's error)."""
+    import numpy as np
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import FP32, Net
+
+    cfg = wl.cnn_batch()
+    h = cfg["specs"][0]["h"]
+    net = Net(cnn_blob(h), FP32, device=dev)
+    x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
+    cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cp = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    nodes = cn.total_nodes
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    cn.set_state(x0, v0)
+    cn.step_net(net, 3)
+    t_net = timed(lambda k: cn.step_net(net, k), args.cnn_steps)
+    cp.set_state(x0, v0)
+    cp.rollout(10, graph_chunk=10)
+    t_plain = timed(lambda k: cp.rollout(k, graph_chunk=100), 10 * args.cnn_steps)
+    net_rate = nodes * args.cnn_steps / t_net
+    plain_rate = nodes * 10 * args.cnn_steps / t_plain
+    # error after 100 steps from the same start (Table 2 reading: mean |dx| / width)
+    cn.set_state(x0, v0); cn.step_net(net, 100)
+    cp.set_state(x0, v0); cp.step(100)
+    xn, _ = cn.get_state()
+    xp, _ = cp.get_state()
+    w = (cfg["specs"][0]["cols"] - 1) * h
+    err = (xn - xp).norm(dim=1)
+    disp = (xp - x0).norm(dim=1).mean().item()
+    _, bf16_tflops, _ = peaks()
+    return {
+        "workload": "cnn_batch: 32 cloths of 128 x 128 (524,288 nodes), Kaiming weights (seed 2003), FP32 cell",
+        "precision": "f32",
+        "value": net_rate, "unit": "node-steps/s", "steps": args.cnn_steps,
+        "plain_same_cloths": plain_rate, "ratio_to_plain": net_rate / plain_rate,
+        "error_100_steps_rel_width": err.mean().item() / w,
+        "error_100_steps_rel_displacement": err.mean().item() / max(disp, 1e-30),
+        "achieved_tflops": CNN_FLOP_PER_NODE * net_rate / 1e12,
+        "gpu_launches_per_step": 4,
+    }
 
 
 def main(argv=None):
