@@ -207,6 +207,36 @@ StepWs step_ws(const cloth_ctx* c)
     return w;
 }
 
+// Tiles (cloth, y0, x0, -) of the fused tensor-core network step.
+std::vector<int4> tc_tiles(const cloth_ctx* c)
+{
+    std::vector<int4> t;
+    const int R = net_tc_tile_rows(), WO = net_tc_tile_cols();
+    for (int b = 0; b < c->B; ++b)
+        for (int y0 = 0; y0 < c->grids[b].rows; y0 += R)
+            for (int x0 = 0; x0 < c->grids[b].cols; x0 += WO) t.push_back(make_int4(b, y0, x0, 0));
+    return t;
+}
+
+int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, cudaStream_t s)
+{
+    const std::vector<int4> tiles = tc_tiles(c);
+    if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
+    int4* d_tiles = static_cast<int4*>(d_work);
+    if (c->lists_written != d_work) {
+        CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        c->lists_written = d_work;
+    }
+    const int grid = std::min<int>((int)tiles.size(), c->sm_count);
+    for (int st = 0; st < steps; ++st) {
+        CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), c->d_state(c->cur),
+                              c->d_state(c->cur ^ 1), c->d_pins(), c->d_status(), grid, s));
+        c->cur ^= 1;
+    }
+    return CLOTH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -214,6 +244,10 @@ extern "C" {
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
+    if (precision == CLOTH_NET_BF16) {
+        *bytes = align_up(sizeof(int4) * tc_tiles(c).size(), kAlign);
+        return CLOTH_OK;
+    }
     make_groups(const_cast<cloth_ctx*>(c));
     *bytes = step_ws(c).total;
     return CLOTH_OK;
@@ -223,7 +257,7 @@ int cloth_step_net(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wo
 {
     if (!c || !net || !d_work || steps < 0) return CLOTH_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
-    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
+    if (net->precision == CLOTH_NET_BF16) return step_net_bf16(c, net, steps, d_work, bytes, static_cast<cudaStream_t>(stream));
     make_groups(c);
     const StepWs w = step_ws(c);
     if (bytes < w.total) return CLOTH_ENOMEM;

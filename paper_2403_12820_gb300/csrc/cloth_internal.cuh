@@ -15,6 +15,8 @@ constexpr int kStrip = 120;
 // Plane pitch (floats per row) is a multiple of this, so every float4 of a
 // lane is 16-byte aligned and lies wholly inside or outside [0, pitch).
 constexpr int kPitchAlign = 4;
+// Device status word bits (include/cloth.h: CLOTH_STATUS_*).
+constexpr int kStatusNonfinite = 1, kStatusTimeout = 2;
 
 // Per-cloth descriptor in device memory (built on the host at create).
 struct __align__(16) ClothDesc {

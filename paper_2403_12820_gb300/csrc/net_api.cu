@@ -35,6 +35,7 @@ int ensure_init()
     if (dev < 0 || dev >= 64) return CLOTH_EUNSUPPORTED;
     if (!done[dev]) {
         NCK(net_simt_init());
+        NCK(net_tc_init());
         done[dev] = true;
     }
     return CLOTH_OK;
@@ -77,7 +78,12 @@ int net_create(cloth_net** out, int32_t precision, const float* h_blob, void* d_
     n->ws = static_cast<char*>(d_workspace);
     n->L = L;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(n->d_w(), h_blob, sizeof(float) * kBlob, cudaMemcpyHostToDevice, s);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n->d_w(), h_blob, sizeof(float) * kBlob, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->d_status(), 0, 64, s);
+    if (e == cudaSuccess) e = launch_pack_bf16(n->d_w(), n->d_pack(), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete n;
@@ -92,6 +98,7 @@ int net_set_weights(cloth_net* n, const float* d_blob, void* stream)
     if (!n || !d_blob) return CLOTH_EINVAL;
     NCK(cudaMemcpyAsync(n->d_w(), d_blob, sizeof(float) * kBlob, cudaMemcpyDeviceToDevice,
                         static_cast<cudaStream_t>(stream)));
+    NCK(launch_pack_bf16(n->d_w(), n->d_pack(), static_cast<cudaStream_t>(stream)));
     return CLOTH_OK;
 }
 
@@ -115,7 +122,11 @@ int net_forward(cloth_net* n, const float* d_z, float* d_a, int32_t N, int32_t H
 {
     if (!n || !d_z || !d_a || !dims_ok(N, H, W)) return CLOTH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (n->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
+    if (n->precision == CLOTH_NET_BF16) {
+        if (d_saved) return CLOTH_EINVAL;   // the fused tensor-core kernel keeps nothing
+        NCK(launch_net_tc_forward(n->d_pack(), n->d_w(), d_z, d_a, N, H, W, n->d_status(), n->sm_count, s));
+        return CLOTH_OK;
+    }
     if (!d_saved) return CLOTH_EINVAL;   // the FP32 path keeps its layer outputs there
     const int64_t NHW = (int64_t)N * H * W;
     NetFwdArgs f{};

@@ -65,11 +65,22 @@ cudaError_t launch_net_update(const ClothDesc* desc, const int32_t* cloth_of, in
                               const float* src, float* dst, const uint32_t* pinmask, int32_t* status, cudaStream_t s);
 cudaError_t net_simt_init();
 int net_last_cuda_error();
+// Tensor-core (tcgen05, BF16) fused cell / network step (net_tc.cu).
+cudaError_t net_tc_init();
+int net_tc_pack_bytes();
+int net_tc_tile_rows();
+int net_tc_tile_cols();
+cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s);
+cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDesc* desc, const int4* tiles, int n_tiles,
+                               const float* src, float* dst, const uint32_t* pinmask, int32_t* status, int grid,
+                               cudaStream_t s);
+cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
+                                  int32_t* status, int grid, cudaStream_t s);
 
 
 // Host side of a network handle (include/cloth.h: cloth_net).
 struct NetLayout {
-    size_t blob, part, total;
+    size_t blob, part, pack, status, total;
 };
 inline NetLayout net_layout()
 {
@@ -78,6 +89,8 @@ inline NetLayout net_layout()
     size_t off = 0;
     L.blob = off; off = al(off + sizeof(float) * kBlob);
     L.part = off; off = al(off + sizeof(float) * (size_t)kWgradBlocks * kParams);
+    L.pack = off; off = al(off + 65536);          // packed BF16 tensor-core operands
+    L.status = off; off = al(off + 64);
     L.total = off;
     return L;
 }
@@ -90,4 +103,7 @@ struct cloth_net {
     cloth::NetLayout L{};
     float* d_w() const { return reinterpret_cast<float*>(ws + L.blob); }
     float* d_part() const { return reinterpret_cast<float*>(ws + L.part); }
+    void* d_pack() const { return ws + L.pack; }
+    int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
+    int sm_count = 0;
 };
