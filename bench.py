@@ -341,23 +341,22 @@ def cnn_blob(h: float):
 
 
 def run_cnn(args, dev):
-    """Network step (Fig. 2) on 32 cloths of 128 x 128: node-steps/s, the
-    ratio to the plain step on the same cloths, and the mean node-position
-    error relative to cloth width after 100 steps (Table 2's error)."""
-    import numpy as np
+    """Network step (Fig. 2) on 32 cloths of 128 x 128: node-steps/s of the
+    BF16 tensor-core step and of the FP32 CUDA-core step, the ratio to the
+    plain step on the same cloths, and the mean node-position error relative
+    to cloth width after 100 steps (Table 2's error)."""
     import torch
 
     from paper_2403_12820_gb300 import workloads as wl
     from paper_2403_12820_gb300.cloth import ClothBatch, pack
-    from paper_2403_12820_gb300.net import FP32, Net
+    from paper_2403_12820_gb300.net import BF16, FP32, Net
 
     cfg = wl.cnn_batch()
     h = cfg["specs"][0]["h"]
-    net = Net(cnn_blob(h), FP32, device=dev)
+    blob = cnn_blob(h)
     x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
-    cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cp = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
-    nodes = cn.total_nodes
+    nodes = cp.total_nodes
     stream = torch.cuda.current_stream()
 
     def timed(fn, steps):
@@ -369,33 +368,42 @@ def run_cnn(args, dev):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
-    cn.set_state(x0, v0)
-    cn.step_net(net, 3)
-    t_net = timed(lambda k: cn.step_net(net, k), args.cnn_steps)
     cp.set_state(x0, v0)
     cp.rollout(10, graph_chunk=10)
     t_plain = timed(lambda k: cp.rollout(k, graph_chunk=100), 10 * args.cnn_steps)
-    net_rate = nodes * args.cnn_steps / t_net
     plain_rate = nodes * 10 * args.cnn_steps / t_plain
-    # error after 100 steps from the same start (Table 2 reading: mean |dx| / width)
-    cn.set_state(x0, v0); cn.step_net(net, 100)
-    cp.set_state(x0, v0); cp.step(100)
-    xn, _ = cn.get_state()
+    cp.set_state(x0, v0)
+    cp.step(100)
     xp, _ = cp.get_state()
     w = (cfg["specs"][0]["cols"] - 1) * h
-    err = (xn - xp).norm(dim=1)
     disp = (xp - x0).norm(dim=1).mean().item()
-    _, bf16_tflops, _ = peaks()
-    return {
-        "workload": "cnn_batch: 32 cloths of 128 x 128 (524,288 nodes), Kaiming weights (seed 2003), FP32 cell",
-        "precision": "f32",
-        "value": net_rate, "unit": "node-steps/s", "steps": args.cnn_steps,
-        "plain_same_cloths": plain_rate, "ratio_to_plain": net_rate / plain_rate,
-        "error_100_steps_rel_width": err.mean().item() / w,
-        "error_100_steps_rel_displacement": err.mean().item() / max(disp, 1e-30),
-        "achieved_tflops": CNN_FLOP_PER_NODE * net_rate / 1e12,
-        "gpu_launches_per_step": 4,
-    }
+    _, bf16_peak, peak_kind = peaks()
+    out = {"workload": "cnn_batch: 32 cloths of 128 x 128 (524,288 nodes), Kaiming weights (seed 2003)",
+           "plain_same_cloths": plain_rate}
+    for name, prec, steps in (("bf16", BF16, args.cnn_steps), ("f32", FP32, max(1, args.cnn_steps // 10))):
+        net = Net(blob, prec, device=dev)
+        cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+        cn.set_state(x0, v0)
+        cn.step_net(net, 3)
+        t = timed(lambda k: cn.step_net(net, k), steps)
+        rate = nodes * steps / t
+        cn.set_state(x0, v0)
+        cn.step_net(net, 100)
+        xn, _ = cn.get_state()
+        err = (xn - xp).norm(dim=1).mean().item()
+        tflops = CNN_FLOP_PER_NODE * rate / 1e12
+        out[name] = {"value": rate, "unit": "node-steps/s", "steps": steps, "ms_per_step": t / steps * 1e3,
+                     "ratio_to_plain": rate / plain_rate, "error_100_steps_rel_width": err / w,
+                     "error_100_steps_rel_displacement": err / max(disp, 1e-30), "achieved_tflops": tflops,
+                     "gpu_launches_per_step": 1 if prec == BF16 else 4, "status_word": cn.status()}
+        if prec == BF16:
+            out[name]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                     "frac": tflops / bf16_peak, "peak_kind": f"{peak_kind} (cuBLAS bf16 burst)",
+                                     "algorithmic_flop_per_node": CNN_FLOP_PER_NODE}
+        cn.close()
+        net.close()
+    cp.close()
+    return out
 
 
 def main(argv=None):

@@ -41,7 +41,7 @@ constexpr int N2 = (R + 2) * PT;                // layer-2 positions (pitch PT)
 constexpr int C1 = N1 / 128;                    // layer-1 chunks
 constexpr int C2 = (N2 + 127) / 128;            // layer-2 chunks
 constexpr int N1BUF = (C2 * 128 + 2 * PT + 2 + 127) / 128 * 128;   // + rows read by shifted taps
-constexpr int NTH = 128;
+constexpr int NTH = 256;                         // 8 warps; warps w and w + 4 share TMEM lanes
 constexpr uint32_t kWaitLimit = 1u << 24;
 static_assert(N1 % 128 == 0, "layer-1 region must be whole chunks");
 static_assert(N1BUF >= N1, "layer-1 buffer");
@@ -60,10 +60,12 @@ constexpr int oIN = oA1 + 2 * 4 * 128 * 16;        // u, v [6][IH][IW] float
 constexpr int oQ = oIN + 6 * IH * IW * 4;          // q [N2][27] float
 constexpr int oND = oQ + N2 * 27 * 4;              // N + D [R * WO][3] float
 constexpr int oPar = oND + R * WO * 3 * 4;         // WN[96] WD[96] bL[3] outs[3] ins[6] (+pad)
-constexpr int oBar = oPar + 208 * 4;               // mbarrier, tensor-memory address, flags
-constexpr int kSmem = oBar + 16;
+constexpr int oDesc = oPar + 208 * 4;              // the tile's cloth descriptor
+constexpr int oBar = oDesc + (int)sizeof(ClothDesc);   // 3 mbarriers, tensor-memory address
+constexpr int kSmem = oBar + 32;
 static_assert(kSmem <= 232448, "shared memory");
-static_assert(oIN % 16 == 0 && oQ % 16 == 0 && oND % 16 == 0 && oPar % 16 == 0, "alignment");
+static_assert(oIN % 16 == 0 && oQ % 16 == 0 && oND % 16 == 0 && oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
+              "alignment");
 
 constexpr uint32_t kTmemCols = 256;
 
@@ -98,9 +100,11 @@ template <bool STEP>
 __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3;                 // TMEM lanes [32 quarter, +32) of this warp
+    const int half = warp >> 2;                   // warps 0-3 and 4-7 split the columns
     const uint32_t sbase = tc::smem_u32(sm);
-    const uint32_t bar = sbase + oBar;
+    const uint32_t bar1 = sbase + oBar, bar2[2] = {sbase + oBar + 8, sbase + oBar + 16};
     float* sIN = reinterpret_cast<float*>(sm + oIN);
     float* sQ = reinterpret_cast<float*>(sm + oQ);
     float* sND = reinterpret_cast<float*>(sm + oND);
@@ -109,9 +113,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     float* sBL = sWD + 96;
     float* sOut = sBL + 3;
     float* sIns = sOut + 3;
-    volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oBar + 8);
+    ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
+    volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oBar + 24);
 
-    // ---- one-time set-up: weights, barrier, tensor memory
+    // ---- one-time set-up: weights, barriers, tensor memory
     for (int e = tid; e < kPack / 16; e += NTH) reinterpret_cast<uint4*>(sm)[e] = A.wpack[e];
     for (int e = tid; e < 96; e += NTH) {
         sWN[e] = A.w[kOffWN + e];
@@ -130,55 +135,86 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         reinterpret_cast<uint4*>(sm + (buf ? oL1x : oL1p))[plane * N1BUF + row] = make_uint4(0, 0, 0, 0);
     }
     if (tid == 0) {
-        tc::mbar_init(bar, 1);
+        tc::mbar_init(bar1, 1);
+        tc::mbar_init(bar2[0], 1);
+        tc::mbar_init(bar2[1], 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(sbase + oBar + 8, kTmemCols);
+        tc::tmem_alloc(sbase + oBar + 24, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *sTmem;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t phase = 0;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    uint32_t ph1 = 0, ph2[2] = {0, 0};
     bool timed_out = false;
     const int n_tiles = STEP ? A.n_tiles : A.N * A.tiles_y * A.tiles_x;
+
+    // layer-2 MMAs of chunk c into TMEM columns [128 (c & 1), +96)
+    auto issue_layer2 = [&](int c2) {
+        tc::fence_after();
+        const uint32_t d = tmem + 128u * (uint32_t)(c2 & 1);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int row = c2 * 128 + (tap / 3) * PT + tap % 3;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool acc = tap > 0 || h > 0;
+                const uint64_t ap = tc::sdesc(sbase + oL1p + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
+                const uint64_t bp = tc::sdesc(sbase + oB2p + (tap * 4 + 2 * h) * 64 * 16, 64 * 16, 128);
+                tc::mma_bf16(d, ap, bp, tc::idesc_bf16(128, 64), acc);
+                const uint64_t ax = tc::sdesc(sbase + oL1x + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
+                const uint64_t bx = tc::sdesc(sbase + oB2x + (tap * 4 + 2 * h) * 32 * 16, 32 * 16, 128);
+                tc::mma_bf16(d + 64, ax, bx, tc::idesc_bf16(128, 32), acc);
+            }
+        }
+        tc::mma_commit(bar2[c2 & 1]);
+    };
 
     for (int tile = blockIdx.x; tile < n_tiles && !timed_out; tile += gridDim.x) {
         // ---- tile geometry
         int y0, x0, H, W, n = 0;
-        const ClothDesc* D = nullptr;
         if constexpr (STEP) {
             const int4 t = A.tiles[tile];
-            D = &A.desc[t.x];
-            y0 = t.y; x0 = t.z; H = D->rows; W = D->cols;
+            if (tid == 0) *sD = A.desc[t.x];
+            y0 = t.y; x0 = t.z;
+            __syncthreads();
+            H = sD->rows; W = sD->cols;
         } else {
             n = tile / (A.tiles_y * A.tiles_x);
             const int r = tile % (A.tiles_y * A.tiles_x);
             y0 = (r / A.tiles_x) * R; x0 = (r % A.tiles_x) * WO; H = A.H; W = A.W;
         }
         // ---- 1. input tile: u, v (raw) with a 3-node halo, zero outside the grid
-        for (int e = tid; e < 6 * IH * IW; e += NTH) {
-            const int ch = e / (IH * IW), rem = e % (IH * IW);
-            const int y = y0 - 3 + rem / IW, x = x0 - 3 + rem % IW;
-            float val = 0.f;
-            if (y >= 0 && y < H && x >= 0 && x < W) {
-                if constexpr (STEP)
-                    val = A.src[D->plane_off + ch * D->plane_stride + (int64_t)y * D->pitch + col_pos(x)];
-                else
-                    val = A.z[(((int64_t)n * 6 + ch) * H + y) * W + x];
+        {
+            int64_t cbase = 0, cstride = 0, rstride = 0;
+            const float* srcp;
+            if constexpr (STEP) {
+                srcp = A.src + sD->plane_off; cstride = sD->plane_stride; rstride = sD->pitch;
+            } else {
+                srcp = A.z + (int64_t)n * 6 * H * W; cstride = (int64_t)H * W; rstride = W;
             }
-            sIN[e] = val;
+            (void)cbase;
+#pragma unroll 4
+            for (int e = tid; e < 6 * IH * IW; e += NTH) {
+                const int ch = e / (IH * IW), rem = e % (IH * IW);
+                const int y = y0 - 3 + rem / IW, x = x0 - 3 + rem % IW;
+                float val = 0.f;
+                if (y >= 0 && y < H && x >= 0 && x < W)
+                    val = __ldg(srcp + ch * cstride + (int64_t)y * rstride + (STEP ? col_pos(x) : x));
+                sIN[e] = val;
+            }
         }
         __syncthreads();
 
         // ---- 2. layer 1 (Eq. 6), chunk by chunk
         for (int c1 = 0; c1 < C1 && !timed_out; ++c1) {
-            const int j1 = c1 * 128 + tid, ry1 = j1 / PT, rx1 = j1 % PT;
-#pragma unroll
-            for (int f = 0; f < 2; ++f)
+            {   // im2col: thread = (field, row)
+                const int row = tid & 127, f = tid >> 7;
+                const int j1 = c1 * 128 + row, ry1 = j1 / PT, rx1 = j1 % PT;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     float v[8];
@@ -193,8 +229,9 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                             v[e] = 0.f;
                         }
                     }
-                    reinterpret_cast<uint4*>(sm + oA1)[(f * 4 + p) * 128 + tid] = pack8(v);
+                    reinterpret_cast<uint4*>(sm + oA1)[(f * 4 + p) * 128 + row] = pack8(v);
                 }
+            }
             tc::fence_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -207,29 +244,27 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                         const uint64_t bd = tc::sdesc(sbase + oB1 + (f * 4 + 2 * h) * 32 * 16, 32 * 16, 128);
                         tc::mma_bf16(tmem + 32 * f, ad, bd, tc::idesc_bf16(128, 32), h > 0);
                     }
-                tc::mma_commit(bar);
+                tc::mma_commit(bar1);
             }
-            const bool done = tc::mbar_wait(bar, phase, kWaitLimit);
-            phase ^= 1u;
+            const bool done = tc::mbar_wait(bar1, ph1, kWaitLimit);
+            ph1 ^= 1u;
             if (__syncthreads_or(!done)) { timed_out = true; break; }
             tc::fence_after();
-            float r1[32], r2[32];
-            tc::tmem_ld32(lane_base + 0, r1);
-            tc::tmem_ld32(lane_base + 32, r2);
-            tc::tmem_wait_ld();
-            // layer-1 outputs outside the cloth are zero (layer 2's zero padding)
-            const int y = y0 - 2 + ry1, x = x0 - 2 + rx1;
-            const bool in = y >= 0 && y < H && x >= 0 && x < W;
+            {   // epilogue: warp half 0 -> phi1, half 1 -> xi1; zero outside the cloth
+                float r[32];
+                tc::tmem_ld32(lane_base + 32 * half, r);
+                tc::tmem_wait_ld();
+                const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
+                const int y = y0 - 2 + ry1, x = x0 - 2 + rx1;
+                const bool in = y >= 0 && y < H && x >= 0 && x < W;
+                uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float a8[8], b8[8];
+                for (int p = 0; p < 4; ++p) {
+                    float a8[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    a8[e] = in ? r1[8 * p + e] : 0.f;
-                    b8[e] = in ? r2[8 * p + e] : 0.f;
+                    for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
+                    dstb[p * N1BUF + j1] = pack8(a8);
                 }
-                reinterpret_cast<uint4*>(sm + oL1p)[p * N1BUF + j1] = pack8(a8);
-                reinterpret_cast<uint4*>(sm + oL1x)[p * N1BUF + j1] = pack8(b8);
             }
             tc::fence_before();
             __syncthreads();
@@ -238,53 +273,44 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         tc::fence_async_smem();
         __syncthreads();
 
-        // ---- 3-4. layer 2 as implicit GEMM, then the per-node epilogue
+        // ---- 3-4. layer 2 as implicit GEMM (double-buffered in TMEM), epilogue
+        if (tid == 0) issue_layer2(0);
         for (int c2 = 0; c2 < C2 && !timed_out; ++c2) {
-            if (tid == 0) {
-                tc::fence_after();
-#pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int row = c2 * 128 + (tap / 3) * PT + tap % 3;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const bool acc = tap > 0 || h > 0;
-                        const uint64_t ap = tc::sdesc(sbase + oL1p + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
-                        const uint64_t bp = tc::sdesc(sbase + oB2p + (tap * 4 + 2 * h) * 64 * 16, 64 * 16, 128);
-                        tc::mma_bf16(tmem + 0, ap, bp, tc::idesc_bf16(128, 64), acc);
-                        const uint64_t ax = tc::sdesc(sbase + oL1x + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
-                        const uint64_t bx = tc::sdesc(sbase + oB2x + (tap * 4 + 2 * h) * 32 * 16, 32 * 16, 128);
-                        tc::mma_bf16(tmem + 64, ax, bx, tc::idesc_bf16(128, 32), acc);
-                    }
-                }
-                tc::mma_commit(bar);
-            }
-            const bool done = tc::mbar_wait(bar, phase, kWaitLimit);
-            phase ^= 1u;
+            if (tid == 0 && c2 + 1 < C2) issue_layer2(c2 + 1);
+            const int b = c2 & 1;
+            const bool done = tc::mbar_wait(bar2[b], ph2[b], kWaitLimit);
+            ph2[b] ^= 1u;
             if (__syncthreads_or(!done)) { timed_out = true; break; }
             tc::fence_after();
-            float t[32], q[32], xi[32];
-            tc::tmem_ld32(lane_base + 0, t);
-            tc::tmem_ld32(lane_base + 32, q);
-            tc::tmem_ld32(lane_base + 64, xi);
-            tc::tmem_wait_ld();
-            const int j2 = c2 * 128 + tid;
-            if (j2 < N2) {
-                const int ry2 = j2 / PT, rx2 = j2 % PT;
-                const int y = y0 - 1 + ry2, x = x0 - 1 + rx2;
-                const bool valid = rx2 < WO + 2 && y >= 0 && y < H && x >= 0 && x < W;
-                float* qr = sQ + j2 * 27;
+            const int j2 = c2 * 128 + quarter * 32 + lane;
+            const int ry2 = j2 / PT, rx2 = j2 % PT;
+            const int y = y0 - 1 + ry2, x = x0 - 1 + rx2;
+            const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < H && x >= 0 && x < W;
+            const uint32_t col = lane_base + 128u * (uint32_t)b;
+            if (half == 1) {   // q: the WL partial sums, zero outside the cloth
+                float q[32];
+                tc::tmem_ld32(col + 32, q);
+                tc::tmem_wait_ld();
+                if (j2 < N2) {
+                    float* qr = sQ + j2 * 27;
 #pragma unroll
-                for (int k = 0; k < 27; ++k) qr[k] = valid ? q[k] : 0.f;
+                    for (int k = 0; k < 27; ++k) qr[k] = valid ? q[k] : 0.f;
+                }
+            } else {           // s = tanh(t), N + D at output nodes
+                float t[32], xi[32];
+                tc::tmem_ld32(col + 0, t);
+                tc::tmem_ld32(col + 64, xi);
+                tc::tmem_wait_ld();
                 const int oy = ry2 - 1, ox = rx2 - 1;
                 if (valid && oy >= 0 && oy < R && ox >= 0 && ox < WO) {
                     float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
 #pragma unroll
                     for (int c = 0; c < 32; ++c) {
-                        const float s = tc::tanh_approx(t[c]);
-                        const float xs = xi[c] * s;
-                        nd0 = fmaf(sWN[c], s, fmaf(sWD[c], xs, nd0));
-                        nd1 = fmaf(sWN[32 + c], s, fmaf(sWD[32 + c], xs, nd1));
-                        nd2 = fmaf(sWN[64 + c], s, fmaf(sWD[64 + c], xs, nd2));
+                        const float sv = tc::tanh_approx(t[c]);
+                        const float xs = xi[c] * sv;
+                        nd0 = fmaf(sWN[c], sv, fmaf(sWD[c], xs, nd0));
+                        nd1 = fmaf(sWN[32 + c], sv, fmaf(sWD[32 + c], xs, nd1));
+                        nd2 = fmaf(sWN[64 + c], sv, fmaf(sWD[64 + c], xs, nd2));
                     }
                     float* o = sND + (oy * WO + ox) * 3;
                     o[0] = nd0; o[1] = nd1; o[2] = nd2;
@@ -312,59 +338,66 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
                 for (int co = 0; co < 3; ++co) A.a[(((int64_t)n * 3 + co) * H + y) * W + x] = acc[co];
             } else {
+                const ClothDesc& D = *sD;
                 const int iy = oy + 3, ix = ox + 3;
                 auto U = [&](int ch, int dy, int dx) { return sIN[ch * IH * IW + (iy + dy) * IW + ix + dx]; };
-                if (D->p_quarter != 0.f) {
+                if (D.p_quarter != 0.f) {
                     const float bE = x + 1 < W ? 1.f : 0.f, bW = x > 0 ? 1.f : 0.f;
                     const float bN = y + 1 < H ? 1.f : 0.f, bS = y > 0 ? 1.f : 0.f;
                     float e[3], nn[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float ui = U(c, 0, 0);
-                        e[c] = bE * (U(c, 0, 1) - ui + (c == 0 ? D->h : 0.f)) - bW * (U(c, 0, -1) - ui - (c == 0 ? D->h : 0.f));
-                        nn[c] = bN * (U(c, 1, 0) - ui + (c == 1 ? D->h : 0.f)) - bS * (U(c, -1, 0) - ui - (c == 1 ? D->h : 0.f));
+                        e[c] = bE * (U(c, 0, 1) - ui + (c == 0 ? D.h : 0.f)) - bW * (U(c, 0, -1) - ui - (c == 0 ? D.h : 0.f));
+                        nn[c] = bN * (U(c, 1, 0) - ui + (c == 1 ? D.h : 0.f)) - bS * (U(c, -1, 0) - ui - (c == 1 ? D.h : 0.f));
                     }
-                    const float sc = D->p_quarter * D->inv_m;
+                    const float sc = D.p_quarter * D.inv_m;
                     acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
                     acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
                     acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
                 }
-                const bool pinned = (A.pinmask[D->pin_off + (int64_t)y * D->pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
+                const bool pinned = (A.pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
                 float vn[3], un[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    vn[c] = pinned ? 0.f : fmaf(D->dt, acc[c], U(3 + c, 0, 0));
-                    un[c] = fmaf(D->dt, vn[c], U(c, 0, 0));
+                    vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], U(3 + c, 0, 0));
+                    un[c] = fmaf(D.dt, vn[c], U(c, 0, 0));
                 }
-                if (D->sph_on) {
-                    const float rx = fmaf((float)x, D->h, -D->sph_cx) + un[0];
-                    const float ry = fmaf((float)y, D->h, -D->sph_cy) + un[1];
-                    const float rz = un[2] - D->sph_cz;
+                if (D.sph_on) {
+                    const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
+                    const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
+                    const float rz = un[2] - D.sph_cz;
                     const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    if (dd < D->sph_r2 && dd > 0.f) {
-                        const float s = D->sph_r * rsqrtf(dd);
-                        un[0] = fmaf(s, rx, un[0] - rx);
-                        un[1] = fmaf(s, ry, un[1] - ry);
-                        un[2] = fmaf(s, rz, un[2] - rz);
+                    if (dd < D.sph_r2 && dd > 0.f) {
+                        const float sc = D.sph_r * rsqrtf(dd);
+                        un[0] = fmaf(sc, rx, un[0] - rx);
+                        un[1] = fmaf(sc, ry, un[1] - ry);
+                        un[2] = fmaf(sc, rz, un[2] - rz);
                         vn[0] = vn[1] = vn[2] = 0.f;
                     }
                 }
                 if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
-                float* out = A.dst + D->plane_off + (int64_t)y * D->pitch + col_pos(x);
+                float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    out[c * D->plane_stride] = un[c];
-                    out[(3 + c) * D->plane_stride] = vn[c];
+                    out[c * D.plane_stride] = un[c];
+                    out[(3 + c) * D.plane_stride] = vn[c];
                 }
             }
         }
         __syncthreads();
     }
 
-    // ---- tear-down: on a timeout wait (bounded) for the MMAs still in flight
+    // ---- tear-down: after a timeout, wait (bounded) for the MMAs in flight
     if (timed_out) {
         if (tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
-        tc::mbar_wait(bar, phase ^ 1u, kWaitLimit);
+        // a chunk may have been issued and not yet waited for: try both
+        // phases of every barrier, each wait bounded
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_wait(bar1, ph1 ^ (uint32_t)k, 1u << 20);
+            tc::mbar_wait(bar2[0], ph2[0] ^ (uint32_t)k, 1u << 20);
+            tc::mbar_wait(bar2[1], ph2[1] ^ (uint32_t)k, 1u << 20);
+        }
     }
     tc::fence_before();
     __syncthreads();
