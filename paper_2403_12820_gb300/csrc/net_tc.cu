@@ -2,23 +2,26 @@
 // into one kernel on the tcgen05 tensor cores: BF16 operands in shared
 // memory, FP32 accumulators in tensor memory.
 //
-// One CTA (4 warps) per SM loops over tiles of R x WO output nodes.  With
-// the layer pitch PT = WO + 4, node (ry, rx) of a layer region has the
-// linear index ry * PT + rx, and an M = 128 MMA covers 128 consecutive
-// linear indices ("a chunk").  Per tile:
-//   1. stage u, v of the (R+6) x (WO+6) input tile (3-node halo) in smem;
-//   2. layer 1 (Eq. 6): per chunk of the (R+4) x PT layer-1 region, an
-//      im2col A tile (K = 3 channels x 9 taps = 27, padded to 32) per field,
-//      two MMAs per field against W1[:, field] -> phi1, xi1 (BF16, zero
-//      outside the cloth) in smem, K-major core-matrix layout;
-//   3. layer 2 as implicit GEMM: for each chunk of the (R+2)-row layer-2
-//      region and each tap (dy, dx), the A operand is the layer-1 buffer
-//      shifted by dy * PT + dx rows — a descriptor offset, no copy.  The
-//      position field multiplies by [P.W2 | WL_tap.W2] (N = 64): it yields
-//      t = P phi (the pre-activation of s) and the 27 partial sums
-//      q_tap,co = sum_c WL[co][c][tap] phi_c directly, since phi enters
-//      Eq. 7 only linearly through P and WL; the velocity field multiplies
-//      by W2 (N = 32) -> xi;
+// One CTA (8 warps) per SM loops over tiles of R x WO output nodes.  Every
+// layer region of a tile is stored at the pitch PT = WO + 6, so node
+// (ry, rx) of a region has the linear index ry * PT + rx, an M = 128 MMA
+// covers 128 consecutive linear indices ("a chunk"), and a 3x3 tap (ky, kx)
+// is the same buffer shifted by ky * PT + kx rows — a descriptor offset,
+// never a copy (implicit GEMM).  Per tile:
+//   1. stage u, v of the (R+6)-row input region as BF16, 8 channels per
+//      node and field (in_scale u | 0, in_scale v | 0);
+//   2. layer 1 (Eq. 6): per chunk and field, 5 MMAs of K = 16, each pairing
+//      two taps (the second core-matrix column of K sits LBO = the taps'
+//      row distance further) against W1[:, field] -> phi1, xi1 (BF16, zero
+//      outside the cloth), K-major core-matrix layout;
+//   3. layer 2: per chunk and tap two MMAs of K = 16 over the shifted
+//      layer-1 buffers.  The position field multiplies by
+//      [P.W2 | WL_tap.W2] (N = 64): it yields t = P phi (the pre-activation
+//      of s) and the 27 partial sums q_tap,co = sum_c WL[co][c][tap] phi_c
+//      directly, since phi enters Eq. 7 only linearly through P and WL; the
+//      velocity field multiplies by W2 (N = 32) -> xi.  Accumulators are
+//      double-buffered in tensor memory so chunk c+1 runs during the
+//      epilogue of chunk c;
 //   4. epilogue per layer-2 node: s = tanh(t), N + D = WN s + WD (xi . s),
 //      q kept in smem (zero outside the cloth: WL's zero padding);
 //   5. per output node: L = bL + sum_tap q_tap at the tap's neighbour,
@@ -34,40 +37,60 @@
 namespace cloth {
 namespace {
 
-constexpr int R = 12, WO = 28, PT = WO + 4;   // output rows, output columns, layer pitch
-constexpr int IH = R + 6, IW = WO + 6;          // input tile (3-node halo)
-constexpr int N1 = (R + 4) * PT;                // layer-1 nodes of a tile
-constexpr int N2 = (R + 2) * PT;                // layer-2 positions (pitch PT)
-constexpr int C1 = N1 / 128;                    // layer-1 chunks
+constexpr int R = 12, WO = 28, PT = WO + 6;   // output rows, output columns, region pitch
+constexpr int N0 = (R + 6) * PT;                // input-region nodes of a tile
+constexpr int N1 = (R + 4) * PT;                // layer-1 region
+constexpr int N2 = (R + 2) * PT;                // layer-2 region
+constexpr int C1 = (N1 + 127) / 128;            // layer-1 chunks
 constexpr int C2 = (N2 + 127) / 128;            // layer-2 chunks
-constexpr int N1BUF = (C2 * 128 + 2 * PT + 2 + 127) / 128 * 128;   // + rows read by shifted taps
-constexpr int NTH = 256;                         // 8 warps; warps w and w + 4 share TMEM lanes
+constexpr int N1BUF = (C2 * 128 + 2 * PT + 2 + 15) / 16 * 16;   // layer-1 rows layer 2 reads
+constexpr int N0BUF = (C1 * 128 + 2 * PT + 3 + 15) / 16 * 16;   // input rows layer 1 reads
+constexpr int NWORK = 256;                       // 8 worker warps; warps w and w + 4 share TMEM lanes
+constexpr int NTH = NWORK + 32;                  // + 1 warp that issues the MMAs
 constexpr uint32_t kWaitLimit = 1u << 24;
-static_assert(N1 % 128 == 0, "layer-1 region must be whole chunks");
-static_assert(N1BUF >= N1, "layer-1 buffer");
+static_assert(N1BUF >= N1 && N0BUF >= N0, "buffers");
 
-// packed BF16 weights: B1 [field][plane][32][8], B2p [tap][plane][64][8],
-// B2x [tap][plane][32][8]; plane = 8 consecutive K (input) channels
-constexpr int kB1 = 2 * 4 * 32 * 16, kB2p = 9 * 4 * 64 * 16, kB2x = 9 * 4 * 32 * 16;
+// Layer-1 tap pairs: MMA p covers taps kPairA[p] and kPairB[p] (-1: none).
+__host__ __device__ constexpr int pair_a(int p) { return 2 * p; }
+__host__ __device__ constexpr int pair_b(int p) { return p < 4 ? 2 * p + 1 : -1; }
+__host__ __device__ constexpr int tap_off(int t) { return (t / 3) * PT + t % 3; }
+
+// packed BF16 weights: B1 [pair 5][khalf 2][64][8] (khalf = the pair's
+// first / second tap; n < 32 -> phi1 from input channels 0..2 (u),
+// n >= 32 -> xi1 from channels 3..5 (v)), B2p [tap][plane][64][8],
+// B2x [tap][plane][32][8] (plane = 8 input channels)
+constexpr int kB1 = 5 * 2 * 64 * 16, kB2p = 9 * 4 * 64 * 16, kB2x = 9 * 4 * 32 * 16;
 constexpr int kPack = kB1 + kB2p + kB2x;
+
+// FP32 u, v of the output nodes and their 1-node halo, for the update
+constexpr int UH = R + 2, UW = WO + 2;
+// q is kept for the valid layer-2 positions only: (R+2) x (WO+2)
+constexpr int NQ = (R + 2) * (WO + 2);
 
 // shared memory map (bytes)
 constexpr int oB1 = 0, oB2p = oB1 + kB1, oB2x = oB2p + kB2p;
-constexpr int oL1p = oB2x + kB2x;                  // phi1 [plane][N1BUF][8] bf16
-constexpr int oL1x = oL1p + 4 * N1BUF * 16;        // xi1
-constexpr int oA1 = oL1x + 4 * N1BUF * 16;         // im2col [field][plane][128][8]
-constexpr int oIN = oA1 + 2 * 4 * 128 * 16;        // u, v [6][IH][IW] float
-constexpr int oQ = oIN + 6 * IH * IW * 4;          // q [N2][27] float
-constexpr int oND = oQ + N2 * 27 * 4;              // N + D [R * WO][3] float
-constexpr int oPar = oND + R * WO * 3 * 4;         // WN[96] WD[96] bL[3] outs[3] ins[6] (+pad)
-constexpr int oDesc = oPar + 208 * 4;              // the tile's cloth descriptor
-constexpr int oBar = oDesc + (int)sizeof(ClothDesc);   // 3 mbarriers, tensor-memory address
-constexpr int kSmem = oBar + 32;
+constexpr int oIn = oB2x + kB2x;                    // input [N0BUF][8] bf16: in_scale (u, v), 0, 0
+constexpr int oL1p = oIn + N0BUF * 16;              // phi1 [plane][N1BUF][8] bf16
+constexpr int oL1x = oL1p + 4 * N1BUF * 16;         // xi1
+constexpr int oQ = oL1x + 4 * N1BUF * 16;           // q [NQ][27] float
+constexpr int oU = oQ + NQ * 27 * 4;                // u, v [6][UH][UW] float
+constexpr int oND = oU + 6 * UH * UW * 4;           // N + D, two halves [2][R * WO][3] float
+constexpr int oPar = oND + 2 * R * WO * 3 * 4;      // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
+constexpr int oDesc = oPar + (256 + 16) * 4;        // the tile's cloth descriptor
+constexpr int oBar = oDesc + (int)sizeof(ClothDesc);   // mbarriers: layer 1 [C1], layer 2 [2]; TMEM address
+constexpr int kNumBars = C1 + 2;
+constexpr int oTmemSlot = oBar + 8 * kNumBars;
+constexpr int kSmem = oTmemSlot + 16;
 static_assert(kSmem <= 232448, "shared memory");
-static_assert(oIN % 16 == 0 && oQ % 16 == 0 && oND % 16 == 0 && oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
+static_assert(oIn % 16 == 0 && oL1p % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 && oND % 16 == 0 &&
+                  oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
               "alignment");
 
-constexpr uint32_t kTmemCols = 256;
+// TMEM columns: layer-1 chunk c at [64 c, +64); layer-2 buffer b at
+// [kL2Col + 96 b, +96)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kL2Col = 64 * C1;
+static_assert(kL2Col + 2 * 96 <= kTmemCols, "tensor memory columns");
 
 struct TcArgs {
     const uint4* wpack;   // packed BF16 weights (kPack bytes)
@@ -96,52 +119,61 @@ __device__ __forceinline__ uint4 pack8(const float* v)
     return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 template <bool STEP>
 __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = tid < NWORK, issuer = tid == NWORK;
     const int quarter = warp & 3;                 // TMEM lanes [32 quarter, +32) of this warp
-    const int half = warp >> 2;                   // warps 0-3 and 4-7 split the columns
+    const int half = (warp >> 2) & 1;             // worker warps 0-3 and 4-7 split the columns
     const uint32_t sbase = tc::smem_u32(sm);
-    const uint32_t bar1 = sbase + oBar, bar2[2] = {sbase + oBar + 8, sbase + oBar + 16};
-    float* sIN = reinterpret_cast<float*>(sm + oIN);
     float* sQ = reinterpret_cast<float*>(sm + oQ);
+    float* sU = reinterpret_cast<float*>(sm + oU);
     float* sND = reinterpret_cast<float*>(sm + oND);
-    float* sWN = reinterpret_cast<float*>(sm + oPar);
-    float* sWD = sWN + 96;
-    float* sBL = sWD + 96;
+    const float4* sWND = reinterpret_cast<const float4*>(sm + oPar);   // [c][2]
+    float* sPar = reinterpret_cast<float*>(sm + oPar);
+    float* sBL = sPar + 256;
     float* sOut = sBL + 3;
     float* sIns = sOut + 3;
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
-    volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oBar + 24);
+    volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
+    auto bar1 = [&](int c) { return sbase + oBar + 8u * (uint32_t)c; };
+    auto bar2 = [&](int b) { return sbase + oBar + 8u * (uint32_t)(C1 + b); };
 
     // ---- one-time set-up: weights, barriers, tensor memory
     for (int e = tid; e < kPack / 16; e += NTH) reinterpret_cast<uint4*>(sm)[e] = A.wpack[e];
-    for (int e = tid; e < 96; e += NTH) {
-        sWN[e] = A.w[kOffWN + e];
-        sWD[e] = A.w[kOffWD + e];
+    for (int e = tid; e < 32 * 8; e += NTH) {
+        const int c = e >> 3, j = e & 7;
+        sPar[e] = j < 3 ? A.w[kOffWN + j * kC + c] : (j < 6 ? A.w[kOffWD + (j - 3) * kC + c] : 0.f);
     }
     if (tid < 3) {
         sBL[tid] = A.w[kOffBL + tid];
         sOut[tid] = A.w[kOffOuts + tid];
     }
     if (tid < 6) sIns[tid] = A.w[kOffIns + tid];
-    // rows N1 .. N1BUF of the layer-1 buffers are read only by the junk
-    // positions of the last layer-2 chunk; keep them zero
-    for (int e = tid; e < 2 * 4 * (N1BUF - N1); e += NTH) {
-        const int buf = e / (4 * (N1BUF - N1)), rem = e % (4 * (N1BUF - N1));
-        const int plane = rem / (N1BUF - N1), row = N1 + rem % (N1BUF - N1);
-        reinterpret_cast<uint4*>(sm + (buf ? oL1x : oL1p))[plane * N1BUF + row] = make_uint4(0, 0, 0, 0);
-    }
+    // input rows N0 .. N0BUF are read only by junk layer-1 positions; keep them zero
+    for (int e = tid; e < N0BUF - N0; e += NTH) reinterpret_cast<uint4*>(sm + oIn)[N0 + e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        tc::mbar_init(bar1, 1);
-        tc::mbar_init(bar2[0], 1);
-        tc::mbar_init(bar2[1], 1);
+        for (int b = 0; b < kNumBars; ++b) tc::mbar_init(sbase + oBar + 8u * (uint32_t)b, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(sbase + oBar + 24, kTmemCols);
+        tc::tmem_alloc(sbase + oTmemSlot, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::fence_before();
@@ -153,25 +185,43 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     bool timed_out = false;
     const int n_tiles = STEP ? A.n_tiles : A.N * A.tiles_y * A.tiles_x;
 
-    // layer-2 MMAs of chunk c into TMEM columns [128 (c & 1), +96)
-    auto issue_layer2 = [&](int c2) {
+    // Descriptors of the issuer: a descriptor plus (byte offset >> 4) is the
+    // same matrix shifted by that offset (the start-address field is the low
+    // 14 bits and every operand lies below 256 KB).
+    const uint64_t dIn0 = tc::sdesc(sbase + oIn, 16, 128), dIn1 = tc::sdesc(sbase + oIn, 512, 128);
+    const uint64_t dB1 = tc::sdesc(sbase + oB1, 64 * 16, 128);
+    const uint64_t dL1p = tc::sdesc(sbase + oL1p, N1BUF * 16, 128), dL1x = tc::sdesc(sbase + oL1x, N1BUF * 16, 128);
+    const uint64_t dB2p = tc::sdesc(sbase + oB2p, 64 * 16, 128), dB2x = tc::sdesc(sbase + oB2x, 32 * 16, 128);
+
+    auto issue_layer1 = [&]() {   // all chunks at once, chunk c into columns [64 c, +64)
         tc::fence_after();
-        const uint32_t d = tmem + 128u * (uint32_t)(c2 & 1);
+        for (int c1 = 0; c1 < C1; ++c1) {
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                const int ta = pair_a(p), tb = pair_b(p);
+                const uint64_t base = (tb >= 0 && tap_off(tb) - tap_off(ta) != 1) ? dIn1 : dIn0;
+                const uint64_t ad = base + (uint64_t)(c1 * 128 + tap_off(ta));
+                const uint64_t bd = dB1 + (uint64_t)(p * 2 * 64);
+                tc::mma_bf16(tmem + 64u * (uint32_t)c1, ad, bd, tc::idesc_bf16(128, 64), p > 0);
+            }
+            tc::mma_commit(bar1(c1));
+        }
+    };
+    auto issue_layer2 = [&](int c2) {   // chunk c2 into buffer c2 & 1
+        tc::fence_after();
+        const uint32_t d = tmem + kL2Col + 96u * (uint32_t)(c2 & 1);
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-            const int row = c2 * 128 + (tap / 3) * PT + tap % 3;
+            const int row = c2 * 128 + tap_off(tap);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const bool acc = tap > 0 || h > 0;
-                const uint64_t ap = tc::sdesc(sbase + oL1p + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
-                const uint64_t bp = tc::sdesc(sbase + oB2p + (tap * 4 + 2 * h) * 64 * 16, 64 * 16, 128);
-                tc::mma_bf16(d, ap, bp, tc::idesc_bf16(128, 64), acc);
-                const uint64_t ax = tc::sdesc(sbase + oL1x + (2 * h * N1BUF + row) * 16, N1BUF * 16, 128);
-                const uint64_t bx = tc::sdesc(sbase + oB2x + (tap * 4 + 2 * h) * 32 * 16, 32 * 16, 128);
-                tc::mma_bf16(d + 64, ax, bx, tc::idesc_bf16(128, 32), acc);
+                const uint64_t ao = (uint64_t)(2 * h * N1BUF + row);
+                tc::mma_bf16(d, dL1p + ao, dB2p + (uint64_t)((tap * 4 + 2 * h) * 64), tc::idesc_bf16(128, 64), acc);
+                tc::mma_bf16(d + 64, dL1x + ao, dB2x + (uint64_t)((tap * 4 + 2 * h) * 32), tc::idesc_bf16(128, 32), acc);
             }
         }
-        tc::mma_commit(bar2[c2 & 1]);
+        tc::mma_commit(bar2(c2 & 1));
     };
 
     for (int tile = blockIdx.x; tile < n_tiles && !timed_out; tile += gridDim.x) {
@@ -188,200 +238,200 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             const int r = tile % (A.tiles_y * A.tiles_x);
             y0 = (r / A.tiles_x) * R; x0 = (r % A.tiles_x) * WO; H = A.H; W = A.W;
         }
-        // ---- 1. input tile: u, v (raw) with a 3-node halo, zero outside the grid
-        {
-            int64_t cbase = 0, cstride = 0, rstride = 0;
-            const float* srcp;
-            if constexpr (STEP) {
-                srcp = A.src + sD->plane_off; cstride = sD->plane_stride; rstride = sD->pitch;
-            } else {
-                srcp = A.z + (int64_t)n * 6 * H * W; cstride = (int64_t)H * W; rstride = W;
+        int64_t cstride, rstride;
+        const float* srcp;
+        if constexpr (STEP) {
+            srcp = A.src + sD->plane_off; cstride = sD->plane_stride; rstride = sD->pitch;
+        } else {
+            srcp = A.z + (int64_t)n * 6 * H * W; cstride = (int64_t)H * W; rstride = W;
+        }
+        // ---- 1. input region as BF16: node (iy, ix) at iy * PT + ix holds
+        // (in_scale u, in_scale v, 0, 0), zero outside the grid; the raw u, v
+        // of the output nodes and their halo also go to the FP32 tile
+        if (worker) {
+            for (int j0 = tid; j0 < N0; j0 += NWORK) {
+                const int iy = j0 / PT, ix = j0 % PT;
+                const int y = y0 - 3 + iy, x = x0 - 3 + ix;
+                float raw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (y >= 0 && y < H && x >= 0 && x < W) {
+                    const float* p0 = srcp + (int64_t)y * rstride + (STEP ? col_pos(x) : x);
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) raw[c] = __ldg(p0 + c * cstride);
+                }
+                float v[8];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[c] = sIns[c] * raw[c];
+                v[6] = v[7] = 0.f;
+                reinterpret_cast<uint4*>(sm + oIn)[j0] = pack8(v);
+                const int uy = iy - 2, ux = ix - 2;
+                if (uy >= 0 && uy < UH && ux >= 0 && ux < UW)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) sU[(c * UH + uy) * UW + ux] = raw[c];
             }
-            (void)cbase;
-#pragma unroll 4
-            for (int e = tid; e < 6 * IH * IW; e += NTH) {
-                const int ch = e / (IH * IW), rem = e % (IH * IW);
-                const int y = y0 - 3 + rem / IW, x = x0 - 3 + rem % IW;
-                float val = 0.f;
-                if (y >= 0 && y < H && x >= 0 && x < W)
-                    val = __ldg(srcp + ch * cstride + (int64_t)y * rstride + (STEP ? col_pos(x) : x));
-                sIN[e] = val;
-            }
+            tc::fence_async_smem();
         }
         __syncthreads();
 
-        // ---- 2. layer 1 (Eq. 6), chunk by chunk
-        for (int c1 = 0; c1 < C1 && !timed_out; ++c1) {
-            {   // im2col: thread = (field, row)
-                const int row = tid & 127, f = tid >> 7;
-                const int j1 = c1 * 128 + row, ry1 = j1 / PT, rx1 = j1 % PT;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int k = 8 * p + e;           // k = channel * 9 + tap
-                        if (k < 27) {
-                            const int ci = k / 9, tap = k % 9;
-                            v[e] = sIns[3 * f + ci] *
-                                   sIN[(3 * f + ci) * IH * IW + (ry1 + tap / 3) * IW + rx1 + tap % 3];
-                        } else {
-                            v[e] = 0.f;
-                        }
-                    }
-                    reinterpret_cast<uint4*>(sm + oA1)[(f * 4 + p) * 128 + row] = pack8(v);
-                }
-            }
-            tc::fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
+        // ---- 2. layer 1 (Eq. 6): the issuer queues every chunk; the workers
+        // store each chunk's phi1 / xi1 as it completes
+        if (issuer) issue_layer1();
+        bool ok = true;
+        if (worker) {
+            for (int c1 = 0; c1 < C1; ++c1) {
+                if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) { ok = false; break; }
                 tc::fence_after();
-#pragma unroll
-                for (int f = 0; f < 2; ++f)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint64_t ad = tc::sdesc(sbase + oA1 + (f * 4 + 2 * h) * 128 * 16, 128 * 16, 128);
-                        const uint64_t bd = tc::sdesc(sbase + oB1 + (f * 4 + 2 * h) * 32 * 16, 32 * 16, 128);
-                        tc::mma_bf16(tmem + 32 * f, ad, bd, tc::idesc_bf16(128, 32), h > 0);
-                    }
-                tc::mma_commit(bar1);
-            }
-            const bool done = tc::mbar_wait(bar1, ph1, kWaitLimit);
-            ph1 ^= 1u;
-            if (__syncthreads_or(!done)) { timed_out = true; break; }
-            tc::fence_after();
-            {   // epilogue: warp half 0 -> phi1, half 1 -> xi1; zero outside the cloth
                 float r[32];
-                tc::tmem_ld32(lane_base + 32 * half, r);
+                tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r);
                 tc::tmem_wait_ld();
                 const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
                 const int y = y0 - 2 + ry1, x = x0 - 2 + rx1;
-                const bool in = y >= 0 && y < H && x >= 0 && x < W;
-                uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
+                const bool in = j1 < N1 && rx1 < WO + 4 && y >= 0 && y < H && x >= 0 && x < W;
+                if (j1 < N1BUF) {
+                    uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float a8[8];
+                    for (int p = 0; p < 4; ++p) {
+                        float a8[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
-                    dstb[p * N1BUF + j1] = pack8(a8);
-                }
-            }
-            tc::fence_before();
-            __syncthreads();
-        }
-        if (timed_out) break;
-        tc::fence_async_smem();
-        __syncthreads();
-
-        // ---- 3-4. layer 2 as implicit GEMM (double-buffered in TMEM), epilogue
-        if (tid == 0) issue_layer2(0);
-        for (int c2 = 0; c2 < C2 && !timed_out; ++c2) {
-            if (tid == 0 && c2 + 1 < C2) issue_layer2(c2 + 1);
-            const int b = c2 & 1;
-            const bool done = tc::mbar_wait(bar2[b], ph2[b], kWaitLimit);
-            ph2[b] ^= 1u;
-            if (__syncthreads_or(!done)) { timed_out = true; break; }
-            tc::fence_after();
-            const int j2 = c2 * 128 + quarter * 32 + lane;
-            const int ry2 = j2 / PT, rx2 = j2 % PT;
-            const int y = y0 - 1 + ry2, x = x0 - 1 + rx2;
-            const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < H && x >= 0 && x < W;
-            const uint32_t col = lane_base + 128u * (uint32_t)b;
-            if (half == 1) {   // q: the WL partial sums, zero outside the cloth
-                float q[32];
-                tc::tmem_ld32(col + 32, q);
-                tc::tmem_wait_ld();
-                if (j2 < N2) {
-                    float* qr = sQ + j2 * 27;
-#pragma unroll
-                    for (int k = 0; k < 27; ++k) qr[k] = valid ? q[k] : 0.f;
-                }
-            } else {           // s = tanh(t), N + D at output nodes
-                float t[32], xi[32];
-                tc::tmem_ld32(col + 0, t);
-                tc::tmem_ld32(col + 64, xi);
-                tc::tmem_wait_ld();
-                const int oy = ry2 - 1, ox = rx2 - 1;
-                if (valid && oy >= 0 && oy < R && ox >= 0 && ox < WO) {
-                    float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const float sv = tc::tanh_approx(t[c]);
-                        const float xs = xi[c] * sv;
-                        nd0 = fmaf(sWN[c], sv, fmaf(sWD[c], xs, nd0));
-                        nd1 = fmaf(sWN[32 + c], sv, fmaf(sWD[32 + c], xs, nd1));
-                        nd2 = fmaf(sWN[64 + c], sv, fmaf(sWD[64 + c], xs, nd2));
+                        for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
+                        dstb[p * N1BUF + j1] = pack8(a8);
                     }
-                    float* o = sND + (oy * WO + ox) * 3;
-                    o[0] = nd0; o[1] = nd1; o[2] = nd2;
                 }
             }
+            tc::fence_async_smem();
             tc::fence_before();
-            __syncthreads();
+        }
+        ph1 ^= 1u;
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+
+        // ---- 3-4. layer 2 as implicit GEMM, double-buffered in TMEM: chunk
+        // c+1 runs while the workers read chunk c
+        if (issuer) {
+            issue_layer2(0);
+            if (C2 > 1) issue_layer2(1);
+        }
+        for (int c2 = 0; c2 < C2; ++c2) {
+            const int b = c2 & 1;
+            ok = true;
+            if (worker) {
+                ok = tc::mbar_wait(bar2(b), ph2[b], kWaitLimit);
+                if (ok) {
+                    tc::fence_after();
+                    const int j2 = c2 * 128 + quarter * 32 + lane;
+                    const int ry2 = j2 / PT, rx2 = j2 % PT;
+                    const int y = y0 - 1 + ry2, x = x0 - 1 + rx2;
+                    const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < H && x >= 0 && x < W;
+                    const int oy = ry2 - 1, ox = rx2 - 1;
+                    const bool out_node = valid && oy >= 0 && oy < R && ox >= 0 && ox < WO;
+                    const uint32_t col = lane_base + kL2Col + 96u * (uint32_t)b;
+                    // s = tanh(t), N + D over the channel half [16 half, +16)
+                    float t[16], xi[16];
+                    tmem_ld16(col + 16 * half, t);
+                    tmem_ld16(col + 64 + 16 * half, xi);
+                    if (half == 1) {   // q: the WL partial sums, zero outside the cloth
+                        float q[32];
+                        tc::tmem_ld32(col + 32, q);
+                        tc::tmem_wait_ld();
+                        if (j2 < N2 && rx2 < WO + 2) {
+                            float* qr = sQ + (ry2 * (WO + 2) + rx2) * 27;
+#pragma unroll
+                            for (int k = 0; k < 27; ++k) qr[k] = valid ? q[k] : 0.f;
+                        }
+                    } else {
+                        tc::tmem_wait_ld();
+                    }
+                    if (out_node) {
+                        float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float sv = tc::tanh_approx(t[c]);
+                            const float xs = xi[c] * sv;
+                            const float4 w0 = sWND[2 * (16 * half + c)], w1 = sWND[2 * (16 * half + c) + 1];
+                            nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
+                            nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
+                            nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
+                        }
+                        float* o = sND + (half * R * WO + oy * WO + ox) * 3;
+                        o[0] = nd0; o[1] = nd1; o[2] = nd2;
+                    }
+                    tc::fence_before();
+                }
+            }
+            ph2[b] ^= 1u;
+            if (__syncthreads_or(!ok)) { timed_out = true; break; }
+            if (issuer && c2 + 2 < C2) issue_layer2(c2 + 2);   // buffer b is free again
         }
         if (timed_out) break;
 
         // ---- 5. per output node: L, a, and (step mode) the update
-        for (int o = tid; o < R * WO; o += NTH) {
-            const int oy = o / WO, ox = o % WO, y = y0 + oy, x = x0 + ox;
-            if (y >= H || x >= W) continue;
-            float acc[3];
+        if (worker) {
+            for (int o = tid; o < R * WO; o += NWORK) {
+                const int oy = o / WO, ox = o % WO, y = y0 + oy, x = x0 + ox;
+                if (y >= H || x >= W) continue;
+                float acc[3];
 #pragma unroll
-            for (int co = 0; co < 3; ++co) {
-                float L = sBL[co];
+                for (int co = 0; co < 3; ++co) {
+                    float L = sBL[co];
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap)
-                    L += sQ[((oy + tap / 3) * PT + ox + tap % 3) * 27 + tap * 3 + co];
-                acc[co] = sOut[co] * (L + sND[o * 3 + co]);
-            }
-            if constexpr (!STEP) {
+                    for (int tap = 0; tap < 9; ++tap)
+                        L += sQ[((oy + tap / 3) * (WO + 2) + ox + tap % 3) * 27 + tap * 3 + co];
+                    acc[co] = sOut[co] * (L + sND[o * 3 + co] + sND[(R * WO + o) * 3 + co]);
+                }
+                if constexpr (!STEP) {
 #pragma unroll
-                for (int co = 0; co < 3; ++co) A.a[(((int64_t)n * 3 + co) * H + y) * W + x] = acc[co];
-            } else {
-                const ClothDesc& D = *sD;
-                const int iy = oy + 3, ix = ox + 3;
-                auto U = [&](int ch, int dy, int dx) { return sIN[ch * IH * IW + (iy + dy) * IW + ix + dx]; };
-                if (D.p_quarter != 0.f) {
-                    const float bE = x + 1 < W ? 1.f : 0.f, bW = x > 0 ? 1.f : 0.f;
-                    const float bN = y + 1 < H ? 1.f : 0.f, bS = y > 0 ? 1.f : 0.f;
-                    float e[3], nn[3];
+                    for (int co = 0; co < 3; ++co) A.a[(((int64_t)n * 3 + co) * H + y) * W + x] = acc[co];
+                } else {
+                    const ClothDesc& D = *sD;
+                    auto U = [&](int ch, int yy, int xx) {   // from the FP32 tile
+                        return sU[(ch * UH + yy - y0 + 1) * UW + xx - x0 + 1];
+                    };
+                    float u[3], v[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float ui = U(c, 0, 0);
-                        e[c] = bE * (U(c, 0, 1) - ui + (c == 0 ? D.h : 0.f)) - bW * (U(c, 0, -1) - ui - (c == 0 ? D.h : 0.f));
-                        nn[c] = bN * (U(c, 1, 0) - ui + (c == 1 ? D.h : 0.f)) - bS * (U(c, -1, 0) - ui - (c == 1 ? D.h : 0.f));
+                        u[c] = U(c, y, x);
+                        v[c] = U(3 + c, y, x);
                     }
-                    const float sc = D.p_quarter * D.inv_m;
-                    acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
-                    acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
-                    acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
-                }
-                const bool pinned = (A.pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
-                float vn[3], un[3];
+                    if (D.p_quarter != 0.f) {
+                        const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
+                        float e[3], nn[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], U(3 + c, 0, 0));
-                    un[c] = fmaf(D.dt, vn[c], U(c, 0, 0));
-                }
-                if (D.sph_on) {
-                    const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
-                    const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
-                    const float rz = un[2] - D.sph_cz;
-                    const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    if (dd < D.sph_r2 && dd > 0.f) {
-                        const float sc = D.sph_r * rsqrtf(dd);
-                        un[0] = fmaf(sc, rx, un[0] - rx);
-                        un[1] = fmaf(sc, ry, un[1] - ry);
-                        un[2] = fmaf(sc, rz, un[2] - rz);
-                        vn[0] = vn[1] = vn[2] = 0.f;
+                        for (int c = 0; c < 3; ++c) {
+                            e[c] = (bE ? U(c, y, x + 1) - u[c] + (c == 0 ? D.h : 0.f) : 0.f) -
+                                   (bW ? U(c, y, x - 1) - u[c] - (c == 0 ? D.h : 0.f) : 0.f);
+                            nn[c] = (bN ? U(c, y + 1, x) - u[c] + (c == 1 ? D.h : 0.f) : 0.f) -
+                                    (bS ? U(c, y - 1, x) - u[c] - (c == 1 ? D.h : 0.f) : 0.f);
+                        }
+                        const float sc = D.p_quarter * D.inv_m;
+                        acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
+                        acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
+                        acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
                     }
-                }
-                if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
-                float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
+                    const bool pinned = (A.pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
+                    float vn[3], un[3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    out[c * D.plane_stride] = un[c];
-                    out[(3 + c) * D.plane_stride] = vn[c];
+                    for (int c = 0; c < 3; ++c) {
+                        vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], v[c]);
+                        un[c] = fmaf(D.dt, vn[c], u[c]);
+                    }
+                    if (D.sph_on) {
+                        const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
+                        const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
+                        const float rz = un[2] - D.sph_cz;
+                        const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        if (dd < D.sph_r2 && dd > 0.f) {
+                            const float sc = D.sph_r * rsqrtf(dd);
+                            un[0] = fmaf(sc, rx, un[0] - rx);
+                            un[1] = fmaf(sc, ry, un[1] - ry);
+                            un[2] = fmaf(sc, rz, un[2] - rz);
+                            vn[0] = vn[1] = vn[2] = 0.f;
+                        }
+                    }
+                    if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
+                    float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        out[c * D.plane_stride] = un[c];
+                        out[(3 + c) * D.plane_stride] = vn[c];
+                    }
                 }
             }
         }
@@ -389,15 +439,12 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     }
 
     // ---- tear-down: after a timeout, wait (bounded) for the MMAs in flight
+    // (a chunk may have been issued and not yet waited for: try both phases)
     if (timed_out) {
         if (tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
-        // a chunk may have been issued and not yet waited for: try both
-        // phases of every barrier, each wait bounded
-        for (int k = 0; k < 2; ++k) {
-            tc::mbar_wait(bar1, ph1 ^ (uint32_t)k, 1u << 20);
-            tc::mbar_wait(bar2[0], ph2[0] ^ (uint32_t)k, 1u << 20);
-            tc::mbar_wait(bar2[1], ph2[1] ^ (uint32_t)k, 1u << 20);
-        }
+        for (int k = 0; k < 2; ++k)
+            for (int b = 0; b < kNumBars; ++b)
+                tc::mbar_wait(sbase + oBar + 8u * (uint32_t)b, (uint32_t)k, 1u << 18);
     }
     tc::fence_before();
     __syncthreads();
@@ -408,15 +455,16 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 __global__ void pack_bf16_kernel(const float* __restrict__ w, uint4* __restrict__ out)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr int R1 = 2 * 4 * 32, R2p = 9 * 4 * 64, R2x = 9 * 4 * 32;
+    constexpr int R1 = 5 * 2 * 64, R2p = 9 * 4 * 64, R2x = 9 * 4 * 32;
     if (r >= R1 + R2p + R2x) return;
     float v[8];
-    if (r < R1) {   // W1 for field f: K = ci * 9 + tap over the field's 3 input channels
-        const int f = r / 128, p = (r / 32) % 4, n = r % 32;
-        for (int e = 0; e < 8; ++e) {
-            const int k = 8 * p + e;
-            v[e] = k < 27 ? w[kOffW1 + (n * 6 + 3 * f + k / 9) * 9 + k % 9] : 0.f;
-        }
+    if (r < R1) {   // W1: tap pair p, the pair's first (kh 0) or second tap; n < 32 phi1 from
+                    // u (channels 0..2 of a node), n >= 32 xi1 from v (channels 3..5)
+        const int p = r / 128, kh = (r / 64) % 2, n = r % 64;
+        const int tap = kh == 0 ? pair_a(p) : pair_b(p);
+        const int f = n / 32, co = n % 32;
+        for (int e = 0; e < 8; ++e)
+            v[e] = (tap >= 0 && e / 3 == f && e < 6) ? w[kOffW1 + (co * 6 + e) * 9 + tap] : 0.f;
     } else if (r < R1 + R2p) {   // [P.W2 | WL_tap.W2] for the position field
         const int q = r - R1, tap = q / 256, p = (q / 64) % 4, n = q % 64;
         for (int e = 0; e < 8; ++e) {
@@ -452,7 +500,7 @@ cudaError_t net_tc_init()
 
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 {
-    constexpr int rows = 2 * 4 * 32 + 9 * 4 * 64 + 9 * 4 * 32;
+    constexpr int rows = 5 * 2 * 64 + 9 * 4 * 64 + 9 * 4 * 32;
     pack_bf16_kernel<<<(rows + 127) / 128, 128, 0, s>>>(w, static_cast<uint4*>(wpack));
     return cudaGetLastError();
 }
