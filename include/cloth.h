@@ -277,6 +277,41 @@ int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* by
  * d_work: cloth_net_workspace_size() bytes. */
 int cloth_step_net(cloth_ctx* ctx, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Training (Sec. 3.2.1, Eq. 8; Table 1)
+ * ---------------------------------------------------------------------- */
+
+/* Device workspace of cloth_train_loss for this context and unroll length. */
+int cloth_train_workspace_size(const cloth_ctx* ctx, int32_t S, size_t* bytes);
+
+/* Loss of Eq. 8 and its gradient for a batch of training windows.
+ * The context holds one window per cloth (all cloths of one size, each
+ * with its own pins and pressure); its current state is the window start
+ * (x_k, v_k).  d_targets [S][total_nodes][3] (packed ABI layout) holds the
+ * recorded positions x_{k+1} .. x_{k+S}.  Per window:
+ *   L = alpha * mean_free(((a_net(x_k, v_k) - a_true) / g_norm)^2)
+ *     + (1 - alpha) / S * sum_{s=1..S} mean_free(((x_hat_{k+s} - x_{k+s}) / h)^2)
+ * where a_true = (Eq. 1 + 2 + 4 force) / m at the window start (the plain
+ * step's acceleration without the pressure, which the network step adds
+ * itself), x_hat is the S-step network rollout of Fig. 2 (pressure and pins
+ * hard-encoded, no sphere), means run over the free (unpinned) nodes and
+ * their 3 components, and h is the cloth's spacing.  Writes the batch mean
+ * of L to d_loss (1 device float) and ADDS its gradient with respect to the
+ * CLOTH_NET_PARAMS weights to d_grad_w.  The gradient is the exact adjoint
+ * (net_backward through every step, the Euler update, pins and pressure);
+ * each step's activations are recomputed during the backward sweep (step
+ * checkpointing).  The context state is left unchanged.  FP32 networks only
+ * (CLOTH_EUNSUPPORTED otherwise); CLOTH_EINVAL if the cloths differ in size. */
+int cloth_train_loss(cloth_ctx* ctx, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
+                     float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream);
+
+/* One Adam update (Table 1's optimizer) of n parameters in place:
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+ * w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * All pointers are device arrays of n floats; t >= 1 is the step count. */
+int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32_t n, int32_t t, float lr,
+                  float beta1, float beta2, float eps, void* stream);
+
 /* Release the context's host resources (graphs, capture stream). */
 void cloth_destroy(cloth_ctx* ctx);
 

@@ -68,6 +68,11 @@ SIGNATURES = {
     "net_destroy": (None, [c_void_p]),
     "net_forward_static": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
     "cloth_net_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
+    "cloth_train_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
+    "cloth_train_loss": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p,
+                                   c_size_t, c_void_p]),
+    "net_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_float,
+                                c_float, c_void_p]),
     "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_info": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
     "cloth_destroy": (None, [c_void_p]),

@@ -142,6 +142,27 @@ class ClothBatch:
         ws = self.net_workspace(net.precision)
         _lib.call("cloth_step_net", self.handle, net.handle, int(steps), _ptr(ws), ws.numel(), self._s())
 
+    def train_loss(self, net, S: int, targets: torch.Tensor, alpha: float = 0.5, g_norm: float = 9.81,
+                   grad_w: torch.Tensor | None = None):
+        """Eq. 8 loss of the windows held by this batch (current state = window
+        start) against `targets` (S, total_nodes, 3); adds its gradient to
+        grad_w (created zero if None).  Returns (loss (1,), grad_w)."""
+        _require_cuda(targets, "targets")
+        if targets.numel() != S * 3 * self.total_nodes:
+            raise ValueError("targets must hold S * total_nodes * 3 floats")
+        n = ctypes.c_size_t()
+        _lib.call("cloth_train_workspace_size", self.handle, int(S), ctypes.byref(n))
+        ws = getattr(self, "_train_ws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+            self._train_ws = ws
+        if grad_w is None:
+            grad_w = torch.zeros(13027, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_train_loss", self.handle, net.handle, int(S), _ptr(targets), ctypes.c_float(alpha),
+                  ctypes.c_float(g_norm), _ptr(loss), _ptr(grad_w), _ptr(ws), ws.numel(), self._s())
+        return loss, grad_w
+
     def topology(self, b: int) -> torch.Tensor:
         s = self.specs[b]
         m = torch.empty(int(s["rows"]) * int(s["cols"]), dtype=torch.int16, device=self.device)

@@ -10,6 +10,7 @@
 #include "../../include/cloth.h"
 #include "cloth_internal.cuh"
 #include "net_internal.cuh"
+#include "train_internal.cuh"
 
 using namespace cloth;
 
@@ -105,6 +106,7 @@ struct cloth_ctx {
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
+    std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
     std::vector<NetGroup> groups;      // network step: cloths grouped by size
     int64_t group_max_nodes = 0;       // largest group's node count
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
@@ -237,9 +239,127 @@ int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wor
     return CLOTH_OK;
 }
 
+// Workspace of cloth_train_loss (float offsets).
+struct TrainWs {
+    size_t z, a, at, ga0, gu, gv, ga, gfp, ge, gn, gz, saved, fabi, coef, part, total;
+};
+TrainWs train_ws(const cloth_ctx* c, int S)
+{
+    const int64_t B = c->B, HW = (int64_t)c->grids[0].rows * c->grids[0].cols, n3 = B * 3 * HW;
+    TrainWs w{};
+    size_t off = 0;
+    auto take = [&](size_t floats) { const size_t o = off; off = align_up(off + floats, kAlign / sizeof(float)); return o; };
+    w.z = take((size_t)(S + 1) * B * 6 * HW);
+    w.a = take(n3); w.at = take(n3); w.ga0 = take(n3); w.gu = take(n3); w.gv = take(n3);
+    w.ga = take(n3); w.gfp = take(n3); w.ge = take(n3); w.gn = take(n3);
+    w.gz = take((size_t)B * 6 * HW);
+    w.saved = take((size_t)kSavedPerNode * B * HW);
+    w.fabi = take((size_t)3 * c->total_nodes);
+    w.coef = take((size_t)2 * B);
+    w.part = take((size_t)(S + 1) * train_blocks(c->grids[0].rows, c->grids[0].cols, c->B));
+    w.total = off * sizeof(float);
+    return w;
+}
+
+bool same_size(const cloth_ctx* c)
+{
+    for (int b = 1; b < c->B; ++b)
+        if (c->grids[b].rows != c->grids[0].rows || c->grids[b].cols != c->grids[0].cols) return false;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
+
+int cloth_train_workspace_size(const cloth_ctx* c, int32_t S, size_t* bytes)
+{
+    if (!c || !bytes || S < 1 || !same_size(c)) return CLOTH_EINVAL;
+    *bytes = train_ws(c, S).total;
+    return CLOTH_OK;
+}
+
+int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
+                     float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !net || !d_targets || !d_loss || !d_grad_w || !d_work || S < 1 || !same_size(c)) return CLOTH_EINVAL;
+    if (!(alpha >= 0.f && alpha <= 1.f) || !(g_norm > 0.f)) return CLOTH_EINVAL;
+    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    const TrainWs L = train_ws(c, S);
+    if (bytes < L.total) return CLOTH_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int B = c->B, H = c->grids[0].rows, W = c->grids[0].cols;
+    const int64_t HW = (int64_t)H * W, NHW = (int64_t)B * HW;
+    float* ws = static_cast<float*>(d_work);
+    float* Z = ws + L.z;
+    auto Zt = [&](int t) { return Z + (size_t)t * B * 6 * HW; };
+    float *A = ws + L.a, *AT = ws + L.at, *GA0 = ws + L.ga0, *GU = ws + L.gu, *GV = ws + L.gv;
+    float *GA = ws + L.ga, *GFP = ws + L.gfp, *GE = ws + L.ge, *GN = ws + L.gn, *GZ = ws + L.gz;
+    float *SAVED = ws + L.saved, *FABI = ws + L.fabi, *COEF = ws + L.coef, *PART = ws + L.part;
+    const int blocks = train_blocks(H, W, B);
+    const ClothDesc* D = c->d_desc();
+    const uint32_t* P = c->d_pins();
+
+    // per-window weights of the two terms (1/B: batch mean)
+    std::vector<float> coef(2 * B);
+    for (int b = 0; b < B; ++b) {
+        const double cnt = 3.0 * (double)std::max<int64_t>(c->free_nodes[b], 1);
+        const double h = c->desc[b].h;
+        coef[b] = (float)(alpha / (cnt * (double)g_norm * g_norm * B));
+        coef[B + b] = (float)((1.0 - alpha) / ((double)S * cnt * h * h * B));
+    }
+    CK(cudaMemcpyAsync(COEF, coef.data(), sizeof(float) * 2 * B, cudaMemcpyHostToDevice, s));
+
+    // targets of the physics term: the plain step's acceleration without pressure
+    int rc = launch_step(c, true, FABI, s);
+    if (rc) return rc;
+    CK(launch_state_to_z(D, c->d_state(c->cur), Zt(0), B, H, W, s));
+    CK(launch_a_true(D, FABI, Zt(0), AT, B, H, W, s));
+
+    auto forward = [&](int t) {   // a = cell(z_t), layer outputs into SAVED
+        NetFwdArgs f{};
+        f.src.z = Zt(t);
+        f.w = net->d_w();
+        f.t1 = SAVED + kSavT1 * NHW;
+        f.t2 = SAVED + kSavT2 * NHW;
+        f.s = SAVED + kSavS * NHW;
+        f.a = A;
+        f.N = B; f.H = H; f.W = W;
+        return launch_net_forward_simt(f, s);
+    };
+    // forward unroll: a_t, z_{t+1}, loss terms
+    for (int t = 0; t < S; ++t) {
+        CK(forward(t));
+        if (t == 0) CK(launch_phys_term(D, P, A, AT, COEF, GA0, PART, B, H, W, s));
+        CK(launch_train_euler(D, P, Zt(t), A, Zt(t + 1), B, H, W, s));
+        CK(launch_data_term(D, P, Zt(t + 1), d_targets + (size_t)t * 3 * c->total_nodes, COEF + B, nullptr,
+                            PART + (size_t)(t + 1) * blocks, B, H, W, s));
+    }
+    CK(launch_sum_partials(PART, (S + 1) * blocks, d_loss, s));
+
+    // backward sweep, recomputing each step's activations (step checkpointing)
+    CK(cudaMemsetAsync(GU, 0, sizeof(float) * 3 * NHW, s));
+    CK(cudaMemsetAsync(GV, 0, sizeof(float) * 3 * NHW, s));
+    for (int t = S; t >= 1; --t) {
+        CK(launch_data_term(D, P, Zt(t), d_targets + (size_t)(t - 1) * 3 * c->total_nodes, COEF + B, GU, nullptr,
+                            B, H, W, s));
+        CK(launch_euler_adjoint(D, P, GU, GV, t == 1 ? GA0 : nullptr, GA, GFP, B, H, W, s));
+        CK(launch_pressure_vjp(D, Zt(t - 1), GFP, GE, GN, GU, B, H, W, s));
+        CK(forward(t - 1));
+        CK(launch_net_backward_simt(net->d_w(), Zt(t - 1), SAVED, GA, GZ, net->d_part(), d_grad_w, B, H, W, s));
+        CK(launch_add_gz(GZ, GU, GV, B, H, W, s));
+    }
+    return CLOTH_OK;
+}
+
+int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32_t n, int32_t t, float lr,
+                  float beta1, float beta2, float eps, void* stream)
+{
+    if (!d_w || !d_grad || !d_m || !d_v || n < 1 || t < 1) return CLOTH_EINVAL;
+    CK(launch_adam(d_w, d_grad, d_m, d_v, n, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
 
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
@@ -364,15 +484,19 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
             d.sph_r = spheres[b].radius;
             d.sph_r2 = spheres[b].radius * spheres[b].radius;
         }
+        int64_t pinned = 0;
         if (pins && pins[b].count > 0) {
             if (!pins[b].node) { delete c; return CLOTH_EINVAL; }
             for (int i = 0; i < pins[b].count; ++i) {
                 const int32_t n = pins[b].node[i];
                 if (n < 0 || (int64_t)n >= (int64_t)g.rows * g.cols) { delete c; return CLOTH_EINVAL; }
                 const int r = n / g.cols, col = n % g.cols;
-                pinmask[words + (int64_t)r * d.pin_wpr + col / 32] |= 1u << (col % 32);
+                uint32_t& wd = pinmask[words + (int64_t)r * d.pin_wpr + col / 32];
+                if (!(wd & (1u << (col % 32)))) ++pinned;
+                wd |= 1u << (col % 32);
             }
         }
+        c->free_nodes.push_back((int64_t)g.rows * g.cols - pinned);
         c->desc.push_back(d);
         floats += align_up((size_t)(6 * d.plane_stride), kAlign / sizeof(float));
         words += (int64_t)g.rows * d.pin_wpr;

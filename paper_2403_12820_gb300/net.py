@@ -96,6 +96,15 @@ class Net:
             pass
 
 
+def adam_step(w: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, t: int, lr: float = 1e-3,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n: int | None = None) -> None:
+    """One in-place Adam update of the first n entries of w (libcloth kernel)."""
+    n = int(n if n is not None else g.numel())
+    _lib.call("net_adam_step", _ptr(w), _ptr(g), _ptr(m), _ptr(v), n, int(t), ctypes.c_float(lr),
+              ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps),
+              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
 class CellFunction(torch.autograd.Function):
     """a = cell(z; w) with libcloth's forward and hand-written backward.
 

@@ -1,0 +1,84 @@
+"""Training of the CNN cell on plain-simulator rollouts (Sec. 3.2.1, Eq. 8).
+
+Host-side orchestration only: the trajectories are produced by libcloth's
+plain step (recorded rollouts), the loss, its gradient through the 8-step
+unroll and the Adam update run in libcloth's kernels.  The host samples the
+windows (trajectory, start step) and gathers their states from the recorded
+trajectories.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import workloads as wl
+from .cloth import ClothBatch, pack
+from .net import FP32, N_BLOB, N_PARAMS, Net, adam_step
+
+
+class Dataset:
+    """`count` cloths of n x n stepped `steps` plain steps; positions and
+    velocities of every step kept on the device: x[t], v[t] of shape
+    (steps + 1, count * n * n, 3)."""
+
+    def __init__(self, count: int = 512, n: int = 64, steps: int = 200, seed: int = 1004, device="cuda",
+                 cfg: dict | None = None):
+        self.cfg = cfg if cfg is not None else wl.train_cloths(seed=seed, count=count, n=n)
+        self.count, self.n, self.steps = len(self.cfg["specs"]), int(self.cfg["specs"][0]["rows"]), int(steps)
+        sim = ClothBatch(self.cfg["specs"], self.cfg["pins"], device=device)
+        x0, v0 = pack(self.cfg["x"]).to(device), pack(self.cfg["v"]).to(device)
+        N = sim.total_nodes
+        self.x = torch.empty(steps + 1, N, 3, device=device)
+        self.v = torch.empty(steps + 1, N, 3, device=device)
+        self.x[0], self.v[0] = x0, v0
+        sim.set_state(x0, v0)
+        for t in range(1, steps + 1):
+            sim.step(1)
+            sim.get_state(self.x[t], self.v[t])
+        sim.close()
+        self.nodes = self.n * self.n
+
+
+class Trainer:
+    """Batches of `batch` windows, each an `unroll`-step stretch of one
+    trajectory; Adam (Table 1) with lr 1e-3."""
+
+    def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
+                 alpha: float = 0.5, seed: int = 7, device="cuda"):
+        self.data, self.batch, self.unroll, self.lr, self.alpha = data, batch, unroll, lr, alpha
+        self.rng = np.random.default_rng(seed)
+        h = data.cfg["specs"][0]["h"]
+        if blob is None:
+            blob = wl.kaiming_blob(2004, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
+        self.w = torch.from_numpy(np.asarray(blob, dtype=np.float32)).to(device)
+        self.m = torch.zeros(N_PARAMS, device=device)
+        self.v = torch.zeros(N_PARAMS, device=device)
+        self.t = 0
+        self.net = Net(blob, FP32, device=device)
+        self.device = device
+
+    def sample(self):
+        """Windows (trajectory, start) and a ClothBatch holding their cloths."""
+        d = self.data
+        traj = self.rng.choice(d.count, size=self.batch, replace=d.count < self.batch)
+        start = self.rng.integers(0, d.steps - self.unroll + 1, size=self.batch)
+        specs = [d.cfg["specs"][i] for i in traj]
+        pins = [d.cfg["pins"][i] for i in traj]
+        nn = d.nodes
+        idx = torch.from_numpy((traj[:, None] * nn + np.arange(nn)[None, :]).reshape(-1)).to(self.device)
+        st = torch.from_numpy(np.repeat(start, nn)).to(self.device)
+        x0 = d.x[st, idx].contiguous()
+        v0 = d.v[st, idx].contiguous()
+        tg = torch.stack([d.x[st + s, idx] for s in range(1, self.unroll + 1)]).contiguous()
+        return specs, pins, x0, v0, tg
+
+    def step(self) -> float:
+        specs, pins, x0, v0, tg = self.sample()
+        cb = ClothBatch(specs, pins, device=self.device)
+        cb.set_state(x0, v0)
+        self.net.set_weights(self.w)
+        loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
+        self.t += 1
+        adam_step(self.w, g, self.m, self.v, self.t, lr=self.lr, n=N_PARAMS)
+        cb.close()
+        return float(loss.item())
