@@ -277,6 +277,40 @@ int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* by
  * d_work: cloth_net_workspace_size() bytes. */
 int cloth_step_net(cloth_ctx* ctx, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream);
 
+/* Network rollout with the plain step as fallback and judge (Fig. 2: the
+ * framework couples the network with the physics-based simulator).
+ *  steps: steps to run.  check_every: every check_every-th step (0 = never)
+ *    both steps start from the same state; cloth b's residual r_b is the
+ *    largest |x_net - x_plain| over its nodes (m), and if r_b exceeds
+ *    residual_bound the cloth is switched to the plain step for the rest of
+ *    the rollout (the switch persists until cloth_reset_modes) and takes the
+ *    plain result of that step.
+ *  graph_chunk: steps per captured CUDA graph (rounded up to a whole number
+ *    of check periods and an even count; 0 = no graph). */
+typedef struct {
+    int32_t steps;
+    int32_t check_every;
+    float residual_bound;
+    int32_t graph_chunk;
+} cloth_net_rollout_opts;
+
+/* Workspace of cloth_rollout_net (tile list and one scratch state). */
+int cloth_net_rollout_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* bytes);
+
+/* Network rollout under the options above.  Residual checks need a BF16
+ * (tensor-core) network (CLOTH_EUNSUPPORTED otherwise). */
+int cloth_rollout_net(cloth_ctx* ctx, const cloth_net* net, const cloth_net_rollout_opts* opts, void* d_work,
+                      size_t bytes, void* stream);
+
+/* Per-cloth step mode (0 = network, 1 = plain after a failed check) and the
+ * residual of the cloth's last check (m; for a switched cloth, the one that
+ * switched it), copied to device arrays of B entries; either pointer may be
+ * NULL.  Stream-ordered. */
+int cloth_modes(cloth_ctx* ctx, int32_t* d_mode, float* d_residual, void* stream);
+
+/* Switch every cloth back to the network step. */
+int cloth_reset_modes(cloth_ctx* ctx, void* stream);
+
 /* ------------------------------------------------------------------------
  * Training (Sec. 3.2.1, Eq. 8; Table 1)
  * ---------------------------------------------------------------------- */

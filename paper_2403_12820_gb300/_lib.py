@@ -43,6 +43,10 @@ class RolloutOpts(ctypes.Structure):
     _fields_ = [("steps", c_int32), ("graph_chunk", c_int32), ("d_record", c_void_p), ("record_every", c_int32)]
 
 
+class NetRolloutOpts(ctypes.Structure):
+    _fields_ = [("steps", c_int32), ("check_every", c_int32), ("residual_bound", c_float), ("graph_chunk", c_int32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "cloth_workspace_size": (c_int32, [c_int32, P(ClothGrid), P(c_size_t)]),
@@ -74,6 +78,10 @@ SIGNATURES = {
     "net_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_float,
                                 c_float, c_void_p]),
     "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
+    "cloth_net_rollout_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
+    "cloth_rollout_net": (c_int32, [c_void_p, c_void_p, P(NetRolloutOpts), c_void_p, c_size_t, c_void_p]),
+    "cloth_modes": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "cloth_reset_modes": (c_int32, [c_void_p, c_void_p]),
     "cloth_info": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
     "cloth_destroy": (None, [c_void_p]),
     "cloth_strerror": (ctypes.c_char_p, [c_int32]),

@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import ClothGrid, ClothParams, ClothPins, ClothSphere, RolloutOpts
+from ._lib import ClothGrid, ClothParams, ClothPins, ClothSphere, NetRolloutOpts, RolloutOpts
 
 
 def _stream_handle(stream: torch.cuda.Stream | None) -> ctypes.c_void_p:
@@ -141,6 +141,30 @@ class ClothBatch:
         """`steps` network steps (Fig. 2) with the given Net."""
         ws = self.net_workspace(net.precision)
         _lib.call("cloth_step_net", self.handle, net.handle, int(steps), _ptr(ws), ws.numel(), self._s())
+
+    def rollout_net(self, net, steps: int, check_every: int = 0, residual_bound: float = 0.0,
+                    graph_chunk: int = 0) -> None:
+        """Network rollout (Fig. 2); every `check_every`-th step the plain step
+        judges it and cloths whose largest node difference exceeds
+        `residual_bound` (m) switch to the plain step."""
+        n = ctypes.c_size_t()
+        _lib.call("cloth_net_rollout_workspace_size", self.handle, int(net.precision), ctypes.byref(n))
+        ws = getattr(self, "_roll_ws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._roll_ws = ws
+        o = NetRolloutOpts(int(steps), int(check_every), float(residual_bound), int(graph_chunk))
+        _lib.call("cloth_rollout_net", self.handle, net.handle, ctypes.byref(o), _ptr(ws), ws.numel(), self._s())
+
+    def modes(self) -> tuple[torch.Tensor, torch.Tensor]:
+        """(mode (B,) int32: 0 network, 1 plain; residual of the last check (B,) m)."""
+        m = torch.empty(self.B, dtype=torch.int32, device=self.device)
+        r = torch.empty(self.B, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_modes", self.handle, _ptr(m), _ptr(r), self._s())
+        return m, r
+
+    def reset_modes(self) -> None:
+        _lib.call("cloth_reset_modes", self.handle, self._s())
 
     def train_loss(self, net, S: int, targets: torch.Tensor, alpha: float = 0.5, g_norm: float = 9.81,
                    grad_w: torch.Tensor | None = None):

@@ -34,7 +34,7 @@ int64_t units_for(const cloth_grid* g, int B, int seg_rows)
 }
 
 struct Layout {
-    size_t desc, units, pins, state[2], status, total;
+    size_t desc, units, pins, state[2], status, ctl, total;
     int64_t state_floats, pin_words, max_units;
 };
 
@@ -57,6 +57,7 @@ Layout make_layout(int B, const cloth_grid* g)
     L.state[0] = off; off = align_up(off + sizeof(float) * floats, kAlign);
     L.state[1] = off; off = align_up(off + sizeof(float) * floats, kAlign);
     L.status = off;   off = align_up(off + 64, kAlign);
+    L.ctl = off;      off = align_up(off + 12 * (size_t)B, kAlign);   // modes, residuals, last residuals
     L.total = off;
     return L;
 }
@@ -110,12 +111,16 @@ struct cloth_ctx {
     std::vector<NetGroup> groups;      // network step: cloths grouped by size
     int64_t group_max_nodes = 0;       // largest group's node count
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
+    int lists_kind = -1;                   // which list it holds (network precision)
 
     ClothDesc* d_desc() const { return reinterpret_cast<ClothDesc*>(ws + L.desc); }
     WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
     uint32_t* d_pins() const { return reinterpret_cast<uint32_t*>(ws + L.pins); }
     float* d_state(int k) const { return reinterpret_cast<float*>(ws + L.state[k]); }
     int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
+    int32_t* d_mode() const { return reinterpret_cast<int32_t*>(ws + L.ctl); }
+    float* d_resid() const { return reinterpret_cast<float*>(ws + L.ctl) + B; }
+    float* d_last() const { return reinterpret_cast<float*>(ws + L.ctl) + 2 * B; }
 };
 
 namespace {
@@ -154,9 +159,26 @@ int pick_seg_rows(const cloth_ctx* c)
     return 8;
 }
 
+// Plain step from src into dst; with `mode`, only cloths in plain mode.
+int launch_plain(cloth_ctx* c, const float* src, float* dst, const int32_t* mode, cudaStream_t s)
+{
+    StepArgs a{};
+    a.desc = c->d_desc();
+    a.units = c->d_units();
+    a.n_units = c->n_units;
+    a.src = src;
+    a.dst = dst;
+    a.pinmask = c->d_pins();
+    a.status = c->d_status();
+    a.mode = mode;
+    if (c->damp) CK(launch_plain_step_damp(a, false, c->grid, c->block, s));
+    else CK(launch_plain_step(a, false, c->grid, c->block, s));
+    return CLOTH_OK;
+}
+
 int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s)
 {
-    StepArgs a;
+    StepArgs a{};
     a.desc = c->d_desc();
     a.units = c->d_units();
     a.n_units = c->n_units;
@@ -225,10 +247,11 @@ int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wor
     const std::vector<int4> tiles = tc_tiles(c);
     if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
     int4* d_tiles = static_cast<int4*>(d_work);
-    if (c->lists_written != d_work) {
+    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_BF16) {
         CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         c->lists_written = d_work;
+        c->lists_kind = CLOTH_NET_BF16;
     }
     const int grid = std::min<int>((int)tiles.size(), c->sm_count);
     for (int st = 0; st < steps; ++st) {
@@ -361,6 +384,117 @@ int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32
     return CLOTH_OK;
 }
 
+int cloth_net_rollout_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
+{
+    if (!c || !bytes) return CLOTH_EINVAL;
+    if (precision != CLOTH_NET_BF16) return cloth_net_workspace_size(c, precision, bytes);
+    size_t tiles = 0;
+    int rc = cloth_net_workspace_size(c, precision, &tiles);
+    if (rc) return rc;
+    *bytes = align_up(tiles, kAlign) + (c->L.state[1] - c->L.state[0]);   // + one scratch state buffer
+    return CLOTH_OK;
+}
+
+int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollout_opts* o, void* d_work, size_t bytes,
+                      void* stream)
+{
+    if (!c || !net || !o || !d_work || o->steps < 0 || o->check_every < 0 || o->graph_chunk < 0) return CLOTH_EINVAL;
+    if (o->check_every > 0 && !(o->residual_bound >= 0.f)) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (net->precision != CLOTH_NET_BF16) {
+        if (o->check_every > 0) return CLOTH_EUNSUPPORTED;
+        return cloth_step_net(c, net, o->steps, d_work, bytes, stream);
+    }
+    size_t need = 0;
+    int rc = cloth_net_rollout_workspace_size(c, CLOTH_NET_BF16, &need);
+    if (rc) return rc;
+    if (bytes < need) return CLOTH_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    const std::vector<int4> tiles = tc_tiles(c);
+    int4* d_tiles = static_cast<int4*>(d_work);
+    float* scratch = reinterpret_cast<float*>(static_cast<char*>(d_work) + align_up(sizeof(int4) * tiles.size(), kAlign));
+    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_BF16) {
+        CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        c->lists_written = d_work;
+        c->lists_kind = CLOTH_NET_BF16;
+    }
+    const int grid = std::min<int>((int)tiles.size(), c->sm_count);
+    const int ce = o->check_every;
+    auto one_step = [&](int st, cudaStream_t ss) -> int {
+        const float* src = c->d_state(c->cur);
+        float* dst = c->d_state(c->cur ^ 1);
+        if (ce > 0 && st % ce == 0) {
+            // both steps from the same state: plain into dst, network into the
+            // scratch buffer, then keep, or latch to plain, per cloth
+            int r = launch_plain(c, src, dst, nullptr, ss);
+            if (r) return r;
+            CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, scratch,
+                                  c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
+            CK(launch_fallback_check(c->d_desc(), c->B, c->max_nodes, c->d_mode(), c->d_resid(), c->d_last(),
+                                     o->residual_bound, scratch, dst, ss));
+        } else {
+            int r = launch_plain(c, src, dst, c->d_mode(), ss);
+            if (r) return r;
+            CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, dst,
+                                  c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
+        }
+        c->cur ^= 1;
+        return CLOTH_OK;
+    };
+    // graph chunks hold a whole number of check periods and an even number of
+    // steps, so every replay starts on a check step with the same buffer
+    int chunk = o->graph_chunk;
+    if (chunk > 0) {
+        const int period = ce > 0 ? (ce % 2 ? 2 * ce : ce) : 2;
+        chunk = (chunk + period - 1) / period * period;
+    }
+    int done = 0;
+    if (chunk > 0 && o->steps >= chunk) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        const int cur0 = c->cur;
+        int r = CLOTH_OK;
+        for (int i = 0; i < chunk && r == CLOTH_OK; ++i) r = one_step(i, c->cap);
+        const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        c->cur = cur0;
+        if (r) { if (g) cudaGraphDestroy(g); return r; }
+        if (e != cudaSuccess) return cuda_fail(e);
+        const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return cuda_fail(e2);
+        cudaError_t e3 = cudaSuccess;
+        while (o->steps - done >= chunk && e3 == cudaSuccess) {
+            e3 = cudaGraphLaunch(ge, s);
+            done += chunk;
+        }
+        cudaGraphExecDestroy(ge);
+        if (e3 != cudaSuccess) return cuda_fail(e3);
+    }
+    for (; done < o->steps; ++done) {
+        const int r = one_step(done, s);
+        if (r) return r;
+    }
+    return CLOTH_OK;
+}
+
+int cloth_modes(cloth_ctx* c, int32_t* d_mode, float* d_residual, void* stream)
+{
+    if (!c) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d_mode) CK(cudaMemcpyAsync(d_mode, c->d_mode(), sizeof(int32_t) * c->B, cudaMemcpyDeviceToDevice, s));
+    if (d_residual) CK(cudaMemcpyAsync(d_residual, c->d_last(), sizeof(float) * c->B, cudaMemcpyDeviceToDevice, s));
+    return CLOTH_OK;
+}
+
+int cloth_reset_modes(cloth_ctx* c, void* stream)
+{
+    if (!c) return CLOTH_EINVAL;
+    CK(cudaMemsetAsync(c->ws + c->L.ctl, 0, 12 * (size_t)c->B, static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
@@ -384,12 +518,13 @@ int cloth_step_net(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(d_work);
     int32_t* lists = reinterpret_cast<int32_t*>(ws + w.lists);
-    if (c->lists_written != d_work) {
+    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_FP32) {
         std::vector<int32_t> all;
         for (const auto& g : c->groups) all.insert(all.end(), g.cloths.begin(), g.cloths.end());
         CK(cudaMemcpyAsync(lists, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         c->lists_written = d_work;
+        c->lists_kind = CLOTH_NET_FP32;
     }
     float* t1 = reinterpret_cast<float*>(ws + w.t1);
     float* t2 = reinterpret_cast<float*>(ws + w.t2);
@@ -511,7 +646,7 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
         e = cudaMemcpyAsync(c->d_pins(), pinmask.data(), sizeof(uint32_t) * L.pin_words, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[0], 0, L.state[1] - L.state[0], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[1], 0, L.status - L.state[1], s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.status, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.status, 0, L.total - L.status, s);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) rc = cuda_fail(e);
     if (rc == CLOTH_OK) rc = set_work(c, pick_seg_rows(c), s);

@@ -17,6 +17,8 @@ constexpr int kStrip = 120;
 constexpr int kPitchAlign = 4;
 // Device status word bits (include/cloth.h: CLOTH_STATUS_*).
 constexpr int kStatusNonfinite = 1, kStatusTimeout = 2;
+// Per-cloth step mode of a network rollout (include/cloth.h: cloth_modes).
+constexpr int32_t kModeNet = 0, kModePlain = 1;
 
 // Per-cloth descriptor in device memory (built on the host at create).
 struct __align__(16) ClothDesc {
@@ -57,6 +59,7 @@ struct StepArgs {
     const uint32_t* pinmask;
     float* force_out;     // forces-only mode: packed ABI layout
     int32_t* status;
+    const int32_t* mode;  // if set, only cloths in plain mode are stepped
 };
 
 // Launchers (plain_step.cu, state.cu).
@@ -66,6 +69,8 @@ cudaError_t launch_set_state(const ClothDesc* desc, int32_t B, int64_t total_nod
                              const float* x, const float* v, float* state, cudaStream_t s);
 cudaError_t launch_get_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,
                              const float* state, float* x, float* v, cudaStream_t s);
+cudaError_t launch_fallback_check(const ClothDesc* desc, int B, int64_t max_nodes, int32_t* mode, float* resid,
+                                  float* last, float bound, const float* net, float* dst, cudaStream_t s);
 cudaError_t launch_topology(const ClothDesc* desc, int32_t b, int32_t rows, int32_t cols, uint16_t* mask,
                             cudaStream_t s);
 

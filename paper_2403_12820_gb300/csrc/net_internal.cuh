@@ -73,7 +73,7 @@ int net_tc_tile_cols();
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s);
 cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDesc* desc, const int4* tiles, int n_tiles,
                                const float* src, float* dst, const uint32_t* pinmask, int32_t* status, int grid,
-                               cudaStream_t s);
+                               cudaStream_t s, const int32_t* mode = nullptr);
 cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
                                   int32_t* status, int grid, cudaStream_t s);
 

@@ -103,6 +103,7 @@ struct TcArgs {
     const float* src;
     float* dst;
     const uint32_t* pinmask;
+    const int32_t* mode;  // if set, only cloths in network mode are stepped
     // cell mode: z [N][6][H][W] -> a [N][3][H][W]
     const float* z;
     float* a;
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         int y0, x0, H, W, n = 0;
         if constexpr (STEP) {
             const int4 t = A.tiles[tile];
+            if (A.mode && A.mode[t.x] != kModeNet) continue;   // uniform over the CTA
             if (tid == 0) *sD = A.desc[t.x];
             y0 = t.y; x0 = t.z;
             __syncthreads();
@@ -507,7 +509,7 @@ cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 
 cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDesc* desc, const int4* tiles, int n_tiles,
                                const float* src, float* dst, const uint32_t* pinmask, int32_t* status, int grid,
-                               cudaStream_t s)
+                               cudaStream_t s, const int32_t* mode)
 {
     TcArgs a{};
     a.wpack = static_cast<const uint4*>(wpack);
@@ -519,6 +521,7 @@ cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDes
     a.src = src;
     a.dst = dst;
     a.pinmask = pinmask;
+    a.mode = mode;
     net_tc_kernel<true><<<grid, NTH, kSmem, s>>>(a);
     return cudaGetLastError();
 }

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
 
     for (int u = gwarp; u < a.n_units; u += nwarps) {
         const WorkUnit wu = a.units[u];
+        if (a.mode && a.mode[wu.b] != kModePlain) continue;   // stepped by the network
         const ClothDesc& D = a.desc[wu.b];
         const int rows = D.rows, cols = D.cols, pitch = D.pitch;
         const int64_t stride = D.plane_stride;
