@@ -50,6 +50,22 @@ struct __align__(16) WorkUnit {
 __host__ __device__ constexpr int col_slot(int j) { return j == 1 ? 2 : (j == 2 ? 1 : j); }
 __host__ __device__ constexpr int col_pos(int c) { return (c & ~3) + col_slot(c & 3); }
 
+// Hardware reciprocal square root and reciprocal with subnormals flushed:
+// squared spring lengths and |d| + L are never subnormal for a cloth, and the
+// flush drops the subnormal range fix-up around each approximation.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct StepArgs {
     const ClothDesc* desc;
     const WorkUnit* units;

@@ -103,10 +103,10 @@ __device__ __forceinline__ f2 spring2(const f2 (&ui)[3], const f2 (&uj)[3], f2 h
     d[2] = duz;
     num = fma2(duz, duz, num);                       // |d|^2 - L^2
     const f2 q = add2(num, L2);                      // |d|^2
-    const f2 rq = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+    const f2 rq = make_float2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
     const f2 den = fma2(q, rq, L);                   // |d| + L
     const f2 t = mul2(mul2(k, num), rq);
-    f2 s = mul2(t, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)));
+    f2 s = mul2(t, make_float2(rcp_ftz(den.x), rcp_ftz(den.y)));
     s.x = ok0 ? s.x : 0.f;
     s.y = ok1 ? s.y : 0.f;
     return s;

@@ -91,8 +91,8 @@ __device__ __forceinline__ float3 spring(float lx, float ly, float L, float k, f
     const float dx = lx + dux, dy = ly + duy, dz = duz;
     const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float num = fmaf(dux, dx + lx, fmaf(duy, dy + ly, duz * dz));   // |d|^2 - L^2
-    const float rq = rsqrtf(q);
-    float s = __fdividef(k * num * rq, fmaf(q, rq, L));
+    const float rq = rsqrt_ftz(q);
+    float s = k * num * rq * rcp_ftz(fmaf(q, rq, L));
     if constexpr (NC == 6) {
         const float dvx = j.c[3] - i.c[3], dvy = j.c[4] - i.c[4], dvz = j.c[5] - i.c[5];
         s = fmaf(mu * fmaf(dvx, dx, fmaf(dvy, dy, dvz * dz)), rq * rq, s);
