@@ -48,6 +48,10 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cnn", action="store_true")
     p.add_argument("--cnn-steps", type=int, default=200)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--mixed-steps", type=int, default=400)
+    p.add_argument("--no-train", action="store_true")
+    p.add_argument("--train-iters", type=int, default=20)
     return p.parse_args(argv)
 
 
@@ -321,6 +325,10 @@ def run_plain(args, rank, world, local):
 
     if not args.no_cnn:
         out["cnn"] = run_cnn(args, dev)
+    if not args.no_mixed:
+        out["mixed_fallback"] = run_mixed(args, dev)
+    if not args.no_train:
+        out["train"] = run_train(args, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -404,6 +412,89 @@ def run_cnn(args, dev):
         net.close()
     cp.close()
     return out
+
+
+def run_mixed(args, dev):
+    """Large mixed batch with the plain-step fallback: 16 cloths with sides
+    U{256..1024} over a sphere, BF16 network rollout captured in CUDA graphs,
+    every 10th step judged by one plain step from the same state; a cloth
+    whose largest node difference exceeds 1e-3 m switches to the plain step.
+    Reports node-steps/s of the checked rollout, of the unchecked network
+    rollout and of the plain rollout on the same cloths."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import BF16, Net
+
+    cfg = wl.mixed_batch()
+    h = cfg["specs"][0]["h"]
+    x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    nodes = cb.total_nodes
+    net = Net(cnn_blob(h), BF16, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = max(100, args.mixed_steps // 100 * 100)
+
+    def timed(fn):
+        cb.set_state(x0, v0)
+        cb.reset_modes()
+        fn(100)                       # warm-up, graph capture
+        cb.set_state(x0, v0)
+        cb.reset_modes()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return nodes * steps / (e0.elapsed_time(e1) / 1e3)
+
+    checked = timed(lambda k: cb.rollout_net(net, k, check_every=10, residual_bound=1e-3, graph_chunk=100))
+    mode, resid = cb.modes()
+    status = cb.status()
+    unchecked = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100))
+    plain = timed(lambda k: cb.rollout(k, graph_chunk=100))
+    out = {"workload": f"mixed_batch: 16 cloths, sides U{{256..1024}} (seed 1005), {nodes / 1e6:.2f}M nodes, "
+                       "sphere R = 0.3 w, BF16 network (Kaiming weights, seed 2003), FP32 state",
+           "value": checked, "unit": "node-steps/s", "steps": steps, "check_every": 10, "residual_bound_m": 1e-3,
+           "graph_chunk": 100, "switched_to_plain": int(mode.sum().item()),
+           "largest_residual_m": float(resid.max().item()), "network_unchecked": unchecked,
+           "plain_same_cloths": plain, "ratio_to_plain": checked / plain, "status_word": status,
+           "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
+    net.close()
+    cb.close()
+    return out
+
+
+def run_train(args, dev):
+    """Training iterations (Eq. 8, Table 1): 512 plain trajectories of 64 x 64
+    x 200 steps kept on the device; each iteration samples 64 windows,
+    unrolls 8 network steps with checkpoints, back-propagates through them
+    and takes one Adam step.  Host time (window sampling) included."""
+    import torch
+
+    from paper_2403_12820_gb300.train import Dataset, Trainer
+
+    t0 = time.perf_counter()
+    data = Dataset(count=512, n=64, steps=200, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    tr = Trainer(data, batch=64, unroll=8, device=dev)
+    losses = [tr.step() for _ in range(3)]
+    torch.cuda.synchronize()
+    iters = max(1, args.train_iters)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        losses.append(tr.step())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    win = 64 * 8 * data.nodes
+    return {"workload": "train: 512 trajectories of 64 x 64 x 200 plain steps (seed 1004); batch 64 windows, "
+                        "8-step unroll, Adam lr 1e-3, FP32",
+            "iters_per_s": iters / el, "windows_per_s": 64 * iters / el,
+            "unrolled_node_steps_per_s": win * iters / el, "iters": iters,
+            "dataset_generation_s": gen_s, "loss_first": losses[0], "loss_last": losses[-1]}
 
 
 def main(argv=None):
