@@ -31,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE_STEP = 48       # read u, v (24 B) + write u, v (24 B), FP32
+PLAIN_SOURCES = ["paper_2403_12820_gb300/csrc/plain_step.cu", "paper_2403_12820_gb300/csrc/cloth_internal.cuh"]
 CLOCK_FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -274,7 +275,7 @@ def run_plain(args, rank, world, local):
     hbm, _, peak_kind = peaks()
     launch_s = ms / 1e3 / args.steps          # one plain-step kernel per step
     achieved = BYTES_PER_NODE_STEP * nodes / launch_s / 1e9
-    traffic = ncu_traffic("plain_step_traffic", ["paper_2403_12820_gb300/csrc/plain_step.cu"], nodes)
+    traffic = ncu_traffic("plain_step_traffic", PLAIN_SOURCES, nodes)
 
     out = {
         "metric": "cloth node-steps/s (plain mass-spring step, batched cloths)",
