@@ -23,6 +23,8 @@
 // du = u_j - u_i, and its stretch uses |d|^2 - L^2 = du . (2 l + du) (since
 // |l| = L), so (|d| - L) / |d| = (|d|^2 - L^2) / (|d| (|d| + L)) carries no
 // cancellation in FP32.
+#include <type_traits>
+
 #include "cloth_internal.cuh"
 
 // Resident blocks of 128 threads per SM the register budget is sized for.
@@ -76,11 +78,13 @@ __device__ __forceinline__ f2 lat(f2 h, f2 h2, f2 nh)
 
 // Spring pair of lattice offset (SX, SY) h: returns s with f_i = s d and
 // f_j = -s d, d = x_j - x_i (written to d).  Eq. 1 with x_ij = x_i - x_j
-// gives s = k (|d| - L) / |d| = k (|d|^2 - L^2) / (|d| (|d| + L)).  A half
-// whose spring does not exist gets s = 0.
+// gives s = k (|d| - L) / |d| = k (|d|^2 - L^2) / (|d| (|d| + L)).  The
+// stiffness pair k is 0 in a half whose spring does not exist, which gives
+// s = 0 there: partner slots outside the grid hold finite values (zero fill
+// or the zeroed padding columns), so |d| is finite and non-zero.
 template <int SX, int SY>
 __device__ __forceinline__ f2 spring2(const f2 (&ui)[3], const f2 (&uj)[3], f2 h, f2 h2, f2 nh, f2 L, f2 L2, f2 k,
-                                      bool ok0, bool ok1, f2 (&d)[3])
+                                      f2 (&d)[3])
 {
     const f2 dux = sub2(uj[0], ui[0]), duy = sub2(uj[1], ui[1]), duz = sub2(uj[2], ui[2]);
     f2 num;
@@ -106,10 +110,7 @@ __device__ __forceinline__ f2 spring2(const f2 (&ui)[3], const f2 (&uj)[3], f2 h
     const f2 rq = make_float2(rsqrt_ftz(q.x), rsqrt_ftz(q.y));
     const f2 den = fma2(q, rq, L);                   // |d| + L
     const f2 t = mul2(mul2(k, num), rq);
-    f2 s = mul2(t, make_float2(rcp_ftz(den.x), rcp_ftz(den.y)));
-    s.x = ok0 ? s.x : 0.f;
-    s.y = ok1 ? s.y : 0.f;
-    return s;
+    return mul2(t, make_float2(rcp_ftz(den.x), rcp_ftz(den.y)));
 }
 
 __device__ __forceinline__ void acc2(f2 (&a)[3], f2 s, const f2 (&d)[3])
@@ -120,10 +121,21 @@ __device__ __forceinline__ void acc2(f2 (&a)[3], f2 s, const f2 (&d)[3])
 __device__ __forceinline__ float shup(float v) { return __shfl_up_sync(kFull, v, 1); }
 __device__ __forceinline__ float shdn(float v) { return __shfl_down_sync(kFull, v, 1); }
 
+// Stiffness pairs of the 12 springs a lane evaluates per row, indexed
+// [spring][thread]: E, 2E, N, 2N, NE, NW of pair A, then of pair B.
+enum { kE, kT, kN, k2N, kNE, kNW };
+constexpr int kSprings = 12;
+
 template <bool FORCES>
 __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepArgs a)
 {
+    // Each entry is k where the spring exists and 0 elsewhere: the column
+    // part is fixed per work unit, the row part changes only in the first
+    // and last rows of a cloth.  Kept in shared memory (12 KB per block)
+    // rather than registers or per-spring selects.
+    __shared__ float2 s_kp[kSprings][128];
     const int lane = threadIdx.x & 31;
+    float2* kp = &s_kp[0][threadIdx.x];
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const bool out_lane = lane >= 1 && lane <= 30;
@@ -144,14 +156,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             cm |= (col >= 0 && col < cols) ? (1u << j) : 0u;
         }
         auto bit = [&](int j) { return ((cm >> j) & 1u) != 0u; };
-        // column part of each spring pair's existence: own node and partner
-        const bool oA0 = bit(1), oA1 = bit(3), oB0 = bit(2), oB1 = bit(4);
-        const bool eA0 = oA0 && bit(2), eA1 = oA1 && bit(4);      // E, NE of A: partners c1, c3
-        const bool tA0 = oA0 && bit(3), tA1 = oA1 && bit(5);      // 2E of A: c2, c4
-        const bool wA0 = oA0 && bit(0), wA1 = oA1 && bit(2);      // NW of A: c-1, c1
-        const bool eB0 = oB0 && bit(3), eB1 = oB1 && bit(5);      // E, NE of B: c2, c4
-        const bool tB0 = oB0 && bit(4), tB1 = oB1 && bit(6);      // 2E of B: c3, c5
-        const bool wB0 = oB0 && bit(1), wB1 = oB1 && bit(3);      // NW of B: c0, c2
+        const bool oA0 = bit(1);   // column c4 exists
         // pressure masks: the E neighbour of each half exists (mE) / the W
         // neighbour exists (mW, stored negated)
         const f2 mEA = make_float2(bit(2) ? 1.f : 0.f, bit(4) ? 1.f : 0.f);
@@ -163,7 +168,30 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
         const f2 h = F2(hs), h2 = F2(2.f * hs), nh = F2(-hs);
         const f2 Ls = F2(hs), Ls2 = F2(hs * hs), Lb = F2(2.f * hs), Lb2 = F2(4.f * hs * hs);
         const f2 Ld = F2(1.41421356237309515f * hs), Ld2 = F2(2.f * hs * hs);
-        const f2 ks = F2(D.k_struct), ksh = F2(D.k_shear), kb = F2(D.k_bend);
+        // stiffness pairs with the column part of each spring's existence
+        // (own node and partner in the grid's columns); `rows_on` adds the
+        // row part: springs reaching row r+1 (N) or r+2 (2N) exist only
+        // while that row does, and a row above the grid owns none
+        auto set_kp = [&](bool row_r, bool row_r1, bool row_r2) {
+            auto pr = [&](float k, bool on, int o0, int p0, int o1, int p1) {
+                return make_float2(on && bit(o0) && bit(p0) ? k : 0.f, on && bit(o1) && bit(p1) ? k : 0.f);
+            };
+            const float ks = D.k_struct, ksh = D.k_shear, kb = D.k_bend;
+            const bool n1 = row_r && row_r1, n2 = row_r && row_r2;
+            kp[(0 + kE) * 128] = pr(ks, row_r, 1, 2, 3, 4);   // A: partners c1, c3
+            kp[(0 + kT) * 128] = pr(kb, row_r, 1, 3, 3, 5);   //    c2, c4
+            kp[(0 + kN) * 128] = pr(ks, n1, 1, 1, 3, 3);
+            kp[(0 + k2N) * 128] = pr(kb, n2, 1, 1, 3, 3);
+            kp[(0 + kNE) * 128] = pr(ksh, n1, 1, 2, 3, 4);
+            kp[(0 + kNW) * 128] = pr(ksh, n1, 1, 0, 3, 2);    //    c-1, c1
+            kp[(6 + kE) * 128] = pr(ks, row_r, 2, 3, 4, 5);   // B: partners c2, c4
+            kp[(6 + kT) * 128] = pr(kb, row_r, 2, 4, 4, 6);   //    c3, c5
+            kp[(6 + kN) * 128] = pr(ks, n1, 2, 2, 4, 4);
+            kp[(6 + k2N) * 128] = pr(kb, n2, 2, 2, 4, 4);
+            kp[(6 + kNE) * 128] = pr(ksh, n1, 2, 3, 4, 5);
+            kp[(6 + kNW) * 128] = pr(ksh, n1, 2, 1, 4, 3);    //    c0, c2
+        };
+        auto K = [&](int j) { return kp[j * 128]; };
         const f2 hxA = mul2(sub2(mEA, mWA), h), hxB = mul2(sub2(mEB, mWB), h);   // (mE + |mW|) h
         const float pq = D.p_quarter;
         const int64_t lane_off = D.plane_off + (lane_in ? c4 : 0);
@@ -172,115 +200,144 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
         auto rowp = [&](int q) { return src + (int64_t)(rok(q) ? q : 0) * pitch; };
 
         const int rb = wu.r0 - 2;
+        set_kp(rok(rb), rok(rb + 1), rok(rb + 2));
         Row2 P0, P1, P2, F0, F1, Fq;   // rows r, r+1, r+2; forces of r, r+1, r+2
         load2(P0, rowp(rb), stride, 0, lane_in && rok(rb));
         load2(P1, rowp(rb + 1), stride, 0, lane_in && rok(rb + 1));
         load2(P2, rowp(rb + 2), stride, 0, lane_in && rok(rb + 2));
         zero(F0); zero(F1); zero(Fq);
 
-        for (int r = rb; r < wu.r1; ++r) {
+        // One row of the march.  kMode 2: an output row.  The two warm-up
+        // rows above the unit (kMode 0: r0 - 2, kMode 1: r0 - 1) only feed the
+        // accumulators of rows r0 and r0 + 1, so they evaluate only the springs
+        // that reach those rows (row r0 - 2: 2N; row r0 - 1: N, 2N, NE, NW) and
+        // the pressure of row r0; the output rows see the same contributions in
+        // the same order either way.
+        auto row = [&](auto mode_tag, const int r) {
+            constexpr int kMode = decltype(mode_tag)::value;
             // positions of row r+3 are needed next row; the velocity of row r
             // only at the end of this one: both loads have a row of work to land
             Row2 PN, V0;
             load2(PN, rowp(r + 3), stride, 0, lane_in && rok(r + 3));
-            const bool vout = r >= wu.r0 && rok(r) && out_lane;
-            load2(V0, rowp(r), stride, 3, lane_in && vout);
+            if constexpr (kMode == 2) load2(V0, rowp(r), stride, 3, lane_in && rok(r) && out_lane);
 
             const bool ok_r = rok(r), ok_r1 = rok(r + 1), ok_r2 = rok(r + 2);
-            const bool okN = ok_r && ok_r1, ok2N = ok_r && ok_r2;
+            // the row part of the stiffness pairs changes only at a cloth's
+            // first two rows (the top halo ends) and last two rows
+            if (r > rb && (r <= 0 || !ok_r2)) set_kp(ok_r, ok_r1, ok_r2);
             // assembled partner pairs (per component):
             //   X0 = (c2, c4) of row r, Y0 = (c3, c5) of row r,
             //   X1 = (c2, c4) of row r+1, Z1 = (c-1, c1) of row r+1
             f2 X0[3], Y0[3], X1[3], Z1[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                X0[c] = make_float2(P0.A[c].y, shdn(P0.A[c].x));
-                Y0[c] = make_float2(P0.B[c].y, shdn(P0.B[c].x));
-                X1[c] = make_float2(P1.A[c].y, shdn(P1.A[c].x));
-                Z1[c] = make_float2(shup(P1.B[c].y), P1.B[c].x);
+                if constexpr (kMode == 2) {
+                    X0[c] = make_float2(P0.A[c].y, shdn(P0.A[c].x));
+                    Y0[c] = make_float2(P0.B[c].y, shdn(P0.B[c].x));
+                }
+                if constexpr (kMode >= 1) {
+                    X1[c] = make_float2(P1.A[c].y, shdn(P1.A[c].x));
+                    Z1[c] = make_float2(shup(P1.B[c].y), P1.B[c].x);
+                }
             }
             f2 d[3], s;
             float sR0r[3] = {0.f, 0.f, 0.f}, sR1r[3] = {0.f, 0.f, 0.f};
             float sR0r1[3] = {0.f, 0.f, 0.f}, sL3r1[3] = {0.f, 0.f, 0.f};
 
             // ---- springs of the A pair (c0, c2)
-            s = spring2<1, 0>(P0.A, P0.B, h, h2, nh, Ls, Ls2, ks, ok_r && eA0, ok_r && eA1, d);      // E -> (c1, c3)
-            acc2(F0.A, s, d);
-            acc2(F0.B, mul2(s, F2(-1.f)), d);
-            s = spring2<2, 0>(P0.A, X0, h, h2, nh, Lb, Lb2, kb, ok_r && tA0, ok_r && tA1, d);        // 2E -> (c2, c4)
-            acc2(F0.A, s, d);
+            if constexpr (kMode == 2) {
+                s = spring2<1, 0>(P0.A, P0.B, h, h2, nh, Ls, Ls2, K(0 + kE), d);      // E -> (c1, c3)
+                acc2(F0.A, s, d);
+                acc2(F0.B, mul2(s, F2(-1.f)), d);
+                s = spring2<2, 0>(P0.A, X0, h, h2, nh, Lb, Lb2, K(0 + kT), d);        // 2E -> (c2, c4)
+                acc2(F0.A, s, d);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const f2 f = mul2(s, d[c]);
-                F0.A[c].y -= f.x;
-                sR0r[c] += f.y;
+                for (int c = 0; c < 3; ++c) {
+                    const f2 f = mul2(s, d[c]);
+                    F0.A[c].y -= f.x;
+                    sR0r[c] += f.y;
+                }
             }
-            s = spring2<0, 1>(P0.A, P1.A, h, h2, nh, Ls, Ls2, ks, okN && oA0, okN && oA1, d);        // N
-            acc2(F0.A, s, d);
-            acc2(F1.A, mul2(s, F2(-1.f)), d);
-            s = spring2<0, 2>(P0.A, P2.A, h, h2, nh, Lb, Lb2, kb, ok2N && oA0, ok2N && oA1, d);      // 2N
+            if constexpr (kMode >= 1) {
+                s = spring2<0, 1>(P0.A, P1.A, h, h2, nh, Ls, Ls2, K(0 + kN), d);        // N
+                acc2(F0.A, s, d);
+                acc2(F1.A, mul2(s, F2(-1.f)), d);
+            }
+            s = spring2<0, 2>(P0.A, P2.A, h, h2, nh, Lb, Lb2, K(0 + k2N), d);          // 2N
             acc2(F0.A, s, d);
             acc2(Fq.A, mul2(s, F2(-1.f)), d);
-            s = spring2<1, 1>(P0.A, P1.B, h, h2, nh, Ld, Ld2, ksh, okN && eA0, okN && eA1, d);       // NE -> (c1, c3)
-            acc2(F0.A, s, d);
-            acc2(F1.B, mul2(s, F2(-1.f)), d);
-            s = spring2<-1, 1>(P0.A, Z1, h, h2, nh, Ld, Ld2, ksh, okN && wA0, okN && wA1, d);        // NW -> (c-1, c1)
-            acc2(F0.A, s, d);
+            if constexpr (kMode >= 1) {
+                s = spring2<1, 1>(P0.A, P1.B, h, h2, nh, Ld, Ld2, K(0 + kNE), d);       // NE -> (c1, c3)
+                acc2(F0.A, s, d);
+                acc2(F1.B, mul2(s, F2(-1.f)), d);
+                s = spring2<-1, 1>(P0.A, Z1, h, h2, nh, Ld, Ld2, K(0 + kNW), d);        // NW -> (c-1, c1)
+                acc2(F0.A, s, d);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const f2 f = mul2(s, d[c]);
-                sL3r1[c] += f.x;
-                F1.B[c].x -= f.y;
+                for (int c = 0; c < 3; ++c) {
+                    const f2 f = mul2(s, d[c]);
+                    sL3r1[c] += f.x;
+                    F1.B[c].x -= f.y;
+                }
             }
             // ---- springs of the B pair (c1, c3)
-            s = spring2<1, 0>(P0.B, X0, h, h2, nh, Ls, Ls2, ks, ok_r && eB0, ok_r && eB1, d);        // E -> (c2, c4)
-            acc2(F0.B, s, d);
+            if constexpr (kMode == 2) {
+                s = spring2<1, 0>(P0.B, X0, h, h2, nh, Ls, Ls2, K(6 + kE), d);        // E -> (c2, c4)
+                acc2(F0.B, s, d);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const f2 f = mul2(s, d[c]);
-                F0.A[c].y -= f.x;
-                sR0r[c] += f.y;
-            }
-            s = spring2<2, 0>(P0.B, Y0, h, h2, nh, Lb, Lb2, kb, ok_r && tB0, ok_r && tB1, d);        // 2E -> (c3, c5)
-            acc2(F0.B, s, d);
+                for (int c = 0; c < 3; ++c) {
+                    const f2 f = mul2(s, d[c]);
+                    F0.A[c].y -= f.x;
+                    sR0r[c] += f.y;
+                }
+                s = spring2<2, 0>(P0.B, Y0, h, h2, nh, Lb, Lb2, K(6 + kT), d);        // 2E -> (c3, c5)
+                acc2(F0.B, s, d);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const f2 f = mul2(s, d[c]);
-                F0.B[c].y -= f.x;
-                sR1r[c] += f.y;
+                for (int c = 0; c < 3; ++c) {
+                    const f2 f = mul2(s, d[c]);
+                    F0.B[c].y -= f.x;
+                    sR1r[c] += f.y;
+                }
             }
-            s = spring2<0, 1>(P0.B, P1.B, h, h2, nh, Ls, Ls2, ks, okN && oB0, okN && oB1, d);        // N
-            acc2(F0.B, s, d);
-            acc2(F1.B, mul2(s, F2(-1.f)), d);
-            s = spring2<0, 2>(P0.B, P2.B, h, h2, nh, Lb, Lb2, kb, ok2N && oB0, ok2N && oB1, d);      // 2N
+            if constexpr (kMode >= 1) {
+                s = spring2<0, 1>(P0.B, P1.B, h, h2, nh, Ls, Ls2, K(6 + kN), d);        // N
+                acc2(F0.B, s, d);
+                acc2(F1.B, mul2(s, F2(-1.f)), d);
+            }
+            s = spring2<0, 2>(P0.B, P2.B, h, h2, nh, Lb, Lb2, K(6 + k2N), d);          // 2N
             acc2(F0.B, s, d);
             acc2(Fq.B, mul2(s, F2(-1.f)), d);
-            s = spring2<1, 1>(P0.B, X1, h, h2, nh, Ld, Ld2, ksh, okN && eB0, okN && eB1, d);         // NE -> (c2, c4)
-            acc2(F0.B, s, d);
+            if constexpr (kMode >= 1) {
+                s = spring2<1, 1>(P0.B, X1, h, h2, nh, Ld, Ld2, K(6 + kNE), d);         // NE -> (c2, c4)
+                acc2(F0.B, s, d);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const f2 f = mul2(s, d[c]);
-                F1.A[c].y -= f.x;
-                sR0r1[c] += f.y;
+                for (int c = 0; c < 3; ++c) {
+                    const f2 f = mul2(s, d[c]);
+                    F1.A[c].y -= f.x;
+                    sR0r1[c] += f.y;
+                }
+                s = spring2<-1, 1>(P0.B, P1.A, h, h2, nh, Ld, Ld2, K(6 + kNW), d);      // NW -> (c0, c2)
+                acc2(F0.B, s, d);
+                acc2(F1.A, mul2(s, F2(-1.f)), d);
             }
-            s = spring2<-1, 1>(P0.B, P1.A, h, h2, nh, Ld, Ld2, ksh, okN && wB0, okN && wB1, d);      // NW -> (c0, c2)
-            acc2(F0.B, s, d);
-            acc2(F1.A, mul2(s, F2(-1.f)), d);
 
             // ---- reactions that cross to the neighbour lanes
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                F0.A[c].x -= shup(sR0r[c]);
-                F0.B[c].x -= shup(sR1r[c]);
-                F1.A[c].x -= shup(sR0r1[c]);
-                F1.B[c].y -= shdn(sL3r1[c]);
+                if constexpr (kMode == 2) {
+                    F0.A[c].x -= shup(sR0r[c]);
+                    F0.B[c].x -= shup(sR1r[c]);
+                }
+                if constexpr (kMode >= 1) {
+                    F1.A[c].x -= shup(sR0r1[c]);
+                    F1.B[c].y -= shdn(sL3r1[c]);
+                }
             }
 
             // ---- pressure (Eq. 3) of row r+1, whose 4 cardinal neighbours lie
             // in rows r .. r+2.  With d'_n = (neighbour n exists)(x_n - x_i),
             // the sum over the ordered pairs of d'_E x d'_N + d'_N x d'_W +
             // d'_W x d'_S + d'_S x d'_E equals (d'_E - d'_W) x (d'_N - d'_S).
-            if (pq != 0.f && ok_r1) {
+            if (kMode >= 1 && pq != 0.f && ok_r1) {
                 const f2 bN = F2(ok_r2 ? 1.f : 0.f), bSn = F2(ok_r ? -1.f : 0.f);
                 const f2 hy = mul2(sub2(bN, bSn), h);
                 const f2 pq2 = F2(pq);
@@ -307,7 +364,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             }
 
             // ---- row r is complete: gravity and drag (Eq. 4), update (Eq. 5)
-            if (r >= wu.r0 && ok_r && out_lane && oA0) {
+            if (kMode == 2 && ok_r && out_lane && oA0) {
                 const f2 ndrag = F2(-D.drag);
                 const f2 mg[3] = {F2(D.m * D.gx), F2(D.m * D.gy), F2(D.m * D.gz)};
                 Row2 f;
@@ -403,7 +460,10 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             // slide the window down one row
             P0 = P1; P1 = P2; P2 = PN;
             F0 = F1; F1 = Fq; zero(Fq);
-        }
+        };
+        row(std::integral_constant<int, 0>{}, rb);
+        row(std::integral_constant<int, 1>{}, rb + 1);
+        for (int r = wu.r0; r < wu.r1; ++r) row(std::integral_constant<int, 2>{}, r);
     }
 }
 
