@@ -134,8 +134,13 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
     // and last rows of a cloth.  Kept in shared memory (12 KB per block)
     // rather than registers or per-spring selects.
     __shared__ float2 s_kp[kSprings][128];
+    // Pressure coefficients of the lane's pairs A and B (Eq. 3, scaled by
+    // p/4): E and W masks, the own-node weight -(mE + mW), and the lattice
+    // part of d'_E - d'_W along x.
+    __shared__ float2 s_pc[8][128];
     const int lane = threadIdx.x & 31;
     float2* kp = &s_kp[0][threadIdx.x];
+    float2* pc = &s_pc[0][threadIdx.x];
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const bool out_lane = lane >= 1 && lane <= 30;
@@ -157,14 +162,21 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
         }
         auto bit = [&](int j) { return ((cm >> j) & 1u) != 0u; };
         const bool oA0 = bit(1);   // column c4 exists
-        // pressure masks: the E neighbour of each half exists (mE) / the W
-        // neighbour exists (mW, stored negated)
-        const f2 mEA = make_float2(bit(2) ? 1.f : 0.f, bit(4) ? 1.f : 0.f);
-        const f2 mWA = make_float2(bit(0) ? -1.f : 0.f, bit(2) ? -1.f : 0.f);
-        const f2 mEB = make_float2(bit(3) ? 1.f : 0.f, bit(5) ? 1.f : 0.f);
-        const f2 mWB = make_float2(bit(1) ? -1.f : 0.f, bit(3) ? -1.f : 0.f);
-
         const float hs = D.h;
+        const float pq = D.p_quarter;
+        {
+            // pressure masks: the E neighbour of each half exists (mE) / the
+            // W neighbour exists (mW, stored negated)
+            auto put = [&](int j, float e0, float e1, float w0, float w1) {
+                pc[(4 * j + 0) * 128] = make_float2(pq * e0, pq * e1);
+                pc[(4 * j + 1) * 128] = make_float2(-pq * w0, -pq * w1);
+                pc[(4 * j + 2) * 128] = make_float2(pq * (w0 - e0), pq * (w1 - e1));
+                pc[(4 * j + 3) * 128] = make_float2(pq * (e0 + w0) * hs, pq * (e1 + w1) * hs);
+            };
+            auto m = [&](int j) { return bit(j) ? 1.f : 0.f; };
+            put(0, m(2), m(4), m(0), m(2));   // A = (c0, c2): E c1, c3; W c-1, c1
+            put(1, m(3), m(5), m(1), m(3));   // B = (c1, c3): E c2, c4; W c0, c2
+        }
         const f2 h = F2(hs), h2 = F2(2.f * hs), nh = F2(-hs);
         const f2 Ls = F2(hs), Ls2 = F2(hs * hs), Lb = F2(2.f * hs), Lb2 = F2(4.f * hs * hs);
         const f2 Ld = F2(1.41421356237309515f * hs), Ld2 = F2(2.f * hs * hs);
@@ -192,8 +204,6 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             kp[(6 + kNW) * 128] = pr(ksh, n1, 2, 1, 4, 3);    //    c0, c2
         };
         auto K = [&](int j) { return kp[j * 128]; };
-        const f2 hxA = mul2(sub2(mEA, mWA), h), hxB = mul2(sub2(mEB, mWB), h);   // (mE + |mW|) h
-        const float pq = D.p_quarter;
         const int64_t lane_off = D.plane_off + (lane_in ? c4 : 0);
         const float* src = a.src + lane_off;
         auto rok = [&](int q) { return (unsigned)q < (unsigned)rows; };
@@ -337,10 +347,11 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             // in rows r .. r+2.  With d'_n = (neighbour n exists)(x_n - x_i),
             // the sum over the ordered pairs of d'_E x d'_N + d'_N x d'_W +
             // d'_W x d'_S + d'_S x d'_E equals (d'_E - d'_W) x (d'_N - d'_S).
+            // d'_E - d'_W = mE x_E + mW x_W - (mE + mW) x_i (mW negated): for
+            // an interior node x_i drops out and it is x_E - x_W + 2 h x^.
             if (kMode >= 1 && pq != 0.f && ok_r1) {
-                const f2 bN = F2(ok_r2 ? 1.f : 0.f), bSn = F2(ok_r ? -1.f : 0.f);
-                const f2 hy = mul2(sub2(bN, bSn), h);
-                const f2 pq2 = F2(pq);
+                const float fN = ok_r2 ? 1.f : 0.f, fS = ok_r ? 1.f : 0.f;
+                const f2 bN = F2(fN), bSn = F2(-fS), cN = F2(fS - fN), hy = F2((fN + fS) * hs);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const f2* ui = half == 0 ? P1.A : P1.B;
@@ -348,32 +359,34 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                     const f2* uW = half == 0 ? Z1 : P1.A;
                     const f2* uN = half == 0 ? P2.A : P2.B;
                     const f2* uS = half == 0 ? P0.A : P0.B;
-                    const f2 mE = half == 0 ? mEA : mEB, mW = half == 0 ? mWA : mWB;
-                    const f2 hx = half == 0 ? hxA : hxB;
-                    const f2 ex = fma2(mE, sub2(uE[0], ui[0]), fma2(mW, sub2(uW[0], ui[0]), hx));
-                    const f2 ey = fma2(mE, sub2(uE[1], ui[1]), mul2(mW, sub2(uW[1], ui[1])));
-                    const f2 ez = fma2(mE, sub2(uE[2], ui[2]), mul2(mW, sub2(uW[2], ui[2])));
-                    const f2 nx = fma2(bN, sub2(uN[0], ui[0]), mul2(bSn, sub2(uS[0], ui[0])));
-                    const f2 ny = fma2(bN, sub2(uN[1], ui[1]), fma2(bSn, sub2(uS[1], ui[1]), hy));
-                    const f2 nz = fma2(bN, sub2(uN[2], ui[2]), mul2(bSn, sub2(uS[2], ui[2])));
+                    // e = (p/4)(d'_E - d'_W), n = d'_N - d'_S
+                    const f2 qE = pc[(4 * half + 0) * 128], qW = pc[(4 * half + 1) * 128];
+                    const f2 qC = pc[(4 * half + 2) * 128], qh = pc[(4 * half + 3) * 128];
+                    const f2 ex = fma2(qE, uE[0], fma2(qW, uW[0], fma2(qC, ui[0], qh)));
+                    const f2 ey = fma2(qE, uE[1], fma2(qW, uW[1], mul2(qC, ui[1])));
+                    const f2 ez = fma2(qE, uE[2], fma2(qW, uW[2], mul2(qC, ui[2])));
+                    const f2 nx = fma2(bN, uN[0], fma2(bSn, uS[0], mul2(cN, ui[0])));
+                    const f2 ny = fma2(bN, uN[1], fma2(bSn, uS[1], fma2(cN, ui[1], hy)));
+                    const f2 nz = fma2(bN, uN[2], fma2(bSn, uS[2], mul2(cN, ui[2])));
+                    auto neg = [](f2 v) { return make_float2(-v.x, -v.y); };
                     f2* Fh = half == 0 ? F1.A : F1.B;
-                    Fh[0] = fma2(pq2, sub2(mul2(ey, nz), mul2(ez, ny)), Fh[0]);
-                    Fh[1] = fma2(pq2, sub2(mul2(ez, nx), mul2(ex, nz)), Fh[1]);
-                    Fh[2] = fma2(pq2, sub2(mul2(ex, ny), mul2(ey, nx)), Fh[2]);
+                    Fh[0] = fma2(ey, nz, fma2(neg(ez), ny, Fh[0]));
+                    Fh[1] = fma2(ez, nx, fma2(neg(ex), nz, Fh[1]));
+                    Fh[2] = fma2(ex, ny, fma2(neg(ey), nx, Fh[2]));
                 }
             }
 
             // ---- row r is complete: gravity and drag (Eq. 4), update (Eq. 5)
             if (kMode == 2 && ok_r && out_lane && oA0) {
-                const f2 ndrag = F2(-D.drag);
-                const f2 mg[3] = {F2(D.m * D.gx), F2(D.m * D.gy), F2(D.m * D.gz)};
-                Row2 f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    f.A[c] = add2(F0.A[c], fma2(ndrag, V0.A[c], mg[c]));
-                    f.B[c] = add2(F0.B[c], fma2(ndrag, V0.B[c], mg[c]));
-                }
                 if constexpr (FORCES) {
+                    const f2 ndrag = F2(-D.drag);
+                    const f2 mg[3] = {F2(D.m * D.gx), F2(D.m * D.gy), F2(D.m * D.gz)};
+                    Row2 f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        f.A[c] = add2(F0.A[c], fma2(ndrag, V0.A[c], mg[c]));
+                        f.B[c] = add2(F0.B[c], fma2(ndrag, V0.B[c], mg[c]));
+                    }
                     float* o = a.force_out + (D.abi_off + (int64_t)r * cols + c4) * 3;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -383,12 +396,17 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                         if (c4 + 3 < cols) o[3 * 3 + c] = f.B[c].y;
                     }
                 } else {
+                    // v' = v + dt/m (f_int + f_p - d v + m g) = dt/m (f_int + f_p)
+                    //      + ((1 - d dt/m) v + dt g): Eq. 4-5 with the
+                    // constant terms folded
                     const f2 dt = F2(D.dt), dtm = F2(D.dt * D.inv_m);
+                    const f2 keep = F2(1.f - D.dt * D.inv_m * D.drag);
+                    const f2 dtg[3] = {F2(D.dt * D.gx), F2(D.dt * D.gy), F2(D.dt * D.gz)};
                     Row2 un, vn;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        vn.A[c] = fma2(dtm, f.A[c], V0.A[c]);
-                        vn.B[c] = fma2(dtm, f.B[c], V0.B[c]);
+                        vn.A[c] = fma2(dtm, F0.A[c], fma2(keep, V0.A[c], dtg[c]));
+                        vn.B[c] = fma2(dtm, F0.B[c], fma2(keep, V0.B[c], dtg[c]));
                     }
                     const uint32_t pw = __ldg(a.pinmask + D.pin_off + (int64_t)r * D.pin_wpr + (c4 >> 5));
                     const unsigned pb = (pw >> (c4 & 31)) & 0xfu;
@@ -429,11 +447,11 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                             }
                         }
                     }
-                    // non-finite check over the 4 nodes (columns beyond the
-                    // grid hold finite values: their springs are all zero)
-                    f2 chk = add2(add2(un.A[0], un.A[1]), add2(un.A[2], vn.A[0]));
-                    chk = add2(chk, add2(add2(vn.A[1], vn.A[2]), add2(un.B[0], un.B[1])));
-                    chk = add2(chk, add2(add2(un.B[2], vn.B[0]), add2(vn.B[1], vn.B[2])));
+                    // non-finite check over the 4 nodes' positions (a NaN or
+                    // infinite velocity reaches u' = u + dt v' in this step;
+                    // columns beyond the grid hold finite values)
+                    f2 chk = add2(add2(un.A[0], un.A[1]), add2(un.A[2], un.B[0]));
+                    chk = add2(chk, add2(un.B[1], un.B[2]));
                     if (!isfinite(chk.x + chk.y)) atomicOr(a.status, 1);
                     float* dst = a.dst + lane_off + (int64_t)r * pitch;
                     if (c4 + 3 < cols) {
