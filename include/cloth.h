@@ -153,13 +153,24 @@ typedef struct {
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
 
-/* Launch shape of the plain step: the work list is cut into row segments of
- * `seg_rows` rows (>= 4; 0 keeps the current value) and the persistent grid
- * holds `warps_per_sm` warps per SM (0 keeps the current value).  Changes
- * only speed, never results.  Cached graphs are dropped. */
+/* Launch shape of the plain step.  Every warp of the launch runs a
+ * contiguous range of a work list of (cloth, 120-column strip, row segment)
+ * units:
+ *  seg_rows >= 4: strips cut into segments of that many rows, longest
+ *    first, dealt round-robin to the warps (the default, with a segment
+ *    length picked from the batch);
+ *  seg_rows = -1: balanced ranges, the strips' rows cut into equal shares,
+ *    one per warp;
+ *  seg_rows = 0 keeps the current choice.
+ * warps_per_sm (1..64) sets the warps of the launch to that many per SM;
+ * -1 restores the default (one warp per segment, or for balanced ranges as
+ * many warps as are resident at once); 0 keeps the current value.
+ * Changes only speed, never results.  Cached graphs are dropped.
+ * Synchronises `stream`. */
 int cloth_set_launch(cloth_ctx* ctx, int32_t seg_rows, int32_t warps_per_sm, void* stream);
 
-/* Current launch shape (seg_rows, warps_per_sm, number of work units). */
+/* Current launch shape: seg_rows (0 = balanced ranges), warps_per_sm (0 =
+ * the default), number of work units. */
 int cloth_get_launch(const cloth_ctx* ctx, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units);
 
 /* Topology as the step kernels see it: for every node of cloth b, bit s of

@@ -19,6 +19,7 @@ namespace {
 thread_local int g_last_cuda = 0;
 
 constexpr int kMinSegRows = 4;       // smallest row segment the work list may use
+constexpr int kMaxWarps = 1 << 16;   // bound on the warps of one plain-step launch
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -34,7 +35,7 @@ int64_t units_for(const cloth_grid* g, int B, int seg_rows)
 }
 
 struct Layout {
-    size_t desc, units, pins, state[2], status, ctl, total;
+    size_t desc, units, warp_first, pins, state[2], status, ctl, total;
     int64_t state_floats, pin_words, max_units;
 };
 
@@ -49,10 +50,13 @@ Layout make_layout(int B, const cloth_grid* g)
     }
     L.state_floats = floats;
     L.pin_words = words;
-    L.max_units = units_for(g, B, kMinSegRows);
+    // fixed segments split every strip; balanced ranges split each strip at
+    // most once per warp
+    L.max_units = std::max<int64_t>(units_for(g, B, kMinSegRows), units_for(g, B, 1 << 30) + kMaxWarps);
     size_t off = 0;
     L.desc = off;     off = align_up(off + sizeof(ClothDesc) * B, kAlign);
     L.units = off;    off = align_up(off + sizeof(WorkUnit) * L.max_units, kAlign);
+    L.warp_first = off; off = align_up(off + sizeof(int32_t) * (kMaxWarps + 1), kAlign);
     L.pins = off;     off = align_up(off + sizeof(uint32_t) * words, kAlign);
     L.state[0] = off; off = align_up(off + sizeof(float) * floats, kAlign);
     L.state[1] = off; off = align_up(off + sizeof(float) * floats, kAlign);
@@ -102,8 +106,9 @@ struct cloth_ctx {
     int cur = 0;                       // state buffer holding the current state
     int seg_rows = 16;
     int n_units = 0;
+    int n_warps = 0;                   // warps of one plain-step launch that have work
     int grid = 0, block = 128;
-    int warps_per_sm = 16;
+    int warps_per_sm = 0;              // 0: the plain-step kernel's occupancy
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
@@ -115,6 +120,7 @@ struct cloth_ctx {
 
     ClothDesc* d_desc() const { return reinterpret_cast<ClothDesc*>(ws + L.desc); }
     WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
+    int32_t* d_warp_first() const { return reinterpret_cast<int32_t*>(ws + L.warp_first); }
     uint32_t* d_pins() const { return reinterpret_cast<uint32_t*>(ws + L.pins); }
     float* d_state(int k) const { return reinterpret_cast<float*>(ws + L.state[k]); }
     int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
@@ -125,34 +131,77 @@ struct cloth_ctx {
 
 namespace {
 
-// Build and upload the work list for `seg_rows`-row segments; pick the grid
-// as a multiple of the SM count (persistent warps loop over the list).
+// Build and upload the work list of the plain step; every warp of the
+// launch runs a contiguous range of it.
+//  seg_rows > 0 (default: picked by pick_seg_rows): strips cut into
+//    segments of `seg_rows` rows, longest first, dealt round-robin to the
+//    warps.  By default there is one warp per segment: the blocks beyond
+//    those resident start as earlier ones finish, which balances the tail,
+//    and the warps of a block take horizontally adjacent strips of the same
+//    rows (contiguous memory).
+//  seg_rows = 0: balanced ranges.  The strips' rows, laid end to end, are
+//    cut into equal shares, one per warp (by default as many as are resident
+//    at once), so every warp marches the same number of rows (+- 1); a share
+//    that spans two strips restarts its window once.
 int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
 {
-    seg_rows = std::max(seg_rows, kMinSegRows);
-    std::vector<WorkUnit> u;
-    for (int b = 0; b < c->B; ++b) {
-        const int rows = c->grids[b].rows, cols = c->grids[b].cols;
-        for (int r0 = 0; r0 < rows; r0 += seg_rows)
-            for (int c0 = 0; c0 < cols; c0 += kStrip) u.push_back(WorkUnit{b, c0, r0, std::min(rows, r0 + seg_rows)});
-    }
-    // longest units first so the tail of the persistent loop is short
-    std::stable_sort(u.begin(), u.end(), [](const WorkUnit& a, const WorkUnit& b) { return (a.r1 - a.r0) > (b.r1 - b.r0); });
-    if ((int64_t)u.size() > c->L.max_units) return CLOTH_EINVAL;
-    CK(cudaMemcpyAsync(c->d_units(), u.data(), sizeof(WorkUnit) * u.size(), cudaMemcpyHostToDevice, s));
-    c->seg_rows = seg_rows;
-    c->n_units = (int)u.size();
     const int warps_per_block = c->block / 32;
-    const int resident = c->sm_count * c->warps_per_sm;   // warps resident at once
-    const int want = std::min<int64_t>(c->n_units, resident);
-    c->grid = std::max(1, (want + warps_per_block - 1) / warps_per_block);
+    int wps = c->warps_per_sm;
+    if (wps <= 0 && seg_rows <= 0) wps = std::max(1, plain_step_blocks_per_sm(c->damp, c->block)) * warps_per_block;
+    const int W = wps > 0 ? std::max(1, std::min(kMaxWarps, c->sm_count * wps)) : kMaxWarps;
+    std::vector<WorkUnit> u;
+    std::vector<int32_t> first;
+    if (seg_rows > 0) {
+        seg_rows = std::max(seg_rows, kMinSegRows);
+        std::vector<WorkUnit> all;
+        for (int b = 0; b < c->B; ++b) {
+            const int rows = c->grids[b].rows, cols = c->grids[b].cols;
+            for (int r0 = 0; r0 < rows; r0 += seg_rows)
+                for (int c0 = 0; c0 < cols; c0 += kStrip) all.push_back(WorkUnit{b, c0, r0, std::min(rows, r0 + seg_rows)});
+        }
+        std::stable_sort(all.begin(), all.end(),
+                         [](const WorkUnit& a, const WorkUnit& b) { return (a.r1 - a.r0) > (b.r1 - b.r0); });
+        const int nw = std::min<int>(W, (int)all.size());
+        for (int w = 0; w < nw; ++w) {
+            first.push_back((int32_t)u.size());
+            for (size_t i = (size_t)w; i < all.size(); i += (size_t)nw) u.push_back(all[i]);
+        }
+    } else {
+        int64_t total = 0;
+        for (int b = 0; b < c->B; ++b)
+            total += (int64_t)c->grids[b].rows * ((c->grids[b].cols + kStrip - 1) / kStrip);
+        const int64_t q = std::max<int64_t>(1, (total + W - 1) / W);   // rows per warp
+        int64_t pos = 0;
+        for (int b = 0; b < c->B; ++b) {
+            const int rows = c->grids[b].rows, cols = c->grids[b].cols;
+            for (int c0 = 0; c0 < cols; c0 += kStrip)
+                for (int r = 0; r < rows;) {
+                    const int64_t w = pos / q;
+                    const int take = (int)std::min<int64_t>(rows - r, (w + 1) * q - pos);
+                    while ((int64_t)first.size() <= w) first.push_back((int32_t)u.size());
+                    u.push_back(WorkUnit{b, c0, r, r + take});
+                    r += take;
+                    pos += take;
+                }
+        }
+    }
+    first.push_back((int32_t)u.size());
+    if ((int64_t)u.size() > c->L.max_units || (int)first.size() - 1 > kMaxWarps) return CLOTH_EINVAL;
+    CK(cudaMemcpyAsync(c->d_units(), u.data(), sizeof(WorkUnit) * u.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_warp_first(), first.data(), sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice, s));
+    c->seg_rows = seg_rows > 0 ? seg_rows : 0;
+    c->n_units = (int)u.size();
+    c->n_warps = (int)first.size() - 1;
+    c->grid = std::max(1, (c->n_warps + warps_per_block - 1) / warps_per_block);
+    // the host vectors go out of scope: the copies must be done
+    CK(cudaStreamSynchronize(s));
     return CLOTH_OK;
 }
 
 int pick_seg_rows(const cloth_ctx* c)
 {
-    // enough units to cover every SM a few times over, but segments long
-    // enough that the 2 warm-up rows stay a small fraction
+    // enough segments to cover every SM a dozen times, but long enough that
+    // the 2 warm-up rows stay a small fraction
     const int64_t target = (int64_t)c->sm_count * 12;
     for (int R : {64, 32, 16, 8})
         if (units_for(c->grids.data(), c->B, R) >= target) return R;
@@ -165,7 +214,8 @@ int launch_plain(cloth_ctx* c, const float* src, float* dst, const int32_t* mode
     StepArgs a{};
     a.desc = c->d_desc();
     a.units = c->d_units();
-    a.n_units = c->n_units;
+    a.warp_first = c->d_warp_first();
+    a.n_warps = c->n_warps;
     a.src = src;
     a.dst = dst;
     a.pinmask = c->d_pins();
@@ -181,7 +231,8 @@ int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s
     StepArgs a{};
     a.desc = c->d_desc();
     a.units = c->d_units();
-    a.n_units = c->n_units;
+    a.warp_first = c->d_warp_first();
+    a.n_warps = c->n_warps;
     a.src = c->d_state(c->cur);
     a.dst = c->d_state(c->cur ^ 1);
     a.pinmask = c->d_pins();
@@ -749,12 +800,13 @@ int cloth_rollout_plain(cloth_ctx* c, const cloth_rollout_opts* o, void* stream)
 
 int cloth_set_launch(cloth_ctx* c, int32_t seg_rows, int32_t warps_per_sm, void* stream)
 {
-    if (!c || seg_rows < 0 || (seg_rows > 0 && seg_rows < kMinSegRows) || warps_per_sm < 0 || warps_per_sm > 64)
+    if (!c || seg_rows < -1 || (seg_rows > 0 && seg_rows < kMinSegRows) || warps_per_sm < -1 || warps_per_sm > 64)
         return CLOTH_EINVAL;
-    if (warps_per_sm > 0) c->warps_per_sm = warps_per_sm;
+    if (warps_per_sm != 0) c->warps_per_sm = warps_per_sm > 0 ? warps_per_sm : 0;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
-    const int rc = set_work(c, seg_rows > 0 ? seg_rows : c->seg_rows, static_cast<cudaStream_t>(stream));
+    const int seg = seg_rows > 0 ? seg_rows : (seg_rows < 0 ? 0 : c->seg_rows);
+    const int rc = set_work(c, seg, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     return CLOTH_OK;

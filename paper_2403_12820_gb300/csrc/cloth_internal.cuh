@@ -68,8 +68,9 @@ __device__ __forceinline__ float rcp_ftz(float x)
 
 struct StepArgs {
     const ClothDesc* desc;
-    const WorkUnit* units;
-    int32_t n_units;
+    const WorkUnit* units;      // grouped by warp: warp w runs units [warp_first[w], warp_first[w + 1])
+    const int32_t* warp_first;
+    int32_t n_warps;
     const float* src;
     float* dst;
     const uint32_t* pinmask;
@@ -81,6 +82,8 @@ struct StepArgs {
 // Launchers (plain_step.cu, state.cu).
 cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
 cudaError_t launch_plain_step_damp(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
+// Blocks of `block` threads of the plain-step kernel resident per SM.
+int plain_step_blocks_per_sm(bool damp, int block);
 cudaError_t launch_set_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,
                              const float* x, const float* v, float* state, cudaStream_t s);
 cudaError_t launch_get_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,

@@ -142,10 +142,10 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
     float2* kp = &s_kp[0][threadIdx.x];
     float2* pc = &s_pc[0][threadIdx.x];
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const bool out_lane = lane >= 1 && lane <= 30;
 
-    for (int u = gwarp; u < a.n_units; u += nwarps) {
+    if (gwarp >= a.n_warps) return;
+    for (int u = a.warp_first[gwarp]; u < a.warp_first[gwarp + 1]; ++u) {
         const WorkUnit wu = a.units[u];
         if (a.mode && a.mode[wu.b] != kModePlain) continue;   // stepped by the network
         const ClothDesc& D = a.desc[wu.b];
@@ -486,6 +486,13 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
 }
 
 }  // namespace
+
+int plain_step_blocks_per_sm_nodamp(int block)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, plain_step_kernel<false>, block, 0) != cudaSuccess) return 0;
+    return n;
+}
 
 cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s)
 {

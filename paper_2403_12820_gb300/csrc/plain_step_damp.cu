@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(128, 3) plain_step_damp_kernel(StepArgs a)
     constexpr int NC = DAMP ? 6 : 3;
     const int lane = threadIdx.x & 31;
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const bool out_lane = lane >= 1 && lane <= 30;
 
-    for (int u = gwarp; u < a.n_units; u += nwarps) {
+    if (gwarp >= a.n_warps) return;
+    for (int u = a.warp_first[gwarp]; u < a.warp_first[gwarp + 1]; ++u) {
         const WorkUnit wu = a.units[u];
         if (a.mode && a.mode[wu.b] != kModePlain) continue;   // stepped by the network
         const ClothDesc& D = a.desc[wu.b];
@@ -335,6 +335,17 @@ __global__ void __launch_bounds__(128, 3) plain_step_damp_kernel(StepArgs a)
 }
 
 }  // namespace
+
+int plain_step_blocks_per_sm_nodamp(int block);   // plain_step.cu
+
+int plain_step_blocks_per_sm(bool damp, int block)
+{
+    if (!damp) return plain_step_blocks_per_sm_nodamp(block);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, plain_step_damp_kernel<true, false>, block, 0) != cudaSuccess)
+        return 0;
+    return n;
+}
 
 cudaError_t launch_plain_step_damp(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s)
 {

@@ -168,6 +168,24 @@ def test_graph_rollout_and_record_match_single_steps():
     assert torch.equal(rec[2], xa)
 
 
+@pytest.mark.parametrize("mu", [0.0, 0.02])
+def test_launch_shapes_give_identical_results(mu):
+    """Every launch shape (balanced ranges, fixed segments, few or many
+    warps) runs the same arithmetic per node: bitwise equal states."""
+    specs, pins, xs, vs = uneven_batch(seed=13, mu=mu)
+    ref = make(specs, pins, xs, vs)
+    assert ref.get_launch()[1] == 0   # default warp count
+    ref.step(12)
+    xr, vr = ref.get_state()
+    for seg, w in [(4, 1), (8, 4), (32, 12), (-1, 1), (-1, 64), (-1, -1), (5, 3), (16, -1)]:
+        cb = make(specs, pins, xs, vs)
+        cb.set_launch(seg, w)
+        cb.step(12)
+        x, v = cb.get_state()
+        assert torch.equal(x, xr) and torch.equal(v, vr), (seg, w)
+        assert cb.status() == 0
+
+
 def test_bitwise_deterministic():
     specs, pins, xs, vs = uneven_batch(seed=12)
     outs = []
