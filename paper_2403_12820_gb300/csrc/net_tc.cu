@@ -27,6 +27,9 @@
 //   5. per output node: L = bL + sum_tap q_tap at the tap's neighbour,
 //      a = out_scale (L + N + D); then (step mode) v <- C(v + dt (a + f_p /
 //      m)), u <- u + dt v, sphere contact, store.
+// Tiles are pipelined: the input of tile t+1 is staged (into the other FP32
+// tile buffer) while the layer-2 MMAs of tile t run, and the final pass of
+// tile t runs while the layer-1 MMAs of tile t+1 do.
 // Every wait on the tensor cores is bounded; a timeout sets a status bit
 // and the kernel returns after releasing its tensor memory.
 #include <cuda_bf16.h>
@@ -64,7 +67,8 @@ constexpr int kPack = kB1 + kB2p + kB2x;
 
 // FP32 u, v of the output nodes and their 1-node halo, for the update
 constexpr int UH = R + 2, UW = WO + 2;
-// q is kept for the valid layer-2 positions only: (R+2) x (WO+2)
+// q is kept for the valid layer-2 positions only: (R+2) x (WO+2), one plane
+// per value
 constexpr int NQ = (R + 2) * (WO + 2);
 
 // shared memory map (bytes)
@@ -72,12 +76,14 @@ constexpr int oB1 = 0, oB2p = oB1 + kB1, oB2x = oB2p + kB2p;
 constexpr int oIn = oB2x + kB2x;                    // input [N0BUF][8] bf16: in_scale (u, v), 0, 0
 constexpr int oL1p = oIn + N0BUF * 16;              // phi1 [plane][N1BUF][8] bf16
 constexpr int oL1x = oL1p + 4 * N1BUF * 16;         // xi1
-constexpr int oQ = oL1x + 4 * N1BUF * 16;           // q [NQ][27] float
-constexpr int oU = oQ + NQ * 27 * 4;                // u, v [6][UH][UW] float
-constexpr int oND = oU + 6 * UH * UW * 4;           // N + D, two halves [2][R * WO][3] float
-constexpr int oPar = oND + 2 * R * WO * 3 * 4;      // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
-constexpr int oDesc = oPar + (256 + 16) * 4;        // the tile's cloth descriptor
-constexpr int oBar = oDesc + (int)sizeof(ClothDesc);   // mbarriers: layer 1 [C1], layer 2 [2]; TMEM address
+constexpr int oQ = oL1x + 4 * N1BUF * 16;           // q [27][NQ] float
+constexpr int kUFloats = 6 * UH * UW;
+constexpr int oU = oQ + NQ * 27 * 4;                // u, v [2 tiles][6][UH][UW] float
+constexpr int oND = oU + 2 * kUFloats * 4;          // N + D [R * WO][3] float (both channel halves added)
+constexpr int oPar = oND + R * WO * 3 * 4;          // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
+constexpr int oDesc = oPar + (256 + 16) * 4;        // the two tiles' cloth descriptors
+constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
+constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers: layer 1 [C1], layer 2 [2]; TMEM address
 constexpr int kNumBars = C1 + 2;
 constexpr int oTmemSlot = oBar + 8 * kNumBars;
 constexpr int kSmem = oTmemSlot + 16;
@@ -152,6 +158,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     float* sOut = sBL + 3;
     float* sIns = sOut + 3;
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
+    uint8_t* sPin = sm + oPin;
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
     auto bar1 = [&](int c) { return sbase + oBar + 8u * (uint32_t)c; };
     auto bar2 = [&](int b) { return sbase + oBar + 8u * (uint32_t)(C1 + b); };
@@ -167,6 +174,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         sOut[tid] = A.w[kOffOuts + tid];
     }
     if (tid < 6) sIns[tid] = A.w[kOffIns + tid];
+    for (int e = tid; e < R * WO * 3; e += NTH) sND[e] = 0.f;
     // input rows N0 .. N0BUF are read only by junk layer-1 positions; keep them zero
     for (int e = tid; e < N0BUF - N0; e += NTH) reinterpret_cast<uint4*>(sm + oIn)[N0 + e] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
@@ -225,138 +233,291 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         tc::mma_commit(bar2(c2 & 1));
     };
 
-    for (int tile = blockIdx.x; tile < n_tiles && !timed_out; tile += gridDim.x) {
-        // ---- tile geometry
-        int y0, x0, H, W, n = 0;
+    // ---- per-tile pieces
+    struct Geo {
+        int y0, x0, H, W, n;
+        const float* src;
+        int64_t cs, rs;
+        int cloth;
+        const uint32_t* pin;   // the cloth's pin mask, pin_wpr words per row
+        int pin_wpr;
+    };
+    auto geo = [&](int tile) {
+        Geo g{};
         if constexpr (STEP) {
             const int4 t = A.tiles[tile];
-            if (A.mode && A.mode[t.x] != kModeNet) continue;   // uniform over the CTA
-            if (tid == 0) *sD = A.desc[t.x];
-            y0 = t.y; x0 = t.z;
-            __syncthreads();
-            H = sD->rows; W = sD->cols;
+            const ClothDesc& d = A.desc[t.x];
+            g.cloth = t.x; g.y0 = t.y; g.x0 = t.z; g.H = d.rows; g.W = d.cols;
+            g.src = A.src + d.plane_off; g.cs = d.plane_stride; g.rs = d.pitch;
+            g.pin = A.pinmask + d.pin_off; g.pin_wpr = d.pin_wpr;
         } else {
-            n = tile / (A.tiles_y * A.tiles_x);
+            g.n = tile / (A.tiles_y * A.tiles_x);
             const int r = tile % (A.tiles_y * A.tiles_x);
-            y0 = (r / A.tiles_x) * R; x0 = (r % A.tiles_x) * WO; H = A.H; W = A.W;
+            g.y0 = (r / A.tiles_x) * R; g.x0 = (r % A.tiles_x) * WO; g.H = A.H; g.W = A.W;
+            g.src = A.z + (int64_t)g.n * 6 * A.H * A.W; g.cs = (int64_t)A.H * A.W; g.rs = A.W;
         }
-        int64_t cstride, rstride;
-        const float* srcp;
+        return g;
+    };
+    // this CTA's tiles: every gridDim.x-th, skipping cloths not in network mode
+    auto skip = [&](int t) {
         if constexpr (STEP) {
-            srcp = A.src + sD->plane_off; cstride = sD->plane_stride; rstride = sD->pitch;
-        } else {
-            srcp = A.z + (int64_t)n * 6 * H * W; cstride = (int64_t)H * W; rstride = W;
+            if (A.mode)
+                while (t < n_tiles && A.mode[A.tiles[t].x] != kModeNet) t += gridDim.x;
         }
-        // ---- 1. input region as BF16: node (iy, ix) at iy * PT + ix holds
-        // (in_scale u, in_scale v, 0, 0), zero outside the grid; the raw u, v
-        // of the output nodes and their halo also go to the FP32 tile
-        if (worker) {
-            for (int j0 = tid; j0 < N0; j0 += NWORK) {
-                const int iy = j0 / PT, ix = j0 % PT;
-                const int y = y0 - 3 + iy, x = x0 - 3 + ix;
-                float raw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (y >= 0 && y < H && x >= 0 && x < W) {
-                    const float* p0 = srcp + (int64_t)y * rstride + (STEP ? col_pos(x) : x);
+        return t;
+    };
+
+    // 1. the input region as BF16: node (iy, ix) at iy * PT + ix holds
+    // (in_scale u, in_scale v, 0, 0), zero outside the grid; the raw u, v of
+    // the output nodes and their halo also go to FP32 tile buffer `buf`, and
+    // (step mode) the output nodes' pinned flags to sPin[buf].  Split into a
+    // load of input node j0 into registers and its store to shared memory,
+    // so the loads can be in flight while the thread waits for an MMA.
+    struct Raw {
+        float v[6];
+        uint32_t pin;     // the node's pin-mask word; its bit is picked at the store
+    };
+    auto stage_load = [&](const Geo& g, int j0, Raw& rw) {
+        const int iy = j0 / PT, ix = j0 % PT;
+        const int y = g.y0 - 3 + iy, x = g.x0 - 3 + ix;
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) raw[c] = __ldg(p0 + c * cstride);
-                }
-                float v[8];
+        for (int c = 0; c < 6; ++c) rw.v[c] = 0.f;
+        rw.pin = 0;
+        if (y >= 0 && y < g.H && x >= 0 && x < g.W) {
+            const float* p0 = g.src + (int64_t)y * g.rs + (STEP ? col_pos(x) : x);
 #pragma unroll
-                for (int c = 0; c < 6; ++c) v[c] = sIns[c] * raw[c];
-                v[6] = v[7] = 0.f;
-                reinterpret_cast<uint4*>(sm + oIn)[j0] = pack8(v);
-                const int uy = iy - 2, ux = ix - 2;
-                if (uy >= 0 && uy < UH && ux >= 0 && ux < UW)
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) sU[(c * UH + uy) * UW + ux] = raw[c];
+            for (int c = 0; c < 6; ++c) rw.v[c] = __ldg(p0 + c * g.cs);
+            if constexpr (STEP) {
+                const int oy = iy - 3, ox = ix - 3;
+                if (oy >= 0 && oy < R && ox >= 0 && ox < WO) rw.pin = __ldg(g.pin + (int64_t)y * g.pin_wpr + (x >> 5));
             }
+        }
+    };
+    auto stage_store = [&](const Geo& g, int buf, int j0, const Raw& rw) {
+        const int iy = j0 / PT, ix = j0 % PT;
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = sIns[c] * rw.v[c];
+        v[6] = v[7] = 0.f;
+        reinterpret_cast<uint4*>(sm + oIn)[j0] = pack8(v);
+        const int uy = iy - 2, ux = ix - 2;
+        if (uy >= 0 && uy < UH && ux >= 0 && ux < UW) {
+            float* sUb = sU + buf * kUFloats;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) sUb[(c * UH + uy) * UW + ux] = rw.v[c];
+        }
+        const int oy = iy - 3, ox = ix - 3;
+        if (STEP && oy >= 0 && oy < R && ox >= 0 && ox < WO)
+            sPin[buf * R * WO + oy * WO + ox] = (uint8_t)((rw.pin >> ((g.x0 + ox) & 31)) & 1u);
+    };
+    auto stage = [&](const Geo& g, int buf) {   // the whole region at once
+        if (STEP && tid == 0) sD[buf] = A.desc[g.cloth];
+        for (int j0 = tid; j0 < N0; j0 += NWORK) {
+            Raw rw;
+            stage_load(g, j0, rw);
+            stage_store(g, buf, j0, rw);
+        }
+    };
+    constexpr int kStageParts = (N0 + NWORK - 1) / NWORK;   // input nodes per worker
+    static_assert(kStageParts <= C2, "one staging part per layer-2 chunk");
+
+    // 2. layer 1 (Eq. 6) store: each chunk's phi1 / xi1 as BF16 as it
+    // completes (workers; false on a timeout)
+    auto repack = [&](const Geo& g) {
+        for (int c1 = 0; c1 < C1; ++c1) {
+            if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) return false;
+            tc::fence_after();
+            float r[32];
+            tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r);
+            tc::tmem_wait_ld();
+            const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
+            const int y = g.y0 - 2 + ry1, x = g.x0 - 2 + rx1;
+            const bool in = j1 < N1 && rx1 < WO + 4 && y >= 0 && y < g.H && x >= 0 && x < g.W;
+            if (j1 < N1BUF) {
+                uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float a8[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
+                    dstb[p * N1BUF + j1] = pack8(a8);
+                }
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        return true;
+    };
+
+    // 4. epilogue of layer-2 chunk c2 (TMEM buffer b): s = tanh(t), N + D
+    // over the channel half [16 half, +16) added into sND; q, the WL
+    // partial sums, into sQ (zero outside the cloth: WL's zero padding)
+    auto epilogue = [&](const Geo& g, int c2, int b) {
+        tc::fence_after();
+        const int j2 = c2 * 128 + quarter * 32 + lane;
+        const int ry2 = j2 / PT, rx2 = j2 % PT;
+        const int y = g.y0 - 1 + ry2, x = g.x0 - 1 + rx2;
+        const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < g.H && x >= 0 && x < g.W;
+        const int oy = ry2 - 1, ox = rx2 - 1;
+        const bool out_node = valid && oy >= 0 && oy < R && ox >= 0 && ox < WO;
+        const uint32_t col = lane_base + kL2Col + 96u * (uint32_t)b;
+        float t[16], xi[16], q[16];
+        tmem_ld16(col + 16 * half, t);
+        tmem_ld16(col + 64 + 16 * half, xi);
+        tmem_ld16(col + 32 + 16 * half, q);   // q_0..15 (half 0) or q_16..26 and padding (half 1)
+        tc::tmem_wait_ld();
+        if (j2 < N2 && rx2 < WO + 2) {
+            float* qr = sQ + 16 * half * NQ + ry2 * (WO + 2) + rx2;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < 11 || half == 0) qr[k * NQ] = valid ? q[k] : 0.f;
+        }
+        if (out_node) {
+            float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float sv = tc::tanh_approx(t[c]);
+                const float xs = xi[c] * sv;
+                const float4 w0 = sWND[2 * (16 * half + c)], w1 = sWND[2 * (16 * half + c) + 1];
+                nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
+                nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
+                nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
+            }
+            // the two halves' sums land on zero: x + y == y + x, so the
+            // result does not depend on their order
+            float* o = sND + (oy * WO + ox) * 3;
+            atomicAdd(o + 0, nd0);
+            atomicAdd(o + 1, nd1);
+            atomicAdd(o + 2, nd2);
+        }
+        tc::fence_before();
+    };
+
+    // 5. per output node: L, a, and (step mode) the update; sND is zeroed
+    // for the next tile (workers)
+    auto final_pass = [&](const Geo& g, int buf) {
+        const float* sUb = sU + buf * kUFloats;
+        for (int o = tid; o < R * WO; o += NWORK) {
+            const int oy = o / WO, ox = o % WO, y = g.y0 + oy, x = g.x0 + ox;
+            float acc[3];
+#pragma unroll
+            for (int co = 0; co < 3; ++co) {
+                float L = sBL[co];
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap)
+                    L += sQ[(tap * 3 + co) * NQ + (oy + tap / 3) * (WO + 2) + ox + tap % 3];
+                acc[co] = sOut[co] * (L + sND[o * 3 + co]);
+                sND[o * 3 + co] = 0.f;
+            }
+            if (y >= g.H || x >= g.W) continue;
+            if constexpr (!STEP) {
+#pragma unroll
+                for (int co = 0; co < 3; ++co) A.a[(((int64_t)g.n * 3 + co) * g.H + y) * g.W + x] = acc[co];
+            } else {
+                const ClothDesc& D = sD[buf];
+                auto U = [&](int ch, int yy, int xx) {   // from the FP32 tile
+                    return sUb[(ch * UH + yy - g.y0 + 1) * UW + xx - g.x0 + 1];
+                };
+                float u[3], v[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    u[c] = U(c, y, x);
+                    v[c] = U(3 + c, y, x);
+                }
+                if (D.p_quarter != 0.f) {
+                    const bool bE = x + 1 < g.W, bW = x > 0, bN = y + 1 < g.H, bS = y > 0;
+                    float e[3], nn[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        e[c] = (bE ? U(c, y, x + 1) - u[c] + (c == 0 ? D.h : 0.f) : 0.f) -
+                               (bW ? U(c, y, x - 1) - u[c] - (c == 0 ? D.h : 0.f) : 0.f);
+                        nn[c] = (bN ? U(c, y + 1, x) - u[c] + (c == 1 ? D.h : 0.f) : 0.f) -
+                                (bS ? U(c, y - 1, x) - u[c] - (c == 1 ? D.h : 0.f) : 0.f);
+                    }
+                    const float sc = D.p_quarter * D.inv_m;
+                    acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
+                    acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
+                    acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
+                }
+                const bool pinned = sPin[buf * R * WO + o] != 0;
+                float vn[3], un[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], v[c]);
+                    un[c] = fmaf(D.dt, vn[c], u[c]);
+                }
+                if (D.sph_on) {
+                    const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
+                    const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
+                    const float rz = un[2] - D.sph_cz;
+                    const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    if (dd < D.sph_r2 && dd > 0.f) {
+                        const float sc = D.sph_r * rsqrtf(dd);
+                        un[0] = fmaf(sc, rx, un[0] - rx);
+                        un[1] = fmaf(sc, ry, un[1] - ry);
+                        un[2] = fmaf(sc, rz, un[2] - rz);
+                        vn[0] = vn[1] = vn[2] = 0.f;
+                    }
+                }
+                if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
+                float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    out[c * D.plane_stride] = un[c];
+                    out[(3 + c) * D.plane_stride] = vn[c];
+                }
+            }
+        }
+    };
+
+    // ---- the pipeline.  Prologue: stage and run layer 1 of the first tile.
+    int tile = skip((int)blockIdx.x);
+    int buf = 0;
+    Geo g{};
+    if (tile < n_tiles) {
+        g = geo(tile);
+        if (worker) {
+            stage(g, 0);
             tc::fence_async_smem();
         }
         __syncthreads();
-
-        // ---- 2. layer 1 (Eq. 6): the issuer queues every chunk; the workers
-        // store each chunk's phi1 / xi1 as it completes
         if (issuer) issue_layer1();
         bool ok = true;
-        if (worker) {
-            for (int c1 = 0; c1 < C1; ++c1) {
-                if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) { ok = false; break; }
-                tc::fence_after();
-                float r[32];
-                tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r);
-                tc::tmem_wait_ld();
-                const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
-                const int y = y0 - 2 + ry1, x = x0 - 2 + rx1;
-                const bool in = j1 < N1 && rx1 < WO + 4 && y >= 0 && y < H && x >= 0 && x < W;
-                if (j1 < N1BUF) {
-                    uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        float a8[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
-                        dstb[p * N1BUF + j1] = pack8(a8);
-                    }
-                }
-            }
-            tc::fence_async_smem();
-            tc::fence_before();
-        }
+        if (worker) ok = repack(g);
         ph1 ^= 1u;
-        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        if (__syncthreads_or(!ok)) timed_out = true;
+    }
+    while (tile < n_tiles && !timed_out) {
+        const int tn = skip(tile + (int)gridDim.x);
+        const bool has_next = tn < n_tiles;
+        Geo gn{};
+        if (has_next) gn = geo(tn);
 
-        // ---- 3-4. layer 2 as implicit GEMM, double-buffered in TMEM: chunk
-        // c+1 runs while the workers read chunk c
+        // 3-4. layer 2 of this tile as implicit GEMM, double-buffered in TMEM
+        // (chunk c+1 runs while the workers read chunk c).  Each worker loads
+        // its input nodes of the next tile up front and stores one after each
+        // of the first chunks' epilogues, so the loads have the MMAs' time to
+        // land.
         if (issuer) {
             issue_layer2(0);
             if (C2 > 1) issue_layer2(1);
         }
+        if (STEP && has_next && tid == 0) sD[buf ^ 1] = A.desc[gn.cloth];
+        Raw rw[kStageParts];
+        if (worker && has_next) {
+#pragma unroll
+            for (int k = 0; k < kStageParts; ++k)
+                if (tid + k * NWORK < N0) stage_load(gn, tid + k * NWORK, rw[k]);
+        }
         for (int c2 = 0; c2 < C2; ++c2) {
             const int b = c2 & 1;
-            ok = true;
+            bool ok = true;
             if (worker) {
                 ok = tc::mbar_wait(bar2(b), ph2[b], kWaitLimit);
-                if (ok) {
-                    tc::fence_after();
-                    const int j2 = c2 * 128 + quarter * 32 + lane;
-                    const int ry2 = j2 / PT, rx2 = j2 % PT;
-                    const int y = y0 - 1 + ry2, x = x0 - 1 + rx2;
-                    const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < H && x >= 0 && x < W;
-                    const int oy = ry2 - 1, ox = rx2 - 1;
-                    const bool out_node = valid && oy >= 0 && oy < R && ox >= 0 && ox < WO;
-                    const uint32_t col = lane_base + kL2Col + 96u * (uint32_t)b;
-                    // s = tanh(t), N + D over the channel half [16 half, +16)
-                    float t[16], xi[16];
-                    tmem_ld16(col + 16 * half, t);
-                    tmem_ld16(col + 64 + 16 * half, xi);
-                    if (half == 1) {   // q: the WL partial sums, zero outside the cloth
-                        float q[32];
-                        tc::tmem_ld32(col + 32, q);
-                        tc::tmem_wait_ld();
-                        if (j2 < N2 && rx2 < WO + 2) {
-                            float* qr = sQ + (ry2 * (WO + 2) + rx2) * 27;
+                if (ok) epilogue(g, c2, b);
 #pragma unroll
-                            for (int k = 0; k < 27; ++k) qr[k] = valid ? q[k] : 0.f;
-                        }
-                    } else {
-                        tc::tmem_wait_ld();
-                    }
-                    if (out_node) {
-                        float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) {
-                            const float sv = tc::tanh_approx(t[c]);
-                            const float xs = xi[c] * sv;
-                            const float4 w0 = sWND[2 * (16 * half + c)], w1 = sWND[2 * (16 * half + c) + 1];
-                            nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
-                            nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
-                            nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
-                        }
-                        float* o = sND + (half * R * WO + oy * WO + ox) * 3;
-                        o[0] = nd0; o[1] = nd1; o[2] = nd2;
-                    }
-                    tc::fence_before();
-                }
+                for (int k = 0; k < kStageParts; ++k)   // register-indexed: k is a constant here
+                    if (k == c2 && has_next && tid + k * NWORK < N0) stage_store(gn, buf ^ 1, tid + k * NWORK, rw[k]);
             }
             ph2[b] ^= 1u;
             if (__syncthreads_or(!ok)) { timed_out = true; break; }
@@ -364,80 +525,20 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
         if (timed_out) break;
 
-        // ---- 5. per output node: L, a, and (step mode) the update
-        if (worker) {
-            for (int o = tid; o < R * WO; o += NWORK) {
-                const int oy = o / WO, ox = o % WO, y = y0 + oy, x = x0 + ox;
-                if (y >= H || x >= W) continue;
-                float acc[3];
-#pragma unroll
-                for (int co = 0; co < 3; ++co) {
-                    float L = sBL[co];
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap)
-                        L += sQ[((oy + tap / 3) * (WO + 2) + ox + tap % 3) * 27 + tap * 3 + co];
-                    acc[co] = sOut[co] * (L + sND[o * 3 + co] + sND[(R * WO + o) * 3 + co]);
-                }
-                if constexpr (!STEP) {
-#pragma unroll
-                    for (int co = 0; co < 3; ++co) A.a[(((int64_t)n * 3 + co) * H + y) * W + x] = acc[co];
-                } else {
-                    const ClothDesc& D = *sD;
-                    auto U = [&](int ch, int yy, int xx) {   // from the FP32 tile
-                        return sU[(ch * UH + yy - y0 + 1) * UW + xx - x0 + 1];
-                    };
-                    float u[3], v[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        u[c] = U(c, y, x);
-                        v[c] = U(3 + c, y, x);
-                    }
-                    if (D.p_quarter != 0.f) {
-                        const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
-                        float e[3], nn[3];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            e[c] = (bE ? U(c, y, x + 1) - u[c] + (c == 0 ? D.h : 0.f) : 0.f) -
-                                   (bW ? U(c, y, x - 1) - u[c] - (c == 0 ? D.h : 0.f) : 0.f);
-                            nn[c] = (bN ? U(c, y + 1, x) - u[c] + (c == 1 ? D.h : 0.f) : 0.f) -
-                                    (bS ? U(c, y - 1, x) - u[c] - (c == 1 ? D.h : 0.f) : 0.f);
-                        }
-                        const float sc = D.p_quarter * D.inv_m;
-                        acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
-                        acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
-                        acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
-                    }
-                    const bool pinned = (A.pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
-                    float vn[3], un[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], v[c]);
-                        un[c] = fmaf(D.dt, vn[c], u[c]);
-                    }
-                    if (D.sph_on) {
-                        const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
-                        const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
-                        const float rz = un[2] - D.sph_cz;
-                        const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        if (dd < D.sph_r2 && dd > 0.f) {
-                            const float sc = D.sph_r * rsqrtf(dd);
-                            un[0] = fmaf(sc, rx, un[0] - rx);
-                            un[1] = fmaf(sc, ry, un[1] - ry);
-                            un[2] = fmaf(sc, rz, un[2] - rz);
-                            vn[0] = vn[1] = vn[2] = 0.f;
-                        }
-                    }
-                    if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
-                    float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        out[c * D.plane_stride] = un[c];
-                        out[(3 + c) * D.plane_stride] = vn[c];
-                    }
-                }
-            }
-        }
+        // layer 1 of the next tile runs during this tile's final pass
+        if (worker) tc::fence_async_smem();   // the staged input, for the tensor cores
         __syncthreads();
+        if (issuer && has_next) issue_layer1();
+        bool ok = true;
+        if (worker) {
+            final_pass(g, buf);
+            if (has_next) ok = repack(gn);
+        }
+        if (has_next) ph1 ^= 1u;
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        tile = tn;
+        g = gn;
+        buf ^= 1;
     }
 
     // ---- tear-down: after a timeout, wait (bounded) for the MMAs in flight
