@@ -324,12 +324,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // 2. layer 1 (Eq. 6) store: each chunk's phi1 / xi1 as BF16 as it
     // completes (workers; false on a timeout)
     auto repack = [&](const Geo& g) {
-        for (int c1 = 0; c1 < C1; ++c1) {
-            if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) return false;
-            tc::fence_after();
-            float r[32];
-            tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r);
-            tc::tmem_wait_ld();
+        auto put = [&](int c1, const float (&r)[32]) {
             const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
             const int y = g.y0 - 2 + ry1, x = g.x0 - 2 + rx1;
             const bool in = j1 < N1 && rx1 < WO + 4 && y >= 0 && y < g.H && x >= 0 && x < g.W;
@@ -343,6 +338,19 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                     dstb[p * N1BUF + j1] = pack8(a8);
                 }
             }
+        };
+        // two chunks' tensor-memory loads in flight at a time
+        for (int c1 = 0; c1 < C1; c1 += 2) {
+            const bool two = c1 + 1 < C1;
+            if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) return false;
+            if (two && !tc::mbar_wait(bar1(c1 + 1), ph1, kWaitLimit)) return false;
+            tc::fence_after();
+            float r0[32], r1[32];
+            tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r0);
+            if (two) tc::tmem_ld32(lane_base + 64u * (uint32_t)(c1 + 1) + 32u * (uint32_t)half, r1);
+            tc::tmem_wait_ld();
+            put(c1, r0);
+            if (two) put(c1 + 1, r1);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -471,11 +479,16 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     };
 
     // ---- the pipeline.  Prologue: stage and run layer 1 of the first tile.
+    // The geometry of the tile after the current one is known one iteration
+    // ahead, so its loads have landed when its input is fetched.
     int tile = skip((int)blockIdx.x);
     int buf = 0;
-    Geo g{};
+    Geo g{}, gn{};
+    int tn = n_tiles;
     if (tile < n_tiles) {
         g = geo(tile);
+        tn = skip(tile + (int)gridDim.x);
+        if (tn < n_tiles) gn = geo(tn);
         if (worker) {
             stage(g, 0);
             tc::fence_async_smem();
@@ -488,10 +501,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         if (__syncthreads_or(!ok)) timed_out = true;
     }
     while (tile < n_tiles && !timed_out) {
-        const int tn = skip(tile + (int)gridDim.x);
         const bool has_next = tn < n_tiles;
-        Geo gn{};
-        if (has_next) gn = geo(tn);
 
         // 3-4. layer 2 of this tile as implicit GEMM, double-buffered in TMEM
         // (chunk c+1 runs while the workers read chunk c).  Each worker loads
@@ -502,13 +512,21 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             issue_layer2(0);
             if (C2 > 1) issue_layer2(1);
         }
-        if (STEP && has_next && tid == 0) sD[buf ^ 1] = A.desc[gn.cloth];
         Raw rw[kStageParts];
         if (worker && has_next) {
 #pragma unroll
             for (int k = 0; k < kStageParts; ++k)
                 if (tid + k * NWORK < N0) stage_load(gn, tid + k * NWORK, rw[k]);
         }
+        // the next tile's descriptor (8 x 16 bytes), stored after chunk 0
+        constexpr int kDescV = (int)(sizeof(ClothDesc) / sizeof(uint4));
+        static_assert(sizeof(ClothDesc) % sizeof(uint4) == 0 && kDescV <= NWORK, "descriptor copy");
+        uint4 dv = make_uint4(0, 0, 0, 0);
+        if (STEP && has_next && tid < kDescV) dv = reinterpret_cast<const uint4*>(A.desc + gn.cloth)[tid];
+        // the tile after next: its geometry loads land during the chunks
+        const int tnn = has_next ? skip(tn + (int)gridDim.x) : n_tiles;
+        Geo gnn{};
+        if (tnn < n_tiles) gnn = geo(tnn);
         for (int c2 = 0; c2 < C2; ++c2) {
             const int b = c2 & 1;
             bool ok = true;
@@ -518,6 +536,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
                 for (int k = 0; k < kStageParts; ++k)   // register-indexed: k is a constant here
                     if (k == c2 && has_next && tid + k * NWORK < N0) stage_store(gn, buf ^ 1, tid + k * NWORK, rw[k]);
+                if (STEP && c2 == 0 && has_next && tid < kDescV) reinterpret_cast<uint4*>(sD + (buf ^ 1))[tid] = dv;
             }
             ph2[b] ^= 1u;
             if (__syncthreads_or(!ok)) { timed_out = true; break; }
@@ -537,7 +556,9 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         if (has_next) ph1 ^= 1u;
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tile = tn;
+        tn = tnn;
         g = gn;
+        gn = gnn;
         buf ^= 1;
     }
 
