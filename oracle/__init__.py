@@ -5,11 +5,13 @@ library computes.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import it; the product path never does, and
 it shares no code with the CUDA library.
 
-The arithmetic lives in two plain C files compiled on demand with gcc
+The arithmetic lives in plain C files compiled on demand with gcc
 (``cloth_oracle.c``: the mass-spring system of Sec. 3.1, Eq. 1-5;
-``cnn_oracle.c``: the CNN cell of Sec. 3.2, Eq. 6-7 and its backward).  This
-module marshals numpy arrays and composes those primitives into the network
-step of Fig. 2 and the training loss of Eq. 8, step by step.
+``cnn_oracle.c``: the CNN cell of Sec. 3.2, Eq. 6-7 and its backward;
+``pcell_oracle.c``: the cell of Eq. 6-7 read literally, with frozen
+difference channels and ISRU).  This module marshals numpy arrays and
+composes those primitives into the network step of Fig. 2 and the training
+loss of Eq. 8, step by step.
 
 Array conventions: a cloth state is ``x, v`` of shape ``(rows, cols, 3)``
 float64; node (r, c) rests at ``X = (c h, r h, 0)``.
@@ -24,13 +26,17 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["cloth_oracle.c", "cnn_oracle.c"]
+_SRCS = ["cloth_oracle.c", "cnn_oracle.c", "pcell_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
 N_PARAMS = 13027   # trainable entries of the weight blob
 N_BLOB = 13036     # + in_scale[6] + out_scale[3]
+PCELL_BLOB = 40    # w_L[12], w_N[12], w_D[12], b_L[3], alpha
+# channel c of the literal cell: (row offset, column offset) of its neighbour
+PCELL_CHANNELS = ((0, 1), (0, -1), (1, 0), (-1, 0), (1, 1), (1, -1), (-1, 1), (-1, -1),
+                  (0, 2), (0, -2), (2, 0), (-2, 0))
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +85,7 @@ def _load():
             lib.oracle_energy.restype = ctypes.c_double
             lib.oracle_cnn_forward.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, dp]
             lib.oracle_cnn_backward.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp]
+            lib.oracle_pcell_accel.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp]
             lib.oracle_cnn_param_count.restype = ctypes.c_int32
             lib.oracle_cnn_blob_count.restype = ctypes.c_int32
             assert lib.oracle_cnn_param_count() == N_PARAMS
@@ -254,6 +261,44 @@ def net_step(w, c: dict, x, v, pins=(), steps: int = 1):
     sph = c.get("sphere")
     for _ in range(steps):
         acc = net_accel(w, c, x, v) + pressure_force(c, x) / float(c["m"])
+        v = v + float(c["dt"]) * acc
+        v = np.where(pm, 0.0, v)
+        x = x + float(c["dt"]) * v
+        if sph is not None:
+            d = x - np.asarray(sph["center"], dtype=np.float64)
+            ln = np.sqrt((d * d).sum(axis=2, keepdims=True))
+            inside = (ln < float(sph["radius"])) & (ln > 0.0)
+            x = np.where(inside, np.asarray(sph["center"]) + float(sph["radius"]) * d / np.where(ln > 0, ln, 1.0), x)
+            v = np.where(inside, 0.0, v)
+    return x, v
+
+
+# ---------------------------------------------------------------- literal cell
+def pcell_accel(w, c: dict, x, v) -> np.ndarray:
+    """The cell of Eq. 6-7 read literally (Fig. 1): per coordinate, 12
+    frozen difference channels phi_c = x_j - x_i, xi_c = v_j - v_i over the
+    stencil neighbours that exist; a = sum_c [w_L phi + w_N sigma(phi) +
+    w_D xi sigma(phi)] + b_L with the ISRU sigma.  Shape (rows, cols, 3)."""
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    assert w.shape == (PCELL_BLOB,), w.shape
+    rows, cols = int(c["rows"]), int(c["cols"])
+    x = _state(x, rows, cols)
+    v = _state(v, rows, cols)
+    a = np.zeros((rows, cols, 3))
+    _load().oracle_pcell_accel(rows, cols, _dptr(w), _dptr(x), _dptr(v), _dptr(a))
+    return a
+
+
+def pcell_step(w, c: dict, x, v, pins=(), steps: int = 1):
+    """Framework step of Fig. 2 with the literal cell: its acceleration plus
+    the hard-encoded pressure (Eq. 3) drive Eq. 5 with pins and sphere
+    contact."""
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    pm = pin_mask(c, pins).reshape(int(c["rows"]), int(c["cols"]), 1).astype(bool)
+    sph = c.get("sphere")
+    for _ in range(steps):
+        acc = pcell_accel(w, c, x, v) + pressure_force(c, x) / float(c["m"])
         v = v + float(c["dt"]) * acc
         v = np.where(pm, 0.0, v)
         x = x + float(c["dt"]) * v
