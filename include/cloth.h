@@ -323,6 +323,35 @@ int cloth_modes(cloth_ctx* ctx, int32_t* d_mode, float* d_residual, void* stream
 int cloth_reset_modes(cloth_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------------
+ * The physics-embedded cell read literally (Sec. 3.2, Eq. 6-7, Fig. 1).
+ *
+ * Per coordinate k (the same 2D kernels act on x, y and z: isotropy) and
+ * node i, over the 12 stencil neighbours j_c that exist (channel c is the
+ * frozen difference filter of one neighbour; order E, W, N, S, NE, NW, SE,
+ * SW, E2, W2, N2, S2 with N = row + 1, E = column + 1, and the "2" taps two
+ * apart, a dilation-2 kernel):
+ *   phi_c = x_jc - x_i,  xi_c = v_jc - v_i,
+ *   s_c = phi_c / sqrt(1 + alpha phi_c^2)          (ISRU activation)
+ *   a_k = b_L[k] + sum_c (w_L[c] phi_c + w_N[c] s_c + w_D[c] xi_c s_c)
+ * Weight blob, device, CLOTH_PCELL_BLOB floats:
+ *   w_L[12], w_N[12], w_D[12], b_L[3], alpha.
+ * The blob is read on every call; the caller keeps it finite.  The
+ * workspace holds the tile list: size from cloth_pcell_workspace_size,
+ * 256-byte aligned. */
+#define CLOTH_PCELL_BLOB 40
+
+int cloth_pcell_workspace_size(const cloth_ctx* ctx, size_t* bytes);
+
+/* The cell's output a at the current state into d_a (packed [node][3], the
+ * order of cloth_get_state).  State unchanged.  Stream-ordered. */
+int cloth_pcell_accel(cloth_ctx* ctx, const float* d_w, float* d_a, void* d_work, size_t bytes, void* stream);
+
+/* `steps` network steps of Fig. 2 with the literal cell: a + (pressure of
+ * Eq. 3) / m drives Eq. 5 with the pins and sphere contact of the context.
+ * Stream-ordered; a non-finite position sets CLOTH_STATUS_NONFINITE. */
+int cloth_step_pcell(cloth_ctx* ctx, const float* d_w, int32_t steps, void* d_work, size_t bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Training (Sec. 3.2.1, Eq. 8; Table 1)
  * ---------------------------------------------------------------------- */
 

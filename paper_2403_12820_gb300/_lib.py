@@ -18,6 +18,7 @@ P = ctypes.POINTER
 CLOTH_OK = 0
 NET_FP32, NET_BF16 = 0, 1
 NET_PARAMS, NET_BLOB = 13027, 13036
+PCELL_BLOB = 40
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "EUNSUPPORTED"}
 STATUS_NONFINITE, STATUS_TIMEOUT, STATUS_BOUNDS = 1, 2, 4
 
@@ -79,6 +80,9 @@ SIGNATURES = {
                                 c_float, c_void_p]),
     "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_net_rollout_workspace_size": (c_int32, [c_void_p, c_int32, P(c_size_t)]),
+    "cloth_pcell_workspace_size": (c_int32, [c_void_p, P(c_size_t)]),
+    "cloth_pcell_accel": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "cloth_step_pcell": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_rollout_net": (c_int32, [c_void_p, c_void_p, P(NetRolloutOpts), c_void_p, c_size_t, c_void_p]),
     "cloth_modes": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "cloth_reset_modes": (c_int32, [c_void_p, c_void_p]),

@@ -156,6 +156,38 @@ class ClothBatch:
         o = NetRolloutOpts(int(steps), int(check_every), float(residual_bound), int(graph_chunk))
         _lib.call("cloth_rollout_net", self.handle, net.handle, ctypes.byref(o), _ptr(ws), ws.numel(), self._s())
 
+    def _pcell_ws(self) -> torch.Tensor:
+        n = ctypes.c_size_t()
+        _lib.call("cloth_pcell_workspace_size", self.handle, ctypes.byref(n))
+        ws = getattr(self, "_pcell_work", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._pcell_work = ws
+        return ws
+
+    @staticmethod
+    def _pcell_w(w, device) -> torch.Tensor:
+        w = torch.as_tensor(w, dtype=torch.float32).to(device).contiguous()
+        if w.numel() != _lib.PCELL_BLOB:
+            raise ValueError(f"literal-cell weights must hold {_lib.PCELL_BLOB} floats")
+        return w
+
+    def pcell_accel(self, w) -> torch.Tensor:
+        """The literal cell's output (Eq. 6-7, Fig. 1) at the current state,
+        packed (total_nodes, 3)."""
+        w = self._pcell_w(w, self.device)
+        ws = self._pcell_ws()
+        a = torch.empty(self.total_nodes, 3, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_pcell_accel", self.handle, _ptr(w), _ptr(a), _ptr(ws), ws.numel(), self._s())
+        return a
+
+    def step_pcell(self, w, steps: int = 1) -> None:
+        """`steps` network steps (Fig. 2) with the literal cell."""
+        w = self._pcell_w(w, self.device)
+        ws = self._pcell_ws()
+        _lib.call("cloth_step_pcell", self.handle, _ptr(w), int(steps), _ptr(ws), ws.numel(), self._s())
+        self._pcell_keep = w   # alive until the stream has used it
+
     def modes(self) -> tuple[torch.Tensor, torch.Tensor]:
         """(mode (B,) int32: 0 network, 1 plain; residual of the last check (B,) m)."""
         m = torch.empty(self.B, dtype=torch.int32, device=self.device)

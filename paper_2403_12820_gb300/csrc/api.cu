@@ -435,6 +435,69 @@ int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32
     return CLOTH_OK;
 }
 
+namespace {
+constexpr int kListsPcell = 2;   // lists_kind of the literal cell's tile list
+
+std::vector<int4> pcell_tiles(const cloth_ctx* c)
+{
+    std::vector<int4> t;
+    const int R = pcell_tile_rows(), Wt = pcell_tile_cols();
+    for (int b = 0; b < c->B; ++b)
+        for (int y0 = 0; y0 < c->grids[b].rows; y0 += R)
+            for (int x0 = 0; x0 < c->grids[b].cols; x0 += Wt) t.push_back(make_int4(b, y0, x0, 0));
+    return t;
+}
+
+int pcell_prepare(cloth_ctx* c, void* d_work, size_t bytes, cudaStream_t s, int* n_tiles)
+{
+    const std::vector<int4> tiles = pcell_tiles(c);
+    if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    if (c->lists_written != d_work || c->lists_kind != kListsPcell) {
+        CK(cudaMemcpyAsync(d_work, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        c->lists_written = d_work;
+        c->lists_kind = kListsPcell;
+    }
+    *n_tiles = (int)tiles.size();
+    return CLOTH_OK;
+}
+}  // namespace
+
+int cloth_pcell_workspace_size(const cloth_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return CLOTH_EINVAL;
+    *bytes = align_up(sizeof(int4) * pcell_tiles(c).size(), kAlign);
+    return CLOTH_OK;
+}
+
+int cloth_pcell_accel(cloth_ctx* c, const float* d_w, float* d_a, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !d_w || !d_a || !d_work) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int n = 0;
+    const int rc = pcell_prepare(c, d_work, bytes, s, &n);
+    if (rc) return rc;
+    CK(launch_pcell(c->d_desc(), static_cast<const int4*>(d_work), n, d_w, c->d_state(c->cur), nullptr, d_a,
+                    c->d_pins(), c->d_status(), s));
+    return CLOTH_OK;
+}
+
+int cloth_step_pcell(cloth_ctx* c, const float* d_w, int32_t steps, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !d_w || !d_work || steps < 0) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int n = 0;
+    const int rc = pcell_prepare(c, d_work, bytes, s, &n);
+    if (rc) return rc;
+    for (int st = 0; st < steps; ++st) {
+        CK(launch_pcell(c->d_desc(), static_cast<const int4*>(d_work), n, d_w, c->d_state(c->cur),
+                        c->d_state(c->cur ^ 1), nullptr, c->d_pins(), c->d_status(), s));
+        c->cur ^= 1;
+    }
+    return CLOTH_OK;
+}
+
 int cloth_net_rollout_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes) return CLOTH_EINVAL;

@@ -82,6 +82,13 @@ struct StepArgs {
 // Launchers (plain_step.cu, state.cu).
 cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
 cudaError_t launch_plain_step_damp(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s);
+// The literal cell (pcell.cu): tiles of pcell_tile_rows() x pcell_tile_cols()
+// output nodes; a_out set -> the cell's acceleration into a_out (packed ABI
+// order), else one network step src -> dst.
+int pcell_tile_rows();
+int pcell_tile_cols();
+cudaError_t launch_pcell(const ClothDesc* desc, const int4* tiles, int n_tiles, const float* w, const float* src,
+                         float* dst, float* a_out, const uint32_t* pinmask, int32_t* status, cudaStream_t s);
 // Blocks of `block` threads of the plain-step kernel resident per SM.
 int plain_step_blocks_per_sm(bool damp, int block);
 cudaError_t launch_set_state(const ClothDesc* desc, int32_t B, int64_t total_nodes, const int64_t* node_cloth_start,

@@ -178,3 +178,21 @@ def kaiming_blob(seed: int = 2003, in_scale=(1.0,) * 6, out_scale=(1.0,) * 3, bi
     blob = np.concatenate(parts).astype(np.float32)
     assert blob.shape == (N_BLOB,)
     return blob
+
+
+def pcell_blob(seed: int = 2005, h: float = H_DEFAULT, m: float = M_DEFAULT, k=K_DEFAULT,
+               g=G_DEFAULT) -> np.ndarray:
+    """Weights of the literal cell (40 floats: w_L[12], w_N[12], w_D[12],
+    b_L[3], alpha), spring-like: w_L = k_type / m scattered by U(0.9, 1.1)
+    per channel, nonlinear and derivative weights of a tenth of that scale
+    with random signs, b_L = g, alpha = 1 / (2 h)^2 so the ISRU bends at
+    displacements of the lattice scale; rounded to float32."""
+    rng = np.random.default_rng(seed)
+    kc = np.array([k[0]] * 4 + [k[1]] * 4 + [k[2]] * 4) / m
+    w = np.zeros(40)
+    w[0:12] = kc * rng.uniform(0.9, 1.1, 12)
+    w[12:24] = 0.1 * kc * h * rng.choice([-1.0, 1.0], 12) * rng.uniform(0.5, 1.5, 12)
+    w[24:36] = 0.1 * kc * rng.choice([-1.0, 1.0], 12) * rng.uniform(0.5, 1.5, 12) * 1e-3
+    w[36:39] = g
+    w[39] = 1.0 / (2.0 * h) ** 2
+    return w.astype(np.float32)
