@@ -52,6 +52,7 @@ def parse_args(argv=None):
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-steps", type=int, default=400)
     p.add_argument("--no-train", action="store_true")
+    p.add_argument("--no-pcell", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
     return p.parse_args(argv)
 
@@ -328,6 +329,8 @@ def run_plain(args, rank, world, local):
         out["cnn"] = run_cnn(args, dev)
     if not args.no_mixed:
         out["mixed_fallback"] = run_mixed(args, dev)
+    if not args.no_pcell:
+        out["pcell"] = run_pcell(args, dev, value / world)
     if not args.no_train:
         out["train"] = run_train(args, dev)
 
@@ -464,6 +467,44 @@ def run_mixed(args, dev):
            "plain_same_cloths": plain, "ratio_to_plain": checked / plain, "status_word": status,
            "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
     net.close()
+    cb.close()
+    return out
+
+
+def run_pcell(args, dev, plain_rate: float):
+    """Network step with the literal cell (Eq. 6-7, Fig. 1: frozen difference
+    channels, ISRU, three branches) on the plain batch's 64 cloths,
+    spring-like weights (seed 2005): node-steps/s against the HBM roofline
+    (48 B per node-step, as the plain step) and the ratio to the plain step."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+
+    cfg = wl.plain_batch()
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cb.set_state(pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev))
+    nodes = cb.total_nodes
+    w = torch.from_numpy(wl.pcell_blob()).to(dev)
+    stream = torch.cuda.current_stream()
+    cb.step_pcell(w, 20)
+    steps = 400
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cb.step_pcell(w, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    rate = nodes * steps / t
+    hbm, _, peak_kind = peaks()
+    achieved = BYTES_PER_NODE_STEP * rate / 1e9
+    out = {"workload": "plain_batch cloths (5.97M nodes), literal cell with spring-like weights (seed 2005)",
+           "value": rate, "unit": "node-steps/s", "steps": steps, "ms_per_step": t / steps * 1e3,
+           "ratio_to_plain": rate / plain_rate, "gpu_launches_per_step": 1, "status_word": cb.status(),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_kind": f"{peak_kind} (copy bandwidth)",
+                        "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * nodes}}
     cb.close()
     return out
 

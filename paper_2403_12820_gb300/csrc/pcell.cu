@@ -8,24 +8,41 @@
 // Eq. 7 per coordinate: a = b_L + sum_c [w_L phi + w_N s + w_D xi s] with
 // s = phi / sqrt(1 + alpha phi^2) (ISRU).
 //
-// Mapping: one block of 256 threads per 32 x 8 output tile; the tile and a
-// 2-node halo of the six state planes are staged in shared memory; one
-// thread per node.  phi is formed as l_c + (u_j - u_i) from the stored
+// Mapping: one block of 256 threads per 32 x 16 output tile; the tile and a
+// 2-node halo of the six state planes are staged in shared memory (whole
+// aligned groups of 4 columns, one float4 load each, all issued before any
+// is stored); one thread per pair of nodes 8 rows apart, in f32x2 lanes.  phi is formed as l_c + (u_j - u_i) from the stored
 // displacements u = x - X (l_c the lattice offset), which keeps the
 // difference exact to the rounding of u.  Step mode adds the hard-encoded
 // pressure (Eq. 3) and runs Eq. 5 with pins and sphere contact.
 #include "cloth_internal.cuh"
 
+// Resident blocks of 256 threads per SM the register budget is sized for.
+#ifndef CLOTH_PCELL_MINB
+#define CLOTH_PCELL_MINB 4
+#endif
+
 namespace cloth {
 namespace {
 
-constexpr int TW = 32, TH = 8, HALO = 2;
-constexpr int SW = TW + 2 * HALO, SH = TH + 2 * HALO;   // staged tile
-constexpr int NT = TW * TH;
+constexpr int TW = 32, TH = 16, HALO = 2;
+constexpr int GX = 4;                                   // staged columns start 4 left of the tile
+constexpr int SW = TW + 2 * GX, SH = TH + 2 * HALO;     // staged tile: 40 x 12
+constexpr int NT = TW * TH / 2;                          // two nodes per thread
+constexpr int kGroups = 6 * SH * (SW / 4);              // float4 loads per tile
+constexpr int kLoadsPerThread = (kGroups + NT - 1) / NT;
+static_assert(TW % 4 == 0, "tiles start on a column group");
 constexpr int kPcellBlob = 40;
 
-__constant__ int kChDy[12] = {0, 0, 1, -1, 1, 1, -1, -1, 0, 0, 2, -2};
-__constant__ int kChDx[12] = {1, -1, 0, 0, 1, -1, 1, -1, 2, -2, 0, 0};
+// channel offsets (row, column): E W N S NE NW SE SW E2 W2 N2 S2
+__host__ __device__ constexpr int ch_dy(int c)
+{
+    return c == 2 || c == 4 || c == 5 ? 1 : (c == 3 || c == 6 || c == 7 ? -1 : (c == 10 ? 2 : (c == 11 ? -2 : 0)));
+}
+__host__ __device__ constexpr int ch_dx(int c)
+{
+    return c == 0 || c == 4 || c == 6 ? 1 : (c == 1 || c == 5 || c == 7 ? -1 : (c == 8 ? 2 : (c == 9 ? -2 : 0)));
+}
 
 struct PcellArgs {
     const ClothDesc* desc;
@@ -38,8 +55,17 @@ struct PcellArgs {
     int32_t* status;
 };
 
+using f2 = float2;
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, F2(-1.f), a); }
+
+// Each thread computes nodes (y0 + ty, x) and (y0 + ty + TH / 2, x) as one
+// pair of f32x2 lanes.
 template <bool STEP>
-__global__ void __launch_bounds__(NT) pcell_kernel(PcellArgs A)
+__global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A)
 {
     __shared__ float sU[6][SH][SW];
     __shared__ float sW[kPcellBlob];
@@ -50,84 +76,121 @@ __global__ void __launch_bounds__(NT) pcell_kernel(PcellArgs A)
     const int tid = threadIdx.x;
     if (tid < kPcellBlob) sW[tid] = A.w[tid];
     const float* src = A.src + D.plane_off;
-    for (int e = tid; e < 6 * SH * SW; e += NT) {
-        const int p = e / (SH * SW), r = (e / SW) % SH, c = e % SW;
-        const int y = y0 - HALO + r, x = x0 - HALO + c;
-        float val = 0.f;
-        if (y >= 0 && y < H && x >= 0 && x < W) val = __ldg(src + p * D.plane_stride + (int64_t)y * D.pitch + col_pos(x));
-        sU[p][r][c] = val;
+    const int pitch = D.pitch;
+    const int64_t pstride = D.plane_stride;
+    // group g: plane p, staged row r, columns x0 - 4 + 4 q .. +3 (memory order
+    // c0 c2 c1 c3); rows outside the grid and groups outside the pitch stay
+    // zero (columns in the padding are zero in the state buffers)
+    float4 ld[kLoadsPerThread];
+#pragma unroll
+    for (int i = 0; i < kLoadsPerThread; ++i) {
+        const int g = tid + i * NT;
+        const int p = g / (SH * (SW / 4)), r = (g / (SW / 4)) % SH, q = g % (SW / 4);
+        const int y = y0 - HALO + r, xg = x0 - GX + 4 * q;
+        ld[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < kGroups && y >= 0 && y < H && xg >= 0 && xg < pitch)
+            ld[i] = __ldg(reinterpret_cast<const float4*>(src + p * pstride + (int64_t)y * pitch + xg));
+    }
+#pragma unroll
+    for (int i = 0; i < kLoadsPerThread; ++i) {
+        const int g = tid + i * NT;
+        if (g >= kGroups) break;
+        const int p = g / (SH * (SW / 4)), r = (g / (SW / 4)) % SH, q = g % (SW / 4);
+        float* row = &sU[p][r][4 * q];
+        row[0] = ld[i].x; row[2] = ld[i].y; row[1] = ld[i].z; row[3] = ld[i].w;
     }
     __syncthreads();
 
     const int ty = tid / TW, tx = tid % TW;
-    const int y = y0 + ty, x = x0 + tx;
-    if (y >= H || x >= W) return;
-    const int sy = ty + HALO, sx = tx + HALO;
-    const float h = D.h, alpha = sW[39];
-    float acc[3] = {sW[36], sW[37], sW[38]};
+    const int ya = y0 + ty, yb = ya + TH / 2, x = x0 + tx;
+    if (ya >= H || x >= W) return;   // yb > ya: both out
+    const bool hb = yb < H;          // second node exists
+    const int sy = ty + HALO, sx = tx + GX;
+    const float h = D.h;
+    const f2 alpha = F2(sW[39]);
+    auto U2 = [&](int p, int dy, int dx) { return make_float2(sU[p][sy + dy][sx + dx], sU[p][sy + TH / 2 + dy][sx + dx]); };
+    // neighbour existence per node of the pair: rows -2 .. +2, columns -2 .. +2
+    auto rowok = [&](int y, int dy) { return y + dy >= 0 && y + dy < H; };
+    const bool c_m2 = x >= 2, c_m1 = x >= 1, c_p1 = x + 1 < W, c_p2 = x + 2 < W;
+    f2 ui[3], vi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ui[k] = U2(k, 0, 0);
+        vi[k] = U2(3 + k, 0, 0);
+    }
+    f2 acc[3] = {F2(sW[36]), F2(sW[37]), F2(sW[38])};
 #pragma unroll
     for (int ch = 0; ch < 12; ++ch) {
-        const int dy = kChDy[ch], dx = kChDx[ch];
-        if (y + dy < 0 || y + dy >= H || x + dx < 0 || x + dx >= W) continue;
-        const float wl = sW[ch], wn = sW[12 + ch], wd = sW[24 + ch];
+        const int dy = ch_dy(ch), dx = ch_dx(ch);
+        const bool cx = dx == 0 ? true : (dx == 1 ? c_p1 : (dx == -1 ? c_m1 : (dx == 2 ? c_p2 : c_m2)));
+        const f2 m = make_float2(cx && rowok(ya, dy) ? 1.f : 0.f, cx && hb && rowok(yb, dy) ? 1.f : 0.f);
+        const f2 wl = mul2(m, F2(sW[ch])), wn = mul2(m, F2(sW[12 + ch])), wd = mul2(m, F2(sW[24 + ch]));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
-            const float phi = lat + (sU[k][sy + dy][sx + dx] - sU[k][sy][sx]);
-            const float xi = sU[3 + k][sy + dy][sx + dx] - sU[3 + k][sy][sx];
-            const float s = phi * rsqrtf(fmaf(alpha * phi, phi, 1.f));
-            acc[k] = fmaf(wl, phi, fmaf(s, fmaf(wd, xi, wn), acc[k]));
+            const f2 phi = add2(F2(lat), sub2(U2(k, dy, dx), ui[k]));
+            const f2 xi = sub2(U2(3 + k, dy, dx), vi[k]);
+            const f2 q = fma2(mul2(alpha, phi), phi, F2(1.f));
+            const f2 s = mul2(phi, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+            acc[k] = fma2(wl, phi, fma2(s, fma2(wd, xi, wn), acc[k]));
         }
     }
-    if constexpr (!STEP) {
-        float* o = A.a_out + (D.abi_off + (int64_t)y * W + x) * 3;
-        o[0] = acc[0]; o[1] = acc[1]; o[2] = acc[2];
-        return;
-    } else {
-        // pressure (Eq. 3): (p/4) (d'_E - d'_W) x (d'_N - d'_S) with absent
-        // neighbours' terms dropped
-        if (D.p_quarter != 0.f) {
-            const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
-            float e[3], n[3];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        if (half == 1 && !hb) break;
+        const int y = half ? yb : ya, yy = sy + half * (TH / 2);
+        float a3[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a3[k] = half ? acc[k].y : acc[k].x;
+        if constexpr (!STEP) {
+            float* o = A.a_out + (D.abi_off + (int64_t)y * W + x) * 3;
+            o[0] = a3[0]; o[1] = a3[1]; o[2] = a3[2];
+        } else {
+            // pressure (Eq. 3): (p/4) (d'_E - d'_W) x (d'_N - d'_S) with absent
+            // neighbours' terms dropped
+            if (D.p_quarter != 0.f) {
+                const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
+                float e[3], n[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float u0 = sU[k][yy][sx];
+                    e[k] = (bE ? sU[k][yy][sx + 1] - u0 + (k == 0 ? h : 0.f) : 0.f) -
+                           (bW ? sU[k][yy][sx - 1] - u0 - (k == 0 ? h : 0.f) : 0.f);
+                    n[k] = (bN ? sU[k][yy + 1][sx] - u0 + (k == 1 ? h : 0.f) : 0.f) -
+                           (bS ? sU[k][yy - 1][sx] - u0 - (k == 1 ? h : 0.f) : 0.f);
+                }
+                const float sc = D.p_quarter * D.inv_m;
+                a3[0] = fmaf(sc, e[1] * n[2] - e[2] * n[1], a3[0]);
+                a3[1] = fmaf(sc, e[2] * n[0] - e[0] * n[2], a3[1]);
+                a3[2] = fmaf(sc, e[0] * n[1] - e[1] * n[0], a3[2]);
+            }
+            const bool pinned = (__ldg(A.pinmask + D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)) >> (x & 31)) & 1u;
+            float un[3], vn[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float ui = sU[k][sy][sx];
-                e[k] = (bE ? sU[k][sy][sx + 1] - ui + (k == 0 ? h : 0.f) : 0.f) -
-                       (bW ? sU[k][sy][sx - 1] - ui - (k == 0 ? h : 0.f) : 0.f);
-                n[k] = (bN ? sU[k][sy + 1][sx] - ui + (k == 1 ? h : 0.f) : 0.f) -
-                       (bS ? sU[k][sy - 1][sx] - ui - (k == 1 ? h : 0.f) : 0.f);
+                vn[k] = pinned ? 0.f : fmaf(D.dt, a3[k], sU[3 + k][yy][sx]);
+                un[k] = fmaf(D.dt, vn[k], sU[k][yy][sx]);
             }
-            const float sc = D.p_quarter * D.inv_m;
-            acc[0] = fmaf(sc, e[1] * n[2] - e[2] * n[1], acc[0]);
-            acc[1] = fmaf(sc, e[2] * n[0] - e[0] * n[2], acc[1]);
-            acc[2] = fmaf(sc, e[0] * n[1] - e[1] * n[0], acc[2]);
-        }
-        const bool pinned = (__ldg(A.pinmask + D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)) >> (x & 31)) & 1u;
-        float un[3], vn[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            vn[k] = pinned ? 0.f : fmaf(D.dt, acc[k], sU[3 + k][sy][sx]);
-            un[k] = fmaf(D.dt, vn[k], sU[k][sy][sx]);
-        }
-        if (D.sph_on) {
-            const float rx = fmaf((float)x, h, -D.sph_cx) + un[0];
-            const float ry = fmaf((float)y, h, -D.sph_cy) + un[1];
-            const float rz = un[2] - D.sph_cz;
-            const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if (dd < D.sph_r2 && dd > 0.f) {
-                const float sc = D.sph_r * rsqrtf(dd);
-                un[0] = fmaf(sc, rx, un[0] - rx);
-                un[1] = fmaf(sc, ry, un[1] - ry);
-                un[2] = fmaf(sc, rz, un[2] - rz);
-                vn[0] = vn[1] = vn[2] = 0.f;
+            if (D.sph_on) {
+                const float rx = fmaf((float)x, h, -D.sph_cx) + un[0];
+                const float ry = fmaf((float)y, h, -D.sph_cy) + un[1];
+                const float rz = un[2] - D.sph_cz;
+                const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                if (dd < D.sph_r2 && dd > 0.f) {
+                    const float sc = D.sph_r * rsqrtf(dd);
+                    un[0] = fmaf(sc, rx, un[0] - rx);
+                    un[1] = fmaf(sc, ry, un[1] - ry);
+                    un[2] = fmaf(sc, rz, un[2] - rz);
+                    vn[0] = vn[1] = vn[2] = 0.f;
+                }
             }
-        }
-        if (!isfinite(un[0] + un[1] + un[2])) atomicOr(A.status, kStatusNonfinite);
-        float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
+            if (!isfinite(un[0] + un[1] + un[2])) atomicOr(A.status, kStatusNonfinite);
+            float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            out[k * D.plane_stride] = un[k];
-            out[(3 + k) * D.plane_stride] = vn[k];
+            for (int k = 0; k < 3; ++k) {
+                out[k * D.plane_stride] = un[k];
+                out[(3 + k) * D.plane_stride] = vn[k];
+            }
         }
     }
 }
