@@ -26,11 +26,13 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int64_t pitch_of(int cols) { return (int64_t)((cols + kPitchAlign - 1) / kPitchAlign) * kPitchAlign; }
 
-int64_t units_for(const cloth_grid* g, int B, int seg_rows)
+// Work units of `seg_rows`-row segments of `strip`-column strips (the plain
+// kernel's kStrip by default; the narrower strip bounds the layout).
+int64_t units_for(const cloth_grid* g, int B, int seg_rows, int strip = kStrip)
 {
     int64_t n = 0;
     for (int b = 0; b < B; ++b)
-        n += (int64_t)((g[b].cols + kStrip - 1) / kStrip) * ((g[b].rows + seg_rows - 1) / seg_rows);
+        n += (int64_t)((g[b].cols + strip - 1) / strip) * ((g[b].rows + seg_rows - 1) / seg_rows);
     return n;
 }
 
@@ -146,6 +148,7 @@ namespace {
 int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
 {
     const int warps_per_block = c->block / 32;
+    const int strip = c->damp ? kStripDamp : kStrip;
     int wps = c->warps_per_sm;
     if (wps <= 0 && seg_rows <= 0) wps = std::max(1, plain_step_blocks_per_sm(c->damp, c->block)) * warps_per_block;
     const int W = wps > 0 ? std::max(1, std::min(kMaxWarps, c->sm_count * wps)) : kMaxWarps;
@@ -157,7 +160,7 @@ int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
         for (int b = 0; b < c->B; ++b) {
             const int rows = c->grids[b].rows, cols = c->grids[b].cols;
             for (int r0 = 0; r0 < rows; r0 += seg_rows)
-                for (int c0 = 0; c0 < cols; c0 += kStrip) all.push_back(WorkUnit{b, c0, r0, std::min(rows, r0 + seg_rows)});
+                for (int c0 = 0; c0 < cols; c0 += strip) all.push_back(WorkUnit{b, c0, r0, std::min(rows, r0 + seg_rows)});
         }
         std::stable_sort(all.begin(), all.end(),
                          [](const WorkUnit& a, const WorkUnit& b) { return (a.r1 - a.r0) > (b.r1 - b.r0); });
@@ -169,12 +172,12 @@ int set_work(cloth_ctx* c, int seg_rows, cudaStream_t s)
     } else {
         int64_t total = 0;
         for (int b = 0; b < c->B; ++b)
-            total += (int64_t)c->grids[b].rows * ((c->grids[b].cols + kStrip - 1) / kStrip);
+            total += (int64_t)c->grids[b].rows * ((c->grids[b].cols + strip - 1) / strip);
         const int64_t q = std::max<int64_t>(1, (total + W - 1) / W);   // rows per warp
         int64_t pos = 0;
         for (int b = 0; b < c->B; ++b) {
             const int rows = c->grids[b].rows, cols = c->grids[b].cols;
-            for (int c0 = 0; c0 < cols; c0 += kStrip)
+            for (int c0 = 0; c0 < cols; c0 += strip)
                 for (int r = 0; r < rows;) {
                     const int64_t w = pos / q;
                     const int take = (int)std::min<int64_t>(rows - r, (w + 1) * q - pos);
@@ -204,7 +207,7 @@ int pick_seg_rows(const cloth_ctx* c)
     // the 2 warm-up rows stay a small fraction
     const int64_t target = (int64_t)c->sm_count * 12;
     for (int R : {64, 32, 16, 8})
-        if (units_for(c->grids.data(), c->B, R) >= target) return R;
+        if (units_for(c->grids.data(), c->B, R, c->damp ? kStripDamp : kStrip) >= target) return R;
     return 8;
 }
 

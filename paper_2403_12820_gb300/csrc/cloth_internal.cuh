@@ -12,6 +12,7 @@ namespace cloth {
 // halo lanes that supply the springs reaching across the strip border.
 constexpr int kLaneCols = 4;
 constexpr int kStrip = 120;
+constexpr int kStripDamp = kStrip;   // the damped kernel (mu != 0) uses the same strips
 // Plane pitch (floats per row) is a multiple of this, so every float4 of a
 // lane is 16-byte aligned and lies wholly inside or outside [0, pitch).
 constexpr int kPitchAlign = 4;

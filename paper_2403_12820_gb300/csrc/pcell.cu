@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
     const float* src = A.src + D.plane_off;
     const int pitch = D.pitch;
     const int64_t pstride = D.plane_stride;
-    // group g: plane p, staged row r, columns x0 - 4 + 4 q .. +3 (memory order
-    // c0 c2 c1 c3); rows outside the grid and groups outside the pitch stay
+    // group g: plane p, staged row r, columns x0 - 4 + 4 q .. +3 (in the
+    // slots of col_slot); rows outside the grid and groups outside the pitch stay
     // zero (columns in the padding are zero in the state buffers)
     float4 ld[kLoadsPerThread];
 #pragma unroll
@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
         if (g >= kGroups) break;
         const int p = g / (SH * (SW / 4)), r = (g / (SW / 4)) % SH, q = g % (SW / 4);
         float* row = &sU[p][r][4 * q];
-        row[0] = ld[i].x; row[2] = ld[i].y; row[1] = ld[i].z; row[3] = ld[i].w;
+        const float tv[4] = {ld[i].x, ld[i].y, ld[i].z, ld[i].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) row[k] = tv[col_slot(k)];
     }
     __syncthreads();
 

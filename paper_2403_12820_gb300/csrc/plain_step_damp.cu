@@ -3,7 +3,7 @@
 // carries the neighbours' velocities.  The paired-FP32 kernel of
 // plain_step.cu serves every batch without spring damping.
 //
-// Mapping: one warp per work unit (cloth b, strip of kStrip = 120 output
+// Mapping: one warp per work unit (cloth b, strip of kStripDamp = 120 output
 // columns, output rows [r0, r1)).  Lane l holds the 4 consecutive columns
 // c0 - 4 + 4l .. c0 - 1 + 4l as float4 loads of the SoA planes.  The warp
 // marches down the rows with a register window of 4 position rows
@@ -56,7 +56,9 @@ __device__ __forceinline__ void load_row(Row<NC>& r, const float* base, int64_t 
     for (int c = 0; c < NC; ++c) {
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ok) t = __ldg(reinterpret_cast<const float4*>(base + (int64_t)(plane0 + c) * stride));
-        r.c[c][0] = t.x; r.c[c][1] = t.z; r.c[c][2] = t.y; r.c[c][3] = t.w;   // memory order c0 c2 c1 c3
+        const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r.c[c][k] = tv[col_slot(k)];
     }
 }
 
@@ -305,8 +307,14 @@ __global__ void __launch_bounds__(128, 3) plain_step_damp_kernel(StepArgs a)
                     if (c4 + 3 < cols) {
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            *reinterpret_cast<float4*>(dst + c * stride) = make_float4(un[c][0], un[c][2], un[c][1], un[c][3]);
-                            *reinterpret_cast<float4*>(dst + (c + 3) * stride) = make_float4(vn[c][0], vn[c][2], vn[c][1], vn[c][3]);
+                            float ou[4], ov[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                ou[col_slot(k)] = un[c][k];
+                                ov[col_slot(k)] = vn[c][k];
+                            }
+                            *reinterpret_cast<float4*>(dst + c * stride) = make_float4(ou[0], ou[1], ou[2], ou[3]);
+                            *reinterpret_cast<float4*>(dst + (c + 3) * stride) = make_float4(ov[0], ov[1], ov[2], ov[3]);
                         }
                     } else {
 #pragma unroll
