@@ -222,3 +222,65 @@ def test_full_size_batch_sampled_against_oracle():
         xr, _ = oracle.step(s, cfg["x"][b], cfg["v"][b], pins=cfg["pins"][b], steps=20)
         assert np.abs(got[b] - xr).max() <= X_TOL, (b, sizes[b])
     assert cb.status() == 0
+
+
+def _window(spec, x, v, r, c, rad):
+    """Sub-grid of radius `rad` around node (r, c), clipped at the cloth's
+    edges, as its own cloth spec and state; returns (spec, x, v, (r, c) in it)."""
+    r0, r1 = max(0, r - rad), min(spec["rows"], r + rad + 1)
+    c0, c1 = max(0, c - rad), min(spec["cols"], c + rad + 1)
+    s = dict(spec)
+    s["rows"], s["cols"] = r1 - r0, c1 - c0
+    # the window's lattice starts at (c0 h, r0 h): shift positions so that
+    # the rest state of the window is the oracle's lattice
+    sh = np.array([c0 * spec["h"], r0 * spec["h"], 0.0])
+    return s, x[r0:r1, c0:c1] - sh, v[r0:r1, c0:c1], (r - r0, c - c0), sh
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_maximum_size_cloth_sampled_against_oracle(steps):
+    """One 4096 x 4096 cloth (16.8M nodes, 0.8 GB of state): after `steps`
+    steps, sampled nodes (corners, edges, interior) equal the oracle run on
+    the window of radius 2 * steps around them, which holds every node they
+    depend on.  A node pinned and pressure on."""
+    n = 4096
+    rng = np.random.default_rng(91)
+    s = wl.cloth_spec(n, n, p=0.4)
+    x, v = wl.noisy_flat_state(s, 1e-4, rng)
+    pins = [0, n - 1]
+    cb = make([s], [pins], [x], [v])
+    cb.step(steps)
+    xg, vg = cb.get_state()
+    xg = xg.cpu().numpy().reshape(n, n, 3)
+    samples = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (1, 2), (n - 2, n // 2), (n // 2, 1),
+               (n // 2, n // 2)] + [tuple(int(t) for t in rng.integers(0, n, 2)) for _ in range(40)]
+    x64, v64 = x.astype(np.float64), v.astype(np.float64)
+    for (r, c) in samples:
+        ws, wx, wv, (wr, wc), sh = _window(s, x64, v64, r, c, 2 * steps)
+        wp = [p for p in pins if p // n in range(r - 2 * steps, r + 2 * steps + 1)]
+        wpins = [(p // n - (r - wr)) * ws["cols"] + (p % n - (c - wc)) for p in wp
+                 if 0 <= p // n - (r - wr) < ws["rows"] and 0 <= p % n - (c - wc) < ws["cols"]]
+        xr, _ = oracle.step(ws, wx, wv, pins=wpins, steps=steps)
+        assert np.abs(xg[r, c] - (xr[wr, wc] + sh)).max() <= X_TOL, (r, c)
+    assert cb.status() == 0
+    cb.close()
+
+
+def test_all_nodes_pinned_stay_put():
+    s = wl.cloth_spec(9, 13, p=0.5)
+    x, v = wl.sag_state(s, np.random.default_rng(92), amp=0.01, vamp=0.1)
+    cb = make([s], [list(range(9 * 13))], [x], [v])
+    cb.step(25)
+    xg, vg = cb.get_state()
+    assert torch.equal(xg, pack([x]).cuda()) and float(vg.abs().max()) == 0.0
+
+
+def test_coincident_nodes_flag_non_finite():
+    """Two neighbours at the same position make a zero-length spring: the
+    stretch is undefined and the status word reports it."""
+    s = wl.cloth_spec(4, 4)
+    x, v = wl.noisy_flat_state(s, 0.0, np.random.default_rng(93))
+    x[1, 2] = x[1, 1]
+    cb = make([s], [[]], [x], [v])
+    cb.step(1)
+    assert cb.status(clear=True) & 1

@@ -104,3 +104,33 @@ def test_bf16_net_step_is_deterministic():
         cb.step_net(Net(w, BF16), 5)
         outs.append(cb.get_state()[0])
     assert torch.equal(outs[0], outs[1])
+
+
+def test_bf16_maximum_size_cloth_sampled():
+    """One 2048 x 2048 cloth through the tensor-core network step: sampled
+    nodes equal the oracle's network step on the window of radius 3 (the
+    receptive field of the two 3x3 trunk convolutions and the 3x3 linear
+    branch) around them."""
+    n = 2048
+    rng = np.random.default_rng(94)
+    s = wl.cloth_spec(n, n, p=0.3)
+    x, v = wl.noisy_flat_state(s, 1e-3, rng)
+    v = (v + rng.normal(0, 0.05, v.shape)).astype(np.float32)
+    w = blob(95)
+    cb = ClothBatch([s], [[0]])
+    cb.set_state(pack([x]).cuda(), pack([v]).cuda())
+    cb.step_net(Net(w, BF16), 1)
+    xg = cb.get_state()[0].cpu().numpy().reshape(n, n, 3)
+    x64, v64 = x.astype(np.float64), v.astype(np.float64)
+    samples = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (2, 1000), (n // 2, n // 2)] + \
+              [tuple(int(t) for t in rng.integers(0, n, 2)) for _ in range(30)]
+    for (r, c) in samples:
+        r0, r1, c0, c1 = max(0, r - 3), min(n, r + 4), max(0, c - 3), min(n, c + 4)
+        ws = dict(s)
+        ws["rows"], ws["cols"] = r1 - r0, c1 - c0
+        sh = np.array([c0 * s["h"], r0 * s["h"], 0.0])
+        wpins = [0] if (r0, c0) == (0, 0) else []
+        xr, _ = oracle.net_step(w.astype(np.float64), ws, x64[r0:r1, c0:c1] - sh, v64[r0:r1, c0:c1],
+                                pins=wpins, steps=1)
+        assert np.abs(xg[r, c] - (xr[r - r0, c - c0] + sh)).max() <= 1e-4, (r, c)
+    assert cb.status() == 0
