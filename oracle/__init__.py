@@ -86,6 +86,7 @@ def _load():
             lib.oracle_cnn_forward.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, dp]
             lib.oracle_cnn_backward.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp]
             lib.oracle_pcell_accel.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp]
+            lib.oracle_pcell_backward.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp, dp, dp, dp, dp, dp]
             lib.oracle_cnn_param_count.restype = ctypes.c_int32
             lib.oracle_cnn_blob_count.restype = ctypes.c_int32
             assert lib.oracle_cnn_param_count() == N_PARAMS
@@ -289,6 +290,23 @@ def pcell_accel(w, c: dict, x, v) -> np.ndarray:
     return a
 
 
+def pcell_backward(w, c: dict, x, v, ga):
+    """(grad_w[40] with grad_w[39] = 0 (alpha fixed), grad_x, grad_v) of
+    sum(ga . pcell_accel(w, c, x, v)); shapes (rows, cols, 3)."""
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    assert w.shape == (PCELL_BLOB,), w.shape
+    rows, cols = int(c["rows"]), int(c["cols"])
+    x = _state(x, rows, cols)
+    v = _state(v, rows, cols)
+    ga = _state(ga, rows, cols)
+    gw = np.zeros(PCELL_BLOB)
+    gx = np.zeros((rows, cols, 3))
+    gv = np.zeros((rows, cols, 3))
+    _load().oracle_pcell_backward(rows, cols, _dptr(w), _dptr(x), _dptr(v), _dptr(ga), _dptr(gw), _dptr(gx),
+                                  _dptr(gv))
+    return gw, gx, gv
+
+
 def pcell_step(w, c: dict, x, v, pins=(), steps: int = 1):
     """Framework step of Fig. 2 with the literal cell: its acceleration plus
     the hard-encoded pressure (Eq. 3) drive Eq. 5 with pins and sphere
@@ -313,7 +331,7 @@ def pcell_step(w, c: dict, x, v, pins=(), steps: int = 1):
 
 # ---------------------------------------------------------------- loss (Eq. 8)
 def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_norm: float,
-                h_norm: float, with_grad: bool = True):
+                h_norm: float, with_grad: bool = True, cell: str = "cnn"):
     """Training loss of Eq. 8 for one window, and its gradient.
 
     Physics term: alpha * mean over free nodes and 3 components of
@@ -321,9 +339,13 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
     Data term: (1 - alpha) / S * sum_{s=1..S} mean over free nodes and
     components of ((x_hat_s - x_s) / h_norm)^2, where x_hat_s is the
     S-step unroll of `net_step` (no sphere) from (x0, v0).
-    Returns (loss, grad_w[13027]) — grad by the hand-written adjoint of the
-    unroll: Euler, pins, pressure and the cell's backward.
+    Returns (loss, grad_w) — grad by the hand-written adjoint of the
+    unroll: Euler, pins, pressure and the cell's backward.  `cell` is "cnn"
+    (the C-cell, grad_w[13027]) or "pcell" (the literal cell, grad_w[40]
+    with the fixed alpha's entry 0).
     """
+    assert cell in ("cnn", "pcell")
+    accel = net_accel if cell == "cnn" else pcell_accel
     rows, cols = int(c["rows"]), int(c["cols"])
     dt, m = float(c["dt"]), float(c["m"])
     S = int(np.asarray(x_targets).shape[0])
@@ -333,7 +355,7 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
     vs = [np.array(v0, dtype=np.float64)]
     accs = []
     for t in range(S):
-        a = net_accel(w, c, xs[t], vs[t])
+        a = accel(w, c, xs[t], vs[t])
         accs.append(a)
         vn = free * (vs[t] + dt * (a + pressure_force(c, xs[t]) / m))
         vs.append(vn)
@@ -348,7 +370,7 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
     if not with_grad:
         return loss, None
 
-    gw = np.zeros(N_PARAMS)
+    gw = np.zeros(N_PARAMS if cell == "cnn" else PCELL_BLOB)
     gx = np.zeros((rows, cols, 3))
     gv = np.zeros((rows, cols, 3))
     for t in range(S, 0, -1):
@@ -360,12 +382,16 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
             ga = ga + alpha * 2.0 * free * da / (g_norm * cnt)
         gx_prev = gx + pressure_vjp(c, xs[t - 1], dt * wv / m)
         gv_prev = wv
-        gwt, gz = cnn_backward(w, net_input(c, xs[t - 1], vs[t - 1]),
-                               np.ascontiguousarray(ga.transpose(2, 0, 1)[None]))
+        if cell == "cnn":
+            gwt, gz = cnn_backward(w, net_input(c, xs[t - 1], vs[t - 1]),
+                                   np.ascontiguousarray(ga.transpose(2, 0, 1)[None]))
+            gz = gz[0].transpose(1, 2, 0)        # rows, cols, 6
+            gxc, gvc = gz[..., 0:3], gz[..., 3:6]   # u = x - X
+        else:
+            gwt, gxc, gvc = pcell_backward(w, c, xs[t - 1], vs[t - 1], ga)
         gw += gwt
-        gz = gz[0].transpose(1, 2, 0)            # rows, cols, 6
-        gx = gx_prev + gz[..., 0:3]              # u = x - X
-        gv = gv_prev + gz[..., 3:6]
+        gx = gx_prev + gxc
+        gv = gv_prev + gvc
     return loss, gw
 
 

@@ -55,3 +55,47 @@ void oracle_pcell_accel(int32_t rows, int32_t cols, const double* w, const doubl
         }
     }
 }
+
+/* Backward of oracle_pcell_accel for a cotangent ga [rows][cols][3]: the
+ * gradient of sum(ga . a) with respect to the 39 trainable parameters
+ * (w_L, w_N, w_D, b_L; alpha is a fixed hyper-parameter) added to gw, and
+ * with respect to x and v added to gx, gv.  Per channel term
+ * t = w_L phi + w_N s + w_D xi s, s = phi (1 + alpha phi^2)^(-1/2):
+ *   dt/dphi = w_L + (w_N + w_D xi) (1 + alpha phi^2)^(-3/2),
+ *   dt/dxi = w_D s,  and phi = x_j - x_i, xi = v_j - v_i. */
+void oracle_pcell_backward(int32_t rows, int32_t cols, const double* w, const double* x, const double* v,
+                           const double* ga, double* gw, double* gx, double* gv)
+{
+    const double* wL = w;
+    const double* wN = w + 12;
+    const double* wD = w + 24;
+    const double alpha = w[39];
+    for (int r = 0; r < rows; ++r) {
+        for (int c = 0; c < cols; ++c) {
+            const int64_t i = (int64_t)r * cols + c;
+            for (int k = 0; k < 3; ++k) {
+                const double g = ga[3 * i + k];
+                gw[36 + k] += g;
+                for (int ch = 0; ch < 12; ++ch) {
+                    const int rr = r + kDy[ch], cc = c + kDx[ch];
+                    if (rr < 0 || rr >= rows || cc < 0 || cc >= cols) continue;
+                    const int64_t j = (int64_t)rr * cols + cc;
+                    const double phi = x[3 * j + k] - x[3 * i + k];
+                    const double xi = v[3 * j + k] - v[3 * i + k];
+                    const double q = 1.0 + alpha * phi * phi;
+                    const double s = phi / sqrt(q);
+                    const double ds = 1.0 / (q * sqrt(q));
+                    gw[ch] += g * phi;
+                    gw[12 + ch] += g * s;
+                    gw[24 + ch] += g * xi * s;
+                    const double gphi = g * (wL[ch] + (wN[ch] + wD[ch] * xi) * ds);
+                    const double gxi = g * wD[ch] * s;
+                    gx[3 * j + k] += gphi;
+                    gx[3 * i + k] -= gphi;
+                    gv[3 * j + k] += gxi;
+                    gv[3 * i + k] -= gxi;
+                }
+            }
+        }
+    }
+}

@@ -150,3 +150,84 @@ def test_step_free_fall_closed_form():
     # symplectic Euler: v_n = v0 + n dt g, x_n = x0 + n dt v0 + dt^2 g n (n+1) / 2
     assert np.allclose(v, v0 + n * dt * g, rtol=0, atol=1e-13)
     assert np.allclose(x, x0 + n * dt * v0 + dt * dt * g * n * (n + 1) / 2, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- backward
+def test_backward_matches_central_differences():
+    """Gradient of sum(ga . a) for every trainable parameter and for random
+    directions in x and v, against central differences (eps 1e-6)."""
+    s = wl.cloth_spec(4, 5)
+    x, v = rand_state(s, 9)
+    w = rand_w(10, alpha=300.0)
+    ga = np.random.default_rng(11).normal(size=x.shape)
+    f = lambda ww, xx, vv: float((ga * oracle.pcell_accel(ww, s, xx, vv)).sum())  # noqa: E731
+    gw, gx, gv = oracle.pcell_backward(w, s, x, v, ga)
+    eps = 1e-6
+    for p in range(39):
+        e = np.zeros(40)
+        e[p] = eps
+        fd = (f(w + e, x, v) - f(w - e, x, v)) / (2 * eps)
+        assert abs(gw[p] - fd) <= 1e-6 * max(1.0, abs(fd)), p
+    assert gw[39] == 0.0
+    rng = np.random.default_rng(12)
+    for _ in range(4):
+        dx, dv = rng.normal(size=x.shape) * 1e-3, rng.normal(size=v.shape)
+        dx /= np.linalg.norm(dx); dv /= np.linalg.norm(dv)
+        fdx = (f(w, x + eps * dx, v) - f(w, x - eps * dx, v)) / (2 * eps)
+        fdv = (f(w, x, v + eps * dv) - f(w, x, v - eps * dv)) / (2 * eps)
+        assert abs((gx * dx).sum() - fdx) <= 1e-6 * max(1.0, abs(fdx))
+        assert abs((gv * dv).sum() - fdv) <= 1e-6 * max(1.0, abs(fdv))
+
+
+def test_backward_matches_torch_autograd():
+    """The cell rewritten as torch ops on CPU (FP64, shifted slices per
+    channel), differentiated by autograd: a second reference."""
+    torch = pytest.importorskip("torch")
+    s = wl.cloth_spec(5, 6)
+    x, v = rand_state(s, 13)
+    w = rand_w(14, alpha=50.0)
+    ga = np.random.default_rng(15).normal(size=x.shape)
+    X = torch.tensor(x, requires_grad=True)
+    V = torch.tensor(v, requires_grad=True)
+    Wt = torch.tensor(w, requires_grad=True)
+    rows, cols = s["rows"], s["cols"]
+    a = Wt[36:39].expand(rows, cols, 3).clone()
+    for ch, (dy, dx) in enumerate(oracle.PCELL_CHANNELS):
+        ys, xs_ = slice(max(0, -dy), rows - max(0, dy)), slice(max(0, -dx), cols - max(0, dx))
+        yj, xj = slice(max(0, dy), rows - max(0, -dy)), slice(max(0, dx), cols - max(0, -dx))
+        phi = X[yj, xj] - X[ys, xs_]
+        xi = V[yj, xj] - V[ys, xs_]
+        sg = phi / torch.sqrt(1 + Wt[39] * phi * phi)
+        term = torch.zeros(rows, cols, 3, dtype=torch.float64)
+        term[ys, xs_] = Wt[ch] * phi + Wt[12 + ch] * sg + Wt[24 + ch] * xi * sg
+        a = a + term
+    assert np.abs(a.detach().numpy() - oracle.pcell_accel(w, s, x, v)).max() <= 1e-12
+    (a * torch.tensor(ga)).sum().backward()
+    gw, gx, gv = oracle.pcell_backward(w, s, x, v, ga)
+    assert np.abs(gw[:39] - Wt.grad.numpy()[:39]).max() <= 1e-9 * np.abs(gw).max()
+    assert np.abs(gx - X.grad.numpy()).max() <= 1e-9 * np.abs(gx).max()
+    assert np.abs(gv - V.grad.numpy()).max() <= 1e-9 * np.abs(gv).max()
+
+
+def test_unrolled_loss_gradient_matches_central_differences():
+    """Eq. 8 through a 3-step unroll with the literal cell: the adjoint's
+    parameter gradient against central differences of the loss."""
+    s = wl.cloth_spec(5, 6, p=0.4)
+    x0, v0 = rand_state(s, 17, amp=0.005, vamp=0.05)
+    pins = [0, 5]
+    w = np.asarray(wl.pcell_blob(18), dtype=np.float64)
+    tg, xt, vt = [], x0, v0
+    for _ in range(3):
+        xt, vt = oracle.step(s, xt, vt, pins=pins, steps=1)
+        tg.append(xt)
+    a_true = (oracle.total_force(s, x0, v0) - oracle.pressure_force(s, x0)) / s["m"]
+    args = (s, pins, x0, v0, np.array(tg), a_true, 0.5, 9.81, s["h"])
+    loss, gw = oracle.unroll_loss(w, *args, cell="pcell")
+    for p in list(range(0, 39, 3)) + [36, 37, 38]:
+        eps = 1e-3 * max(1.0, abs(w[p]))   # the loss is ~1e6: a smaller step drowns in rounding
+        e = np.zeros(40)
+        e[p] = eps
+        lp, _ = oracle.unroll_loss(w + e, *args, with_grad=False, cell="pcell")
+        lm, _ = oracle.unroll_loss(w - e, *args, with_grad=False, cell="pcell")
+        fd = (lp - lm) / (2 * eps)
+        assert abs(gw[p] - fd) <= 1e-5 * max(abs(fd), 1e-12 * abs(loss) / eps), (p, gw[p], fd)
