@@ -379,6 +379,14 @@ int cloth_train_workspace_size(const cloth_ctx* ctx, int32_t S, size_t* bytes);
 int cloth_train_loss(cloth_ctx* ctx, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
                      float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream);
 
+/* The same loss and gradient with the literal cell (d_w: CLOTH_PCELL_BLOB
+ * floats, see cloth_pcell_accel) as the network: ADDS the gradient with
+ * respect to its 39 trainable entries to d_grad_w[0..38] (alpha, entry 39,
+ * is fixed and left alone).  Same workspace (cloth_train_workspace_size);
+ * the parameter gradient is summed in a fixed order (bitwise reproducible). */
+int cloth_train_loss_pcell(cloth_ctx* ctx, const float* d_w, int32_t S, const float* d_targets, float alpha,
+                           float g_norm, float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream);
+
 /* One Adam update (Table 1's optimizer) of n parameters in place:
  * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
  * w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).

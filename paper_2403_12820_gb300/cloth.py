@@ -219,6 +219,28 @@ class ClothBatch:
                   ctypes.c_float(g_norm), _ptr(loss), _ptr(grad_w), _ptr(ws), ws.numel(), self._s())
         return loss, grad_w
 
+    def train_loss_pcell(self, w, S: int, targets: torch.Tensor, alpha: float = 0.5, g_norm: float = 9.81,
+                         grad_w: torch.Tensor | None = None):
+        """Eq. 8 with the literal cell (weights w, 40 floats): loss (1,) and
+        grad_w (40,), the gradient added to the first 39 entries."""
+        _require_cuda(targets, "targets")
+        if targets.numel() != S * 3 * self.total_nodes:
+            raise ValueError("targets must hold S * total_nodes * 3 floats")
+        w = self._pcell_w(w, self.device)
+        n = ctypes.c_size_t()
+        _lib.call("cloth_train_workspace_size", self.handle, int(S), ctypes.byref(n))
+        ws = getattr(self, "_train_ws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+            self._train_ws = ws
+        if grad_w is None:
+            grad_w = torch.zeros(_lib.PCELL_BLOB, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _lib.call("cloth_train_loss_pcell", self.handle, _ptr(w), int(S), _ptr(targets), ctypes.c_float(alpha),
+                  ctypes.c_float(g_norm), _ptr(loss), _ptr(grad_w), _ptr(ws), ws.numel(), self._s())
+        self._pcell_keep = w
+        return loss, grad_w
+
     def topology(self, b: int) -> torch.Tensor:
         s = self.specs[b]
         m = torch.empty(int(s["rows"]) * int(s["cols"]), dtype=torch.int16, device=self.device)

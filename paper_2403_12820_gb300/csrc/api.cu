@@ -318,7 +318,7 @@ int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wor
 
 // Workspace of cloth_train_loss (float offsets).
 struct TrainWs {
-    size_t z, a, at, ga0, gu, gv, ga, gfp, ge, gn, gz, saved, fabi, coef, part, total;
+    size_t z, a, at, ga0, gu, gv, ga, gfp, ge, gn, gz, saved, fabi, coef, part, ppart, total;
 };
 TrainWs train_ws(const cloth_ctx* c, int S)
 {
@@ -334,6 +334,7 @@ TrainWs train_ws(const cloth_ctx* c, int S)
     w.fabi = take((size_t)3 * c->total_nodes);
     w.coef = take((size_t)2 * B);
     w.part = take((size_t)(S + 1) * train_blocks(c->grids[0].rows, c->grids[0].cols, c->B));
+    w.ppart = take((size_t)40 * pcell_train_blocks(c->grids[0].rows, c->grids[0].cols, c->B));
     w.total = off * sizeof(float);
     return w;
 }
@@ -356,16 +357,22 @@ int cloth_train_workspace_size(const cloth_ctx* c, int32_t S, size_t* bytes)
     return CLOTH_OK;
 }
 
-int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
-                     float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
+}  // extern "C"
+
+namespace {
+
+// Eq. 8 for the windows held by the context, with the cell given by
+// `forward(z_t, a)` (a = cell(z_t)) and `backward(z_t, ga, gz)` (gz = dL/dz_t
+// through the cell, the parameter gradient added to the caller's grad_w).
+template <class Fwd, class Bwd>
+int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha, float g_norm, float* d_loss,
+                    void* d_work, size_t bytes, cudaStream_t s, Fwd forward, Bwd backward)
 {
-    if (!c || !net || !d_targets || !d_loss || !d_grad_w || !d_work || S < 1 || !same_size(c)) return CLOTH_EINVAL;
+    if (!d_targets || !d_loss || !d_work || S < 1 || !same_size(c)) return CLOTH_EINVAL;
     if (!(alpha >= 0.f && alpha <= 1.f) || !(g_norm > 0.f)) return CLOTH_EINVAL;
-    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
     const TrainWs L = train_ws(c, S);
     if (bytes < L.total) return CLOTH_ENOMEM;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int B = c->B, H = c->grids[0].rows, W = c->grids[0].cols;
     const int64_t HW = (int64_t)H * W, NHW = (int64_t)B * HW;
     float* ws = static_cast<float*>(d_work);
@@ -373,7 +380,7 @@ int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_tar
     auto Zt = [&](int t) { return Z + (size_t)t * B * 6 * HW; };
     float *A = ws + L.a, *AT = ws + L.at, *GA0 = ws + L.ga0, *GU = ws + L.gu, *GV = ws + L.gv;
     float *GA = ws + L.ga, *GFP = ws + L.gfp, *GE = ws + L.ge, *GN = ws + L.gn, *GZ = ws + L.gz;
-    float *SAVED = ws + L.saved, *FABI = ws + L.fabi, *COEF = ws + L.coef, *PART = ws + L.part;
+    float *FABI = ws + L.fabi, *COEF = ws + L.coef, *PART = ws + L.part;
     const int blocks = train_blocks(H, W, B);
     const ClothDesc* D = c->d_desc();
     const uint32_t* P = c->d_pins();
@@ -394,20 +401,9 @@ int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_tar
     CK(launch_state_to_z(D, c->d_state(c->cur), Zt(0), B, H, W, s));
     CK(launch_a_true(D, FABI, Zt(0), AT, B, H, W, s));
 
-    auto forward = [&](int t) {   // a = cell(z_t), layer outputs into SAVED
-        NetFwdArgs f{};
-        f.src.z = Zt(t);
-        f.w = net->d_w();
-        f.t1 = SAVED + kSavT1 * NHW;
-        f.t2 = SAVED + kSavT2 * NHW;
-        f.s = SAVED + kSavS * NHW;
-        f.a = A;
-        f.N = B; f.H = H; f.W = W;
-        return launch_net_forward_simt(f, s);
-    };
     // forward unroll: a_t, z_{t+1}, loss terms
     for (int t = 0; t < S; ++t) {
-        CK(forward(t));
+        CK(forward(Zt(t), A));
         if (t == 0) CK(launch_phys_term(D, P, A, AT, COEF, GA0, PART, B, H, W, s));
         CK(launch_train_euler(D, P, Zt(t), A, Zt(t + 1), B, H, W, s));
         CK(launch_data_term(D, P, Zt(t + 1), d_targets + (size_t)t * 3 * c->total_nodes, COEF + B, nullptr,
@@ -423,11 +419,60 @@ int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_tar
                             B, H, W, s));
         CK(launch_euler_adjoint(D, P, GU, GV, t == 1 ? GA0 : nullptr, GA, GFP, B, H, W, s));
         CK(launch_pressure_vjp(D, Zt(t - 1), GFP, GE, GN, GU, B, H, W, s));
-        CK(forward(t - 1));
-        CK(launch_net_backward_simt(net->d_w(), Zt(t - 1), SAVED, GA, GZ, net->d_part(), d_grad_w, B, H, W, s));
+        CK(backward(Zt(t - 1), GA, GZ));
         CK(launch_add_gz(GZ, GU, GV, B, H, W, s));
     }
     return CLOTH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
+                     float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !net || !d_grad_w) return CLOTH_EINVAL;
+    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
+    if (S < 1) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const TrainWs L = train_ws(c, S);
+    const int B = c->B, H = c->grids[0].rows, W = c->grids[0].cols;
+    const int64_t NHW = (int64_t)B * H * W;
+    float* SAVED = static_cast<float*>(d_work) + L.saved;
+    auto forward = [&](const float* z, float* a) {   // a = cell(z_t), layer outputs into SAVED
+        NetFwdArgs f{};
+        f.src.z = z;
+        f.w = net->d_w();
+        f.t1 = SAVED + kSavT1 * NHW;
+        f.t2 = SAVED + kSavT2 * NHW;
+        f.s = SAVED + kSavS * NHW;
+        f.a = a;
+        f.N = B; f.H = H; f.W = W;
+        return launch_net_forward_simt(f, s);
+    };
+    auto backward = [&](const float* z, const float* ga, float* gz) {
+        cudaError_t e = forward(z, static_cast<float*>(d_work) + L.a);   // recompute the step's activations
+        if (e != cudaSuccess) return e;
+        return launch_net_backward_simt(net->d_w(), z, SAVED, ga, gz, net->d_part(), d_grad_w, B, H, W, s);
+    };
+    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward);
+}
+
+int cloth_train_loss_pcell(cloth_ctx* c, const float* d_w, int32_t S, const float* d_targets, float alpha,
+                           float g_norm, float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !d_w || !d_grad_w || S < 1) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const TrainWs L = train_ws(c, S);
+    const int B = c->B, H = c->grids[0].rows, W = c->grids[0].cols;
+    float* PP = static_cast<float*>(d_work) + L.ppart;
+    const ClothDesc* D = c->d_desc();
+    auto forward = [&](const float* z, float* a) { return launch_pcell_fwd_z(D, d_w, z, a, B, H, W, s); };
+    auto backward = [&](const float* z, const float* ga, float* gz) {
+        return launch_pcell_bwd_z(D, d_w, z, ga, gz, PP, d_grad_w, B, H, W, s);
+    };
+    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward);
 }
 
 int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32_t n, int32_t t, float lr,

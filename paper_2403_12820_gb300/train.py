@@ -41,20 +41,26 @@ class Dataset:
 
 class Trainer:
     """Batches of `batch` windows, each an `unroll`-step stretch of one
-    trajectory; Adam (Table 1) with lr 1e-3."""
+    trajectory; Adam (Table 1) with lr 1e-3.  `cell` is "cnn" (the C-cell,
+    FP32) or "pcell" (the literal cell: 39 trainable weights, alpha fixed)."""
 
     def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
-                 alpha: float = 0.5, seed: int = 7, device="cuda"):
+                 alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn"):
+        if cell not in ("cnn", "pcell"):
+            raise ValueError("cell must be 'cnn' or 'pcell'")
         self.data, self.batch, self.unroll, self.lr, self.alpha = data, batch, unroll, lr, alpha
+        self.cell = cell
         self.rng = np.random.default_rng(seed)
         h = data.cfg["specs"][0]["h"]
         if blob is None:
-            blob = wl.kaiming_blob(2004, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
+            blob = (wl.kaiming_blob(2004, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
+                    if cell == "cnn" else wl.pcell_blob(2006, h=h))
         self.w = torch.from_numpy(np.asarray(blob, dtype=np.float32)).to(device)
-        self.m = torch.zeros(N_PARAMS, device=device)
-        self.v = torch.zeros(N_PARAMS, device=device)
+        self.n_params = N_PARAMS if cell == "cnn" else 39
+        self.m = torch.zeros(self.n_params, device=device)
+        self.v = torch.zeros(self.n_params, device=device)
         self.t = 0
-        self.net = Net(blob, FP32, device=device)
+        self.net = Net(blob, FP32, device=device) if cell == "cnn" else None
         self.device = device
 
     def sample(self):
@@ -76,9 +82,12 @@ class Trainer:
         specs, pins, x0, v0, tg = self.sample()
         cb = ClothBatch(specs, pins, device=self.device)
         cb.set_state(x0, v0)
-        self.net.set_weights(self.w)
-        loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
+        if self.cell == "cnn":
+            self.net.set_weights(self.w)
+            loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
+        else:
+            loss, g = cb.train_loss_pcell(self.w, self.unroll, tg, alpha=self.alpha)
         self.t += 1
-        adam_step(self.w, g, self.m, self.v, self.t, lr=self.lr, n=N_PARAMS)
+        adam_step(self.w, g, self.m, self.v, self.t, lr=self.lr, n=self.n_params)
         cb.close()
         return float(loss.item())
