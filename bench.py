@@ -532,11 +532,23 @@ def run_train(args, dev):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     win = 64 * 8 * data.nodes
-    return {"workload": "train: 512 trajectories of 64 x 64 x 200 plain steps (seed 1004); batch 64 windows, "
-                        "8-step unroll, Adam lr 1e-3, FP32",
-            "iters_per_s": iters / el, "windows_per_s": 64 * iters / el,
-            "unrolled_node_steps_per_s": win * iters / el, "iters": iters,
-            "dataset_generation_s": gen_s, "loss_first": losses[0], "loss_last": losses[-1]}
+    out = {"workload": "train: 512 trajectories of 64 x 64 x 200 plain steps (seed 1004); batch 64 windows, "
+                       "8-step unroll, Adam lr 1e-3, FP32",
+           "iters_per_s": iters / el, "windows_per_s": 64 * iters / el,
+           "unrolled_node_steps_per_s": win * iters / el, "iters": iters,
+           "dataset_generation_s": gen_s, "loss_first": losses[0], "loss_last": losses[-1]}
+    # the same iterations with the literal cell (39 trainable weights)
+    tp = Trainer(data, batch=64, unroll=8, device=dev, cell="pcell")
+    lp = [tp.step() for _ in range(3)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        lp.append(tp.step())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["pcell"] = {"iters_per_s": iters / el, "unrolled_node_steps_per_s": win * iters / el,
+                    "loss_first": lp[0], "loss_last": lp[-1]}
+    return out
 
 
 def main(argv=None):
