@@ -66,3 +66,19 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(1e-4), None, 0, None) == -1
     assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(0.0), ctypes.c_void_p(256), 1 << 20, None) == -1
     assert lib.cloth_create(ctypes.byref(h), 1, g, p, None, None, ctypes.c_float(1e-4), ctypes.c_void_p(256), 16, None) == -2
+
+
+def test_missing_library_and_toolchain_fail_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: with no built library and no nvcc, loading raises."""
+    from paper_2403_12820_gb300 import build as bld
+
+    def no_nvcc():
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libcloth")
+
+    monkeypatch.setattr(bld, "LIB", str(tmp_path / "libcloth.so"))
+    monkeypatch.setattr(bld, "_nvcc", no_nvcc)
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        _lib.load()
+    with pytest.raises(RuntimeError, match="not found"):
+        _lib.load(build_if_needed=False)
