@@ -112,6 +112,31 @@ struct WtW1T {
     }
 };
 
+// ----------------------------------------------------------------- staging
+// Element e (0 <= e < count) of a tile: value get(e) stored by put(e, value).
+// Each thread issues kBatch loads before it stores any of them, so a batch
+// costs one memory latency instead of kBatch (the source is reached through
+// a generic pointer, so the compiler would not move the loads above the
+// shared-memory stores by itself).
+constexpr int kBatch = 8;
+template <class Get, class Put>
+__device__ __forceinline__ void stage_tile(int count, int tid, int nthreads, Get get, Put put)
+{
+    for (int e0 = tid; e0 < count; e0 += kBatch * nthreads) {
+        float v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e = e0 + k * nthreads;
+            v[k] = e < count ? get(e) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e = e0 + k * nthreads;
+            if (e < count) put(e, v[k]);
+        }
+    }
+}
+
 // ----------------------------------------------------------------- conv
 // out(img, o, y, x) = sum_{i, ky, kx} W(o, i, ky, kx) in(img, i, y+ky-1, x+kx-1)
 // with zero outside [0, H) x [0, W).  Grid: (tiles_x, tiles_y, images).
@@ -124,15 +149,15 @@ __global__ void __launch_bounds__(NT) conv3x3_kernel(In in, Wt wt, Out out, int 
     float* s_in = s_w + 9 * CIN * COUTP;                   // [CIN][TH+2][TW+2]
     const int img = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
     const int tid = threadIdx.x;
-    for (int e = tid; e < 9 * CIN * COUTP; e += NT) {
+    stage_tile(9 * CIN * COUTP, tid, NT, [&](int e) {
         const int tap = e / (CIN * COUTP), rem = e % (CIN * COUTP), i = rem / COUTP, o = rem % COUTP;
-        s_w[e] = o < COUT ? wt(img, o, i, tap) : 0.f;
-    }
-    for (int e = tid; e < CIN * (TH + 2) * (TW + 2); e += NT) {
+        return o < COUT ? wt(img, o, i, tap) : 0.f;
+    }, [&](int e, float v) { s_w[e] = v; });
+    stage_tile(CIN * (TH + 2) * (TW + 2), tid, NT, [&](int e) {
         const int i = e / ((TH + 2) * (TW + 2)), rem = e % ((TH + 2) * (TW + 2));
         const int y = y0 + rem / (TW + 2) - 1, x = x0 + rem % (TW + 2) - 1;
-        s_in[e] = (y >= 0 && y < H && x >= 0 && x < W) ? in(img, i, y, x) : 0.f;
-    }
+        return (y >= 0 && y < H && x >= 0 && x < W) ? in(img, i, y, x) : 0.f;
+    }, [&](int e, float v) { s_in[e] = v; });
     __syncthreads();
     const int tx = tid & 31, ty = tid >> 5;
     float acc0[COUTP], acc1[COUTP];
@@ -196,17 +221,17 @@ __global__ void __launch_bounds__(NT) branch_fwd_kernel(const float* __restrict_
     float* sPhi = sB + 8;                             // [32][TH+2][TW+2]
     const int n = blockIdx.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, tid = threadIdx.x;
     const int64_t HW = (int64_t)H * W;
-    for (int e = tid; e < 3 * kC * 9; e += NT) sWL[e] = w[kOffWL + e];
-    for (int e = tid; e < kC * kC; e += NT) sP[e] = w[kOffP + e];
+    stage_tile(3 * kC * 9, tid, NT, [&](int e) { return w[kOffWL + e]; }, [&](int e, float v) { sWL[e] = v; });
+    stage_tile(kC * kC, tid, NT, [&](int e) { return w[kOffP + e]; }, [&](int e, float v) { sP[e] = v; });
     for (int e = tid; e < 3 * kC; e += NT) { sWN[e] = w[kOffWN + e]; sWD[e] = w[kOffWD + e]; }
     if (tid < 3) { sB[tid] = w[kOffBL + tid]; sB[3 + tid] = w[kOffOuts + tid]; }
     const float* phi = t2 + (int64_t)n * 2 * kC * HW;
     const float* xi = phi + kC * HW;
-    for (int e = tid; e < kC * (TH + 2) * (TW + 2); e += NT) {
+    stage_tile(kC * (TH + 2) * (TW + 2), tid, NT, [&](int e) {
         const int i = e / ((TH + 2) * (TW + 2)), rem = e % ((TH + 2) * (TW + 2));
         const int y = y0 + rem / (TW + 2) - 1, x = x0 + rem % (TW + 2) - 1;
-        sPhi[e] = (y >= 0 && y < H && x >= 0 && x < W) ? phi[i * HW + (int64_t)y * W + x] : 0.f;
-    }
+        return (y >= 0 && y < H && x >= 0 && x < W) ? phi[i * HW + (int64_t)y * W + x] : 0.f;
+    }, [&](int e, float v) { sPhi[e] = v; });
     __syncthreads();
     const int tx = tid & 31, x = x0 + tx;
     for (int half = 0; half < 2; ++half) {
@@ -263,8 +288,8 @@ __global__ void __launch_bounds__(NT) branch_bwd_kernel(const float* __restrict_
     float* sGy = sB + 8;                              // [3][TH+2][TW+2]
     const int n = blockIdx.z, N = gridDim.z, x0 = blockIdx.x * TW, y0 = blockIdx.y * TH, tid = threadIdx.x;
     const int64_t HW = (int64_t)H * W, NHW = (int64_t)N * HW;
-    for (int e = tid; e < 3 * kC * 9; e += NT) sWL[e] = w[kOffWL + e];
-    for (int e = tid; e < kC * kC; e += NT) sP[e] = w[kOffP + e];
+    stage_tile(3 * kC * 9, tid, NT, [&](int e) { return w[kOffWL + e]; }, [&](int e, float v) { sWL[e] = v; });
+    stage_tile(kC * kC, tid, NT, [&](int e) { return w[kOffP + e]; }, [&](int e, float v) { sP[e] = v; });
     for (int e = tid; e < 3 * kC; e += NT) { sWN[e] = w[kOffWN + e]; sWD[e] = w[kOffWD + e]; }
     if (tid < 3) sB[tid] = w[kOffOuts + tid];
     __syncthreads();
@@ -349,15 +374,15 @@ __global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, 
         const int i = tile / (tiles_x * tiles_y), rem = tile % (tiles_x * tiles_y);
         const int y0 = (rem / tiles_x) * TH, x0 = (rem % tiles_x) * TW;
         __syncthreads();
-        for (int e = tid; e < CA * TH * TW; e += blockDim.x) {
+        stage_tile(CA * TH * TW, tid, blockDim.x, [&](int e) {
             const int a = e / (TH * TW), r2 = e % (TH * TW), y = y0 + r2 / TW, x = x0 + r2 % TW;
-            sA[e] = (y < H && x < W) ? A(i, a, y, x) : 0.f;
-        }
-        for (int e = tid; e < CB * BH * BW; e += blockDim.x) {
+            return (y < H && x < W) ? A(i, a, y, x) : 0.f;
+        }, [&](int e, float v) { sA[e] = v; });
+        stage_tile(CB * BH * BW, tid, blockDim.x, [&](int e) {
             const int bb = e / (BH * BW), r2 = e % (BH * BW);
             const int y = y0 + r2 / BW - HB, x = x0 + r2 % BW - HB;
-            sB[bb * BPL + r2] = (y >= 0 && y < H && x >= 0 && x < W) ? B(i, bb, y, x) : 0.f;
-        }
+            return (y >= 0 && y < H && x >= 0 && x < W) ? B(i, bb, y, x) : 0.f;
+        }, [&](int e, float v) { sB[(e / (BH * BW)) * BPL + e % (BH * BW)] = v; });
         __syncthreads();
         if (ab < CA / ABLK) {
             for (int py = 0; py < TH; ++py)
