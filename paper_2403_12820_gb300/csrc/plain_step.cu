@@ -121,6 +121,16 @@ __device__ __forceinline__ void acc2(f2 (&a)[3], f2 s, const f2 (&d)[3])
 __device__ __forceinline__ float shup(float v) { return __shfl_up_sync(kFull, v, 1); }
 __device__ __forceinline__ float shdn(float v) { return __shfl_down_sync(kFull, v, 1); }
 
+// Per-warp constants of the current unit for the update (Eq. 4-5): read
+// from shared memory where they are used, instead of being held in
+// registers through the spring arithmetic or re-read from the descriptor
+// in global memory after every row's stores.
+struct UnitConst {
+    float dt, dtm, keep, dtg[3];   // dt, dt/m, 1 - dt d/m, dt g
+    int32_t pin_wpr, sph_on;
+    const uint32_t* pins;          // the cloth's pin bitmask
+};
+
 // Stiffness pairs of the 12 springs a lane evaluates per row, indexed
 // [spring][thread]: E, 2E, N, 2N, NE, NW of pair A, then of pair B.
 enum { kE, kT, kN, k2N, kNE, kNW };
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
     // p/4): E and W masks, the own-node weight -(mE + mW), and the lattice
     // part of d'_E - d'_W along x.
     __shared__ float2 s_pc[8][128];
+    __shared__ UnitConst s_uc[4];
     const int lane = threadIdx.x & 31;
     float2* kp = &s_kp[0][threadIdx.x];
     float2* pc = &s_pc[0][threadIdx.x];
@@ -164,6 +175,19 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
         const bool oA0 = bit(1);   // column c4 exists
         const float hs = D.h;
         const float pq = D.p_quarter;
+        volatile UnitConst* uc = &s_uc[threadIdx.x >> 5];
+        if (lane == 0) {
+            uc->dt = D.dt;
+            uc->dtm = D.dt * D.inv_m;
+            uc->keep = 1.f - D.dt * D.inv_m * D.drag;
+            uc->dtg[0] = D.dt * D.gx;
+            uc->dtg[1] = D.dt * D.gy;
+            uc->dtg[2] = D.dt * D.gz;
+            uc->pin_wpr = D.pin_wpr;
+            uc->sph_on = D.sph_on;
+            uc->pins = a.pinmask + D.pin_off;
+        }
+        __syncwarp();
         {
             // pressure masks: the E neighbour of each half exists (mE) / the
             // W neighbour exists (mW, stored negated)
@@ -399,16 +423,16 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                     // v' = v + dt/m (f_int + f_p - d v + m g) = dt/m (f_int + f_p)
                     //      + ((1 - d dt/m) v + dt g): Eq. 4-5 with the
                     // constant terms folded
-                    const f2 dt = F2(D.dt), dtm = F2(D.dt * D.inv_m);
-                    const f2 keep = F2(1.f - D.dt * D.inv_m * D.drag);
-                    const f2 dtg[3] = {F2(D.dt * D.gx), F2(D.dt * D.gy), F2(D.dt * D.gz)};
+                    const f2 dt = F2(uc->dt), dtm = F2(uc->dtm);
+                    const f2 keep = F2(uc->keep);
+                    const f2 dtg[3] = {F2(uc->dtg[0]), F2(uc->dtg[1]), F2(uc->dtg[2])};
                     Row2 un, vn;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         vn.A[c] = fma2(dtm, F0.A[c], fma2(keep, V0.A[c], dtg[c]));
                         vn.B[c] = fma2(dtm, F0.B[c], fma2(keep, V0.B[c], dtg[c]));
                     }
-                    const uint32_t pw = __ldg(a.pinmask + D.pin_off + (int64_t)r * D.pin_wpr + (c4 >> 5));
+                    const uint32_t pw = __ldg(uc->pins + (int64_t)r * uc->pin_wpr + (c4 >> 5));
                     const unsigned pb = (pw >> (c4 & 31)) & 0xfu;
                     if (pb) {   // Dirichlet nodes: C holds their velocity at zero
 #pragma unroll
@@ -424,7 +448,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                         un.A[c] = fma2(dt, vn.A[c], P0.A[c]);
                         un.B[c] = fma2(dt, vn.B[c], P0.B[c]);
                     }
-                    if (D.sph_on) {
+                    if (uc->sph_on) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             // column c4 + k sits in pair A (k even) or B (k odd), half k / 2
