@@ -45,6 +45,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=400)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--graph-chunk", type=int, default=100)
+    p.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cnn", action="store_true")
@@ -252,6 +253,16 @@ def run_plain(args, rank, world, local):
     chunk = args.graph_chunk
     stream = torch.cuda.current_stream()
 
+    # launch shape picked by the autotuner (untimed; the state does not move)
+    if args.no_tune:
+        seg, wps, _ = cb.get_launch()
+        launch = {"seg_rows": seg, "warps_per_sm": wps, "tuned": False}
+    else:
+        from paper_2403_12820_gb300 import tune
+        rec = tune.autotune(cb, candidates=tune.DEFAULT_CANDIDATES, warmup=3, steps=20)
+        launch = {"seg_rows": rec["seg_rows"], "warps_per_sm": rec["warps_per_sm"], "tuned": True,
+                  "candidates_us": {f"{R},{w}": round(t, 2) for R, w, t in rec["candidates"]}}
+
     cb.rollout(args.warmup, graph_chunk=chunk)
     torch.cuda.synchronize()
     barrier(world)
@@ -285,7 +296,7 @@ def run_plain(args, rank, world, local):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "plain_batch: 64 cloths, sides U{64..512} (seed 1002), 5.97M nodes, FP32, "
                                f"CUDA graphs of {chunk} steps",
-                   "global_batch": 64 * world, "nodes_per_gpu": nodes,
+                   "global_batch": 64 * world, "nodes_per_gpu": nodes, "launch": launch,
                    "l2": "inputs larger than L2 (306 MB double-buffered state vs 129 MB L2)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth)", "traffic": traffic,

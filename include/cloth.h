@@ -169,6 +169,20 @@ int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* st
  * Synchronises `stream`. */
 int cloth_set_launch(cloth_ctx* ctx, int32_t seg_rows, int32_t warps_per_sm, void* stream);
 
+/* Launch-shape autotuner of the plain step.  For each of the n candidates
+ * (seg_rows[i], warps_per_sm[i]), in cloth_set_launch's ranges (seg_rows
+ * >= 4 or -1 for balanced ranges; warps_per_sm 1..64 or -1 for the
+ * default), runs `warmup` untimed and then `steps` timed plain steps on
+ * `stream`, timed with CUDA events, and writes the mean microseconds per
+ * step to us_out[i] (host array of n).  The steps read the current state
+ * and write only the other state buffer: the state is unchanged.  The
+ * fastest candidate is then applied as by cloth_set_launch and its index
+ * written to *best (host).  CLOTH_EINVAL, before anything runs, for n < 1,
+ * null arrays, warmup < 0, steps < 1 or a candidate out of range.  Cached
+ * graphs are dropped.  Synchronises `stream`. */
+int cloth_tune_launch(cloth_ctx* ctx, int32_t n, const int32_t* seg_rows, const int32_t* warps_per_sm,
+                      int32_t warmup, int32_t steps, float* us_out, int32_t* best, void* stream);
+
 /* Current launch shape: seg_rows (0 = balanced ranges), warps_per_sm (0 =
  * the default), number of work units. */
 int cloth_get_launch(const cloth_ctx* ctx, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units);

@@ -61,6 +61,8 @@ SIGNATURES = {
     "cloth_topology": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "cloth_set_launch": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
     "cloth_get_launch": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int32)]),
+    "cloth_tune_launch": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32), c_int32, c_int32, P(c_float),
+                                    P(c_int32), c_void_p]),
     "cloth_status": (c_int32, [c_void_p, P(c_int32), c_int32, c_void_p]),
     "net_workspace_size": (c_int32, [P(c_size_t)]),
     "net_create": (c_int32, [P(c_void_p), c_int32, P(c_float), c_void_p, c_size_t, c_void_p]),

@@ -123,6 +123,18 @@ class ClothBatch:
     def set_launch(self, seg_rows: int = 0, warps_per_sm: int = 0) -> None:
         _lib.call("cloth_set_launch", self.handle, int(seg_rows), int(warps_per_sm), self._s())
 
+    def tune_launch(self, candidates: list[tuple[int, int]], warmup: int = 3, steps: int = 20) -> tuple[int, list[float]]:
+        """Time each (seg_rows, warps_per_sm) candidate through cloth_tune_launch;
+        the fastest is applied.  Returns (index of the fastest, us per step)."""
+        n = len(candidates)
+        seg = (ctypes.c_int32 * n)(*[int(c[0]) for c in candidates])
+        wps = (ctypes.c_int32 * n)(*[int(c[1]) for c in candidates])
+        us = (ctypes.c_float * n)()
+        best = ctypes.c_int32()
+        _lib.call("cloth_tune_launch", self.handle, n, seg, wps, int(warmup), int(steps), us, ctypes.byref(best),
+                  self._s())
+        return best.value, [float(v) for v in us]
+
     def get_launch(self) -> tuple[int, int, int]:
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _lib.call("cloth_get_launch", self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))

@@ -923,6 +923,57 @@ int cloth_set_launch(cloth_ctx* c, int32_t seg_rows, int32_t warps_per_sm, void*
     return CLOTH_OK;
 }
 
+int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const int32_t* warps_per_sm, int32_t warmup,
+                      int32_t steps, float* us_out, int32_t* best, void* stream)
+{
+    if (!c || n < 1 || !seg_rows || !warps_per_sm || !us_out || !best || warmup < 0 || steps < 1) return CLOTH_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const int R = seg_rows[i], w = warps_per_sm[i];
+        if (!(R == -1 || R >= kMinSegRows) || !(w == -1 || (w >= 1 && w <= 64))) return CLOTH_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    // apply candidate i as cloth_set_launch would (-1: balanced / default)
+    auto apply = [&](int i) {
+        c->warps_per_sm = warps_per_sm[i] > 0 ? warps_per_sm[i] : 0;
+        return set_work(c, seg_rows[i] > 0 ? seg_rows[i] : 0, s);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = CLOTH_OK;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    // every timed step reads the current state and writes the other buffer,
+    // so the state the caller sees does not move
+    const float* src = c->d_state(c->cur);
+    float* dst = c->d_state(c->cur ^ 1);
+    for (int i = 0; i < n && rc == CLOTH_OK && ce == cudaSuccess; ++i) {
+        rc = apply(i);
+        for (int k = 0; k < warmup && rc == CLOTH_OK; ++k) rc = launch_plain(c, src, dst, nullptr, s);
+        if (rc) break;
+        if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) break;
+        for (int k = 0; k < steps && rc == CLOTH_OK; ++k) rc = launch_plain(c, src, dst, nullptr, s);
+        if (rc) break;
+        if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) break;
+        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        us_out[i] = ms * 1000.f / (float)steps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(ce);
+    if (rc) return rc;
+    int b = 0;
+    for (int i = 1; i < n; ++i)
+        if (us_out[i] < us_out[b]) b = i;
+    *best = b;
+    rc = apply(b);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    return CLOTH_OK;
+}
+
 int cloth_get_launch(const cloth_ctx* c, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units)
 {
     if (!c) return CLOTH_EINVAL;
