@@ -11,7 +11,10 @@ The arithmetic lives in plain C files compiled on demand with gcc
 ``pcell_oracle.c``: the cell of Eq. 6-7 read literally, with frozen
 difference channels and ISRU).  This module marshals numpy arrays and
 composes those primitives into the network step of Fig. 2 and the training
-loss of Eq. 8, step by step.
+loss of Eq. 8, step by step.  ``stages.py`` (numpy) holds the training
+stages around that loss (Sec. 3.2.1, Table 1): the differential-evolution
+pre-process, the learning-rate schedules and the masked Adam update of
+branch-wise fine-tuning.
 
 Array conventions: a cloth state is ``x, v`` of shape ``(rows, cols, 3)``
 float64; node (r, c) rests at ``X = (c h, r h, 0)``.
@@ -402,3 +405,7 @@ def adam_step(theta, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+from .stages import (CNN_GROUPS, PCELL_GROUPS, adam_step_masked, de_minimize, group_mask,  # noqa: E402,F401
+                     lr_cosine, lr_step, scaled_blob)

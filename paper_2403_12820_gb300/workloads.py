@@ -196,3 +196,23 @@ def pcell_blob(seed: int = 2005, h: float = H_DEFAULT, m: float = M_DEFAULT, k=K
     w[36:39] = g
     w[39] = 1.0 / (2.0 * h) ** 2
     return w.astype(np.float32)
+
+
+def de_draws(seed: int = 2007, pop: int = 36, dim: int = 6, generations: int = 20) -> dict:
+    """Random numbers of one differential-evolution run, drawn up front:
+    init (pop, dim) uniforms in [0, 1) for the starting population; idx
+    (generations, pop, 3) three distinct members other than i for member i;
+    jrand (generations, pop) a component index; cross (generations, pop,
+    dim) uniforms in [0, 1) for the crossover."""
+    if pop < 4 or dim < 1 or generations < 0:
+        raise ValueError("differential evolution needs pop >= 4, dim >= 1, generations >= 0")
+    rng = np.random.default_rng(seed)
+    init = rng.random((pop, dim))
+    idx = np.empty((generations, pop, 3), dtype=np.int64)
+    for g in range(generations):
+        for i in range(pop):
+            k = rng.choice(pop - 1, size=3, replace=False)
+            idx[g, i] = k + (k >= i)
+    jrand = rng.integers(0, dim, size=(generations, pop))
+    cross = rng.random((generations, pop, dim))
+    return {"init": init, "idx": idx, "jrand": jrand, "cross": cross}
