@@ -388,7 +388,9 @@ int cloth_train_workspace_size(const cloth_ctx* ctx, int32_t S, size_t* bytes);
  * CLOTH_NET_PARAMS weights to d_grad_w.  The gradient is the exact adjoint
  * (net_backward through every step, the Euler update, pins and pressure);
  * each step's activations are recomputed during the backward sweep (step
- * checkpointing).  The context state is left unchanged.  FP32 networks only
+ * checkpointing).  d_grad_w may be NULL: the loss alone, without the
+ * backward sweep (the objective of the differential-evolution pre-process
+ * of Sec. 3.2.1).  The context state is left unchanged.  FP32 networks only
  * (CLOTH_EUNSUPPORTED otherwise); CLOTH_EINVAL if the cloths differ in size. */
 int cloth_train_loss(cloth_ctx* ctx, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
                      float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream);
@@ -396,8 +398,9 @@ int cloth_train_loss(cloth_ctx* ctx, cloth_net* net, int32_t S, const float* d_t
 /* The same loss and gradient with the literal cell (d_w: CLOTH_PCELL_BLOB
  * floats, see cloth_pcell_accel) as the network: ADDS the gradient with
  * respect to its 39 trainable entries to d_grad_w[0..38] (alpha, entry 39,
- * is fixed and left alone).  Same workspace (cloth_train_workspace_size);
- * the parameter gradient is summed in a fixed order (bitwise reproducible). */
+ * is fixed and left alone); d_grad_w may be NULL (the loss alone).  Same
+ * workspace (cloth_train_workspace_size); the parameter gradient is summed
+ * in a fixed order (bitwise reproducible). */
 int cloth_train_loss_pcell(cloth_ctx* ctx, const float* d_w, int32_t S, const float* d_targets, float alpha,
                            float g_norm, float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream);
 
@@ -407,6 +410,12 @@ int cloth_train_loss_pcell(cloth_ctx* ctx, const float* d_w, int32_t S, const fl
  * All pointers are device arrays of n floats; t >= 1 is the step count. */
 int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32_t n, int32_t t, float lr,
                   float beta1, float beta2, float eps, void* stream);
+
+/* The same update on the entries whose byte of d_mask (device, n bytes) is
+ * non-zero; the others keep w, m and v.  Branch-wise fine-tuning with the
+ * other branches frozen (Sec. 5): the mask selects the trainable groups. */
+int net_adam_step_masked(float* d_w, const float* d_grad, float* d_m, float* d_v, const uint8_t* d_mask, int32_t n,
+                         int32_t t, float lr, float beta1, float beta2, float eps, void* stream);
 
 /* Release the context's host resources (graphs, capture stream). */
 void cloth_destroy(cloth_ctx* ctx);

@@ -80,6 +80,8 @@ SIGNATURES = {
                                    c_size_t, c_void_p]),
     "cloth_train_loss_pcell": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_float, c_float, c_void_p, c_void_p,
                                          c_void_p, c_size_t, c_void_p]),
+    "net_adam_step_masked": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_float,
+                                       c_float, c_float, c_float, c_void_p]),
     "net_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_float, c_float, c_float,
                                 c_float, c_void_p]),
     "cloth_step_net": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),

@@ -211,10 +211,11 @@ class ClothBatch:
         _lib.call("cloth_reset_modes", self.handle, self._s())
 
     def train_loss(self, net, S: int, targets: torch.Tensor, alpha: float = 0.5, g_norm: float = 9.81,
-                   grad_w: torch.Tensor | None = None):
+                   grad_w: torch.Tensor | None = None, with_grad: bool = True):
         """Eq. 8 loss of the windows held by this batch (current state = window
         start) against `targets` (S, total_nodes, 3); adds its gradient to
-        grad_w (created zero if None).  Returns (loss (1,), grad_w)."""
+        grad_w (created zero if None).  Returns (loss (1,), grad_w); with
+        with_grad False only the loss (no backward sweep) and grad_w None."""
         _require_cuda(targets, "targets")
         if targets.numel() != S * 3 * self.total_nodes:
             raise ValueError("targets must hold S * total_nodes * 3 floats")
@@ -224,17 +225,20 @@ class ClothBatch:
         if ws is None or ws.numel() < n.value:
             ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
             self._train_ws = ws
-        if grad_w is None:
+        if grad_w is None and with_grad:
             grad_w = torch.zeros(13027, dtype=torch.float32, device=self.device)
+        if not with_grad:
+            grad_w = None
         loss = torch.empty(1, dtype=torch.float32, device=self.device)
         _lib.call("cloth_train_loss", self.handle, net.handle, int(S), _ptr(targets), ctypes.c_float(alpha),
                   ctypes.c_float(g_norm), _ptr(loss), _ptr(grad_w), _ptr(ws), ws.numel(), self._s())
         return loss, grad_w
 
     def train_loss_pcell(self, w, S: int, targets: torch.Tensor, alpha: float = 0.5, g_norm: float = 9.81,
-                         grad_w: torch.Tensor | None = None):
+                         grad_w: torch.Tensor | None = None, with_grad: bool = True):
         """Eq. 8 with the literal cell (weights w, 40 floats): loss (1,) and
-        grad_w (40,), the gradient added to the first 39 entries."""
+        grad_w (40,), the gradient added to the first 39 entries (None with
+        with_grad False: the loss alone)."""
         _require_cuda(targets, "targets")
         if targets.numel() != S * 3 * self.total_nodes:
             raise ValueError("targets must hold S * total_nodes * 3 floats")
@@ -245,8 +249,10 @@ class ClothBatch:
         if ws is None or ws.numel() < n.value:
             ws = torch.empty(n.value, dtype=torch.uint8, device=self.device)
             self._train_ws = ws
-        if grad_w is None:
+        if grad_w is None and with_grad:
             grad_w = torch.zeros(_lib.PCELL_BLOB, dtype=torch.float32, device=self.device)
+        if not with_grad:
+            grad_w = None
         loss = torch.empty(1, dtype=torch.float32, device=self.device)
         _lib.call("cloth_train_loss_pcell", self.handle, _ptr(w), int(S), _ptr(targets), ctypes.c_float(alpha),
                   ctypes.c_float(g_norm), _ptr(loss), _ptr(grad_w), _ptr(ws), ws.numel(), self._s())

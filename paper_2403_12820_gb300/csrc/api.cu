@@ -366,7 +366,7 @@ namespace {
 // through the cell, the parameter gradient added to the caller's grad_w).
 template <class Fwd, class Bwd>
 int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha, float g_norm, float* d_loss,
-                    void* d_work, size_t bytes, cudaStream_t s, Fwd forward, Bwd backward)
+                    void* d_work, size_t bytes, cudaStream_t s, Fwd forward, Bwd backward, bool with_grad)
 {
     if (!d_targets || !d_loss || !d_work || S < 1 || !same_size(c)) return CLOTH_EINVAL;
     if (!(alpha >= 0.f && alpha <= 1.f) || !(g_norm > 0.f)) return CLOTH_EINVAL;
@@ -410,6 +410,7 @@ int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha
                             PART + (size_t)(t + 1) * blocks, B, H, W, s));
     }
     CK(launch_sum_partials(PART, (S + 1) * blocks, d_loss, s));
+    if (!with_grad) return CLOTH_OK;
 
     // backward sweep, recomputing each step's activations (step checkpointing)
     CK(cudaMemsetAsync(GU, 0, sizeof(float) * 3 * NHW, s));
@@ -432,7 +433,7 @@ extern "C" {
 int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_targets, float alpha, float g_norm,
                      float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
 {
-    if (!c || !net || !d_grad_w) return CLOTH_EINVAL;
+    if (!c || !net) return CLOTH_EINVAL;
     if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
     if (S < 1) return CLOTH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -456,13 +457,14 @@ int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_tar
         if (e != cudaSuccess) return e;
         return launch_net_backward_simt(net->d_w(), z, SAVED, ga, gz, net->d_part(), d_grad_w, B, H, W, s);
     };
-    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward);
+    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward,
+                           d_grad_w != nullptr);
 }
 
 int cloth_train_loss_pcell(cloth_ctx* c, const float* d_w, int32_t S, const float* d_targets, float alpha,
                            float g_norm, float* d_loss, float* d_grad_w, void* d_work, size_t bytes, void* stream)
 {
-    if (!c || !d_w || !d_grad_w || S < 1) return CLOTH_EINVAL;
+    if (!c || !d_w || S < 1) return CLOTH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const TrainWs L = train_ws(c, S);
     const int B = c->B, H = c->grids[0].rows, W = c->grids[0].cols;
@@ -472,14 +474,23 @@ int cloth_train_loss_pcell(cloth_ctx* c, const float* d_w, int32_t S, const floa
     auto backward = [&](const float* z, const float* ga, float* gz) {
         return launch_pcell_bwd_z(D, d_w, z, ga, gz, PP, d_grad_w, B, H, W, s);
     };
-    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward);
+    return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward,
+                           d_grad_w != nullptr);
 }
 
 int net_adam_step(float* d_w, const float* d_grad, float* d_m, float* d_v, int32_t n, int32_t t, float lr,
                   float beta1, float beta2, float eps, void* stream)
 {
     if (!d_w || !d_grad || !d_m || !d_v || n < 1 || t < 1) return CLOTH_EINVAL;
-    CK(launch_adam(d_w, d_grad, d_m, d_v, n, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)));
+    CK(launch_adam(d_w, d_grad, d_m, d_v, nullptr, n, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
+int net_adam_step_masked(float* d_w, const float* d_grad, float* d_m, float* d_v, const uint8_t* d_mask, int32_t n,
+                         int32_t t, float lr, float beta1, float beta2, float eps, void* stream)
+{
+    if (!d_w || !d_grad || !d_m || !d_v || !d_mask || n < 1 || t < 1) return CLOTH_EINVAL;
+    CK(launch_adam(d_w, d_grad, d_m, d_v, d_mask, n, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)));
     return CLOTH_OK;
 }
 

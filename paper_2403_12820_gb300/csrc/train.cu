@@ -261,11 +261,13 @@ __global__ void add_gz_kernel(const float* __restrict__ gz, float* __restrict__ 
     }
 }
 
+// Entries whose mask byte is 0 (mask set) keep w, m and v: frozen groups.
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2)
+                            float* __restrict__ v, const uint8_t* __restrict__ mask, int n, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (mask && !mask[i])) return;
     const float mi = fmaf(b1, m[i], (1.f - b1) * g[i]);
     const float vi = fmaf(b2, v[i], (1.f - b2) * g[i] * g[i]);
     m[i] = mi;
@@ -333,11 +335,11 @@ cudaError_t launch_add_gz(const float* gz, float* gu, float* gv, int B, int H, i
     add_gz_kernel<<<grid2(H, W, B), TB, 0, s>>>(gz, gu, gv, H, W);
     return cudaGetLastError();
 }
-cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, int t, float lr, float b1, float b2,
-                        float eps, cudaStream_t s)
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, const uint8_t* mask, int n, int t, float lr,
+                        float b1, float b2, float eps, cudaStream_t s)
 {
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
-    adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, mask, n, lr, b1, b2, eps, c1, c2);
     return cudaGetLastError();
 }
 

@@ -24,8 +24,8 @@ cudaError_t launch_euler_adjoint(const ClothDesc* d, const uint32_t* pins, const
 cudaError_t launch_pressure_vjp(const ClothDesc* d, const float* z, const float* gfp, float* ge, float* gn, float* gu,
                                 int B, int H, int W, cudaStream_t s);
 cudaError_t launch_add_gz(const float* gz, float* gu, float* gv, int B, int H, int W, cudaStream_t s);
-cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, int t, float lr, float b1, float b2,
-                        float eps, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, const uint8_t* mask, int n, int t, float lr,
+                        float b1, float b2, float eps, cudaStream_t s);
 // The literal cell on the training layout (pcell_train.cu).
 int pcell_train_blocks(int H, int W, int B);
 cudaError_t launch_pcell_fwd_z(const ClothDesc* d, const float* w, const float* z, float* a, int B, int H, int W,

@@ -97,12 +97,20 @@ class Net:
 
 
 def adam_step(w: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, t: int, lr: float = 1e-3,
-              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n: int | None = None) -> None:
-    """One in-place Adam update of the first n entries of w (libcloth kernel)."""
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, n: int | None = None,
+              mask: torch.Tensor | None = None) -> None:
+    """One in-place Adam update of the first n entries of w (libcloth kernel);
+    with `mask` (uint8 CUDA tensor of n bytes) only where it is non-zero."""
     n = int(n if n is not None else g.numel())
-    _lib.call("net_adam_step", _ptr(w), _ptr(g), _ptr(m), _ptr(v), n, int(t), ctypes.c_float(lr),
-              ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps),
-              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if mask is None:
+        _lib.call("net_adam_step", _ptr(w), _ptr(g), _ptr(m), _ptr(v), n, int(t), ctypes.c_float(lr),
+                  ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps), stream)
+        return
+    if not (mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous() and mask.numel() >= n):
+        raise ValueError("mask must be a contiguous uint8 CUDA tensor of at least n entries")
+    _lib.call("net_adam_step_masked", _ptr(w), _ptr(g), _ptr(m), _ptr(v), _ptr(mask), n, int(t), ctypes.c_float(lr),
+              ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps), stream)
 
 
 class CellFunction(torch.autograd.Function):

@@ -11,6 +11,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+from . import stages
 from . import workloads as wl
 from .cloth import ClothBatch, pack
 from .net import FP32, N_BLOB, N_PARAMS, Net, adam_step
@@ -42,10 +43,14 @@ class Dataset:
 class Trainer:
     """Batches of `batch` windows, each an `unroll`-step stretch of one
     trajectory; Adam (Table 1) with lr 1e-3.  `cell` is "cnn" (the C-cell,
-    FP32) or "pcell" (the literal cell: 39 trainable weights, alpha fixed)."""
+    FP32) or "pcell" (the literal cell: 39 trainable weights, alpha fixed).
+    `lr_schedule` (a callable of the 0-based iteration, e.g. stages.StepLR or
+    stages.CosineLR) replaces the constant lr; `trainable` (group names of
+    stages.mask_groups) freezes every other group (branch-wise fine-tuning)."""
 
     def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
-                 alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn"):
+                 alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn", lr_schedule=None,
+                 trainable=None):
         if cell not in ("cnn", "pcell"):
             raise ValueError("cell must be 'cnn' or 'pcell'")
         self.data, self.batch, self.unroll, self.lr, self.alpha = data, batch, unroll, lr, alpha
@@ -62,6 +67,37 @@ class Trainer:
         self.t = 0
         self.net = Net(blob, FP32, device=device) if cell == "cnn" else None
         self.device = device
+        self.lr_schedule = lr_schedule
+        self.mask = None
+        self.set_trainable(trainable)
+
+    def set_trainable(self, trainable=None) -> None:
+        """Train only the named groups (None: every parameter)."""
+        if trainable is None:
+            self.mask = None
+            return
+        m = stages.freeze_mask(self.cell, trainable, self.n_params)
+        self.mask = torch.from_numpy(m).to(self.device)
+
+    def lr_at(self, t: int) -> float:
+        return float(self.lr_schedule(t)) if self.lr_schedule is not None else self.lr
+
+    def pre_process(self, draws, bounds=(-4.0, 4.0), F: float = 0.5, CR: float = 0.9) -> dict:
+        """Differential-evolution pre-process (Sec. 3.2.1): fix the group signs
+        and scales on one sampled batch of windows, apply them to the weights
+        and restart Adam's moments.  Returns the DE record."""
+        specs, pins, x0, v0, tg = self.sample()
+        obj = stages.WindowLoss(self.cell, self.w.detach().cpu().numpy(), specs, pins, x0, v0, tg,
+                                alpha=self.alpha, device=self.device)
+        try:
+            res = stages.de_preprocess(obj, draws, bounds=bounds, F=F, CR=CR)
+        finally:
+            obj.close()
+        self.w.copy_(torch.from_numpy(res["blob"]).to(self.device))
+        self.m.zero_()
+        self.v.zero_()
+        self.t = 0
+        return res
 
     def sample(self):
         """Windows (trajectory, start) and a ClothBatch holding their cloths."""
@@ -87,7 +123,8 @@ class Trainer:
             loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
         else:
             loss, g = cb.train_loss_pcell(self.w, self.unroll, tg, alpha=self.alpha)
+        lr = self.lr_at(self.t)
         self.t += 1
-        adam_step(self.w, g, self.m, self.v, self.t, lr=self.lr, n=self.n_params)
+        adam_step(self.w, g, self.m, self.v, self.t, lr=lr, n=self.n_params, mask=self.mask)
         cb.close()
         return float(loss.item())
