@@ -55,6 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--no-train", action="store_true")
     p.add_argument("--no-pcell", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
+    p.add_argument("--de-generations", type=int, default=6)
     return p.parse_args(argv)
 
 
@@ -559,6 +560,20 @@ def run_train(args, dev):
     el = time.perf_counter() - t0
     out["pcell"] = {"iters_per_s": iters / el, "unrolled_node_steps_per_s": win * iters / el,
                     "loss_first": lp[0], "loss_last": lp[-1]}
+    # the differential-evolution pre-process (Sec. 3.2.1, Table 1): 36
+    # members x 6 group scales; every member is one loss-only Eq. 8 call on
+    # one batch of 64 windows
+    from paper_2403_12820_gb300 import workloads as wl
+    out["de_preprocess"] = {}
+    for cell, gens in (("pcell", args.de_generations), ("cnn", max(1, args.de_generations // 2))):
+        td = Trainer(data, batch=64, unroll=8, device=dev, cell=cell)
+        res = td.pre_process(wl.de_draws(seed=2007, pop=36, dim=6, generations=gens))
+        out["de_preprocess"][cell] = {
+            "population": 36, "generations": gens, "evals": res["evals"], "seconds": res["seconds"],
+            "evals_per_s": res["evals"] / res["seconds"],
+            "unrolled_node_steps_per_s": res["evals"] * win / res["seconds"],
+            "loss_unscaled": float(res["initial_fitness"][0]), "loss_best": res["f"],
+            "scales": [round(float(v), 4) for v in res["x"]]}
     return out
 
 

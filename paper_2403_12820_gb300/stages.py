@@ -118,7 +118,8 @@ def differential_evolution(objective, lo, hi, draws, F: float = 0.5, CR: float =
     binomial crossover (component j from the mutant where cross < CR, and at
     jrand), trials clipped to [lo, hi], then each member replaced by its trial
     where the trial's objective is not larger.  Returns a dict: x, f (the
-    best), history (best after each generation), population, fitness, evals."""
+    best), history (best after each generation), population, fitness,
+    initial_fitness (of the starting population), evals."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     P = lo + np.asarray(draws["init"], dtype=np.float64) * (hi - lo)
@@ -126,6 +127,7 @@ def differential_evolution(objective, lo, hi, draws, F: float = 0.5, CR: float =
     if first is not None:
         P[0] = np.asarray(first, dtype=np.float64)
     fit = np.array([float(objective(p)) for p in P])
+    fit0 = fit.copy()
     evals = NP
     history = []
     rows = np.arange(NP)
@@ -143,7 +145,7 @@ def differential_evolution(objective, lo, hi, draws, F: float = 0.5, CR: float =
         history.append(float(fit.min()))
     b = int(np.argmin(fit))
     return {"x": P[b].copy(), "f": float(fit[b]), "history": history, "population": P, "fitness": fit,
-            "evals": evals}
+            "initial_fitness": fit0, "evals": evals}
 
 
 class WindowLoss:
