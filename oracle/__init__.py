@@ -64,6 +64,7 @@ class _Cloth(ctypes.Structure):
         ("mu", ctypes.c_double), ("drag", ctypes.c_double), ("p", ctypes.c_double),
         ("g", ctypes.c_double * 3), ("dt", ctypes.c_double),
         ("sphere_on", ctypes.c_int32), ("sphere_c", ctypes.c_double * 3), ("sphere_r", ctypes.c_double),
+        ("sphere_mu", ctypes.c_double), ("pin_v", ctypes.c_double * 3),
     ]
 
 
@@ -84,6 +85,7 @@ def _load():
             lib.oracle_external_force.argtypes = [cp, dp, dp]
             lib.oracle_pressure_vjp.argtypes = [cp, dp, dp, dp]
             lib.oracle_step.argtypes = [cp, P(ctypes.c_uint8), dp, dp, ctypes.c_int32]
+            lib.oracle_update.argtypes = [cp, P(ctypes.c_uint8), dp, dp, dp]
             lib.oracle_energy.argtypes = [cp, dp, dp]
             lib.oracle_energy.restype = ctypes.c_double
             lib.oracle_cnn_forward.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp, dp]
@@ -113,11 +115,16 @@ def _cloth(c: dict) -> _Cloth:
         s.g[a] = float(c["g"][a])
     s.dt = float(c.get("dt", 0.0))
     sph = c.get("sphere")
+    s.sphere_mu = -1.0
     if sph is not None:
         s.sphere_on = 1
         for a in range(3):
             s.sphere_c[a] = float(sph["center"][a])
         s.sphere_r = float(sph["radius"])
+        s.sphere_mu = float(sph.get("friction", -1.0))
+    pv = c.get("pin_v", (0.0, 0.0, 0.0))
+    for a in range(3):
+        s.pin_v[a] = float(pv[a])
     return s
 
 
@@ -204,6 +211,22 @@ def step(c: dict, x, v, pins=(), steps: int = 1):
     return x, v
 
 
+def update(c: dict, x, v, acc, pins=()):
+    """One Eq. 5 update for the acceleration `acc` (rows, cols, 3): pinned
+    nodes take the pin velocity c["pin_v"] (default 0), then sphere contact
+    (c["sphere"]["friction"]: < 0 or absent = the node stops, else Coulomb).
+    Returns new (x, v)."""
+    rows, cols = int(c["rows"]), int(c["cols"])
+    x = _state(x, rows, cols).copy()
+    v = _state(v, rows, cols).copy()
+    acc = _state(acc, rows, cols)
+    pm = pin_mask(c, pins)
+    s = _cloth(c)
+    _load().oracle_update(ctypes.byref(s), pm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(acc),
+                          _dptr(x), _dptr(v))
+    return x, v
+
+
 def energy(c: dict, x, v) -> float:
     rows, cols = int(c["rows"]), int(c["cols"])
     x = _state(x, rows, cols)
@@ -261,19 +284,9 @@ def net_step(w, c: dict, x, v, pins=(), steps: int = 1):
     pressure (Eq. 3) drive Eq. 5 with pins and sphere contact."""
     x = np.array(x, dtype=np.float64)
     v = np.array(v, dtype=np.float64)
-    pm = pin_mask(c, pins).reshape(int(c["rows"]), int(c["cols"]), 1).astype(bool)
-    sph = c.get("sphere")
     for _ in range(steps):
         acc = net_accel(w, c, x, v) + pressure_force(c, x) / float(c["m"])
-        v = v + float(c["dt"]) * acc
-        v = np.where(pm, 0.0, v)
-        x = x + float(c["dt"]) * v
-        if sph is not None:
-            d = x - np.asarray(sph["center"], dtype=np.float64)
-            ln = np.sqrt((d * d).sum(axis=2, keepdims=True))
-            inside = (ln < float(sph["radius"])) & (ln > 0.0)
-            x = np.where(inside, np.asarray(sph["center"]) + float(sph["radius"]) * d / np.where(ln > 0, ln, 1.0), x)
-            v = np.where(inside, 0.0, v)
+        x, v = update(c, x, v, acc, pins)
     return x, v
 
 
@@ -316,19 +329,9 @@ def pcell_step(w, c: dict, x, v, pins=(), steps: int = 1):
     contact."""
     x = np.array(x, dtype=np.float64)
     v = np.array(v, dtype=np.float64)
-    pm = pin_mask(c, pins).reshape(int(c["rows"]), int(c["cols"]), 1).astype(bool)
-    sph = c.get("sphere")
     for _ in range(steps):
         acc = pcell_accel(w, c, x, v) + pressure_force(c, x) / float(c["m"])
-        v = v + float(c["dt"]) * acc
-        v = np.where(pm, 0.0, v)
-        x = x + float(c["dt"]) * v
-        if sph is not None:
-            d = x - np.asarray(sph["center"], dtype=np.float64)
-            ln = np.sqrt((d * d).sum(axis=2, keepdims=True))
-            inside = (ln < float(sph["radius"])) & (ln > 0.0)
-            x = np.where(inside, np.asarray(sph["center"]) + float(sph["radius"]) * d / np.where(ln > 0, ln, 1.0), x)
-            v = np.where(inside, 0.0, v)
+        x, v = update(c, x, v, acc, pins)
     return x, v
 
 
@@ -353,6 +356,7 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
     dt, m = float(c["dt"]), float(c["m"])
     S = int(np.asarray(x_targets).shape[0])
     free = (1 - pin_mask(c, pins)).reshape(rows, cols, 1).astype(np.float64)
+    pin_v = np.asarray(c.get("pin_v", (0.0, 0.0, 0.0)), dtype=np.float64)   # pinned nodes move with it
     cnt = 3.0 * free.sum()
     xs = [np.array(x0, dtype=np.float64)]
     vs = [np.array(v0, dtype=np.float64)]
@@ -360,7 +364,7 @@ def unroll_loss(w, c: dict, pins, x0, v0, x_targets, a_true, alpha: float, g_nor
     for t in range(S):
         a = accel(w, c, xs[t], vs[t])
         accs.append(a)
-        vn = free * (vs[t] + dt * (a + pressure_force(c, xs[t]) / m))
+        vn = free * (vs[t] + dt * (a + pressure_force(c, xs[t]) / m)) + (1.0 - free) * pin_v
         vs.append(vn)
         xs.append(xs[t] + dt * vn)
     da = (accs[0] - np.asarray(a_true)) / g_norm

@@ -23,11 +23,17 @@
  *    i.e. the pressure times its lumped area.  The 4 ordered pairs are
  *    (E,N), (N,W), (W,S), (S,E), which gives a flat cloth the normal +z; a
  *    pair contributes only when both of its nodes exist.
- *  - The constraint operator C of Eq. 5 zeroes the velocity of pinned nodes
- *    before the position update; M^-1 is the inverse lumped (uniform) mass.
+ *  - The constraint operator C of Eq. 5 sets the velocity of pinned nodes
+ *    to the velocity of the object they move with (zero for a fixed node,
+ *    the Dirichlet case) before the position update; M^-1 is the inverse
+ *    lumped (uniform) mass.
  *  - Sphere contact (intersection elimination, Sec. 3.1) is a projection of
- *    the updated position onto the sphere surface with the velocity zeroed,
- *    applied after the update.
+ *    the updated position onto the sphere surface, applied after the
+ *    update.  The velocity then either stops (the ball of Sec. 3.2.2 that
+ *    absorbs the bounce and whose friction prevents relative motion; a
+ *    negative friction coefficient) or, for a coefficient mu >= 0, loses
+ *    its approaching normal part and Coulomb friction reduces its
+ *    tangential part by at most mu times that normal part.
  */
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +53,8 @@ typedef struct {
     int32_t sphere_on;                 /* sphere contact enabled                 */
     double sphere_c[3];
     double sphere_r;
+    double sphere_mu;                  /* < 0: contact sticks; else Coulomb mu   */
+    double pin_v[3];                   /* velocity of the pinned nodes, m/s      */
 } oracle_cloth;
 
 /* The 13-point stencil: the centre plus these 12 neighbour offsets (dr, dc).
@@ -229,7 +237,10 @@ void oracle_total_force(const oracle_cloth* c, const double* x, const double* v,
 }
 
 /* Sphere contact: a node found inside the sphere is moved to the nearest
- * point of its surface and stops. */
+ * point of its surface.  With sphere_mu < 0 it stops.  Otherwise, with n
+ * the outward normal, v_n = v . n and v_t = v - v_n n: the approaching part
+ * j = max(-v_n, 0) is absorbed and friction takes min(|v_t|, mu j) off the
+ * tangential speed. */
 static void sphere_project(const oracle_cloth* c, double* x, double* v)
 {
     if (!c->sphere_on) return;
@@ -239,31 +250,57 @@ static void sphere_project(const oracle_cloth* c, double* x, double* v)
         for (int a = 0; a < 3; ++a) d[a] = x[3 * i + a] - c->sphere_c[a];
         const double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (len < c->sphere_r && len > 0.0) {
+            double nrm[3], vn = 0.0;
             for (int a = 0; a < 3; ++a) {
-                x[3 * i + a] = c->sphere_c[a] + c->sphere_r * d[a] / len;
-                v[3 * i + a] = 0.0;
+                nrm[a] = d[a] / len;
+                x[3 * i + a] = c->sphere_c[a] + c->sphere_r * nrm[a];
+                vn += v[3 * i + a] * nrm[a];
             }
+            if (c->sphere_mu < 0.0) {
+                for (int a = 0; a < 3; ++a) v[3 * i + a] = 0.0;
+                continue;
+            }
+            double vt[3], tl2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                vt[a] = v[3 * i + a] - vn * nrm[a];
+                tl2 += vt[a] * vt[a];
+            }
+            const double tl = sqrt(tl2);
+            const double j = vn < 0.0 ? -vn : 0.0;
+            const double keep = tl > c->sphere_mu * j ? 1.0 - c->sphere_mu * j / tl : 0.0;
+            const double vn_out = vn > 0.0 ? vn : 0.0;
+            for (int a = 0; a < 3; ++a) v[3 * i + a] = vn_out * nrm[a] + keep * vt[a];
         }
     }
 }
 
-/* Advance `steps` semi-implicit Euler steps in place (Eq. 5):
- *   v <- C(v + dt f / m);  x <- x + dt v;  then sphere contact.
- * pinned[i] != 0 marks a Dirichlet node (its velocity is held at zero). */
+/* The update of Eq. 5 for a given acceleration acc (m/s^2, per node):
+ *   v <- C(v + dt acc);  x <- x + dt v;  then sphere contact,
+ * where C sets pinned velocities (pinned[i] != 0) to pin_v. */
+void oracle_update(const oracle_cloth* c, const uint8_t* pinned, const double* acc, double* x, double* v)
+{
+    const int n = c->rows * c->cols;
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            double vn = v[3 * i + a] + c->dt * acc[3 * i + a];
+            if (pinned && pinned[i]) vn = c->pin_v[a];
+            v[3 * i + a] = vn;
+            x[3 * i + a] += c->dt * vn;
+        }
+    sphere_project(c, x, v);
+}
+
+/* Advance `steps` semi-implicit Euler steps in place (Eq. 5) with the
+ * plain step's acceleration f / m (oracle_update).  pinned[i] != 0 marks a
+ * node that moves with pin_v (held in place when pin_v = 0). */
 void oracle_step(const oracle_cloth* c, const uint8_t* pinned, double* x, double* v, int32_t steps)
 {
     const int n = c->rows * c->cols;
     double* f = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     for (int t = 0; t < steps; ++t) {
         oracle_total_force(c, x, v, f);
-        for (int i = 0; i < n; ++i)
-            for (int a = 0; a < 3; ++a) {
-                double vn = v[3 * i + a] + c->dt * f[3 * i + a] / c->m;
-                if (pinned && pinned[i]) vn = 0.0;
-                v[3 * i + a] = vn;
-                x[3 * i + a] += c->dt * vn;
-            }
-        sphere_project(c, x, v);
+        for (int k = 0; k < 3 * n; ++k) f[k] /= c->m;
+        oracle_update(c, pinned, f, x, v);
     }
     free(f);
 }
