@@ -78,21 +78,30 @@ typedef struct {
     float gravity[3];
 } cloth_params;
 
-/* Dirichlet nodes of one cloth (Sec. 3.1; the constraint operator C of
- * Eq. 5 holds their velocity at zero).  `node` is a HOST array of `count`
- * node indices r * cols + c, read during cloth_create only. */
+/* Pinned nodes of one cloth (Sec. 3.1; the constraint operator C of Eq. 5
+ * sets their velocity).  They move with `velocity` (m/s), the velocity of
+ * the object they are attached to: zero holds them in place (the Dirichlet
+ * case), anything else carries them along (a cloth part that moves with
+ * another object).  `node` is a HOST array of `count` node indices
+ * r * cols + c, read during cloth_create only. */
 typedef struct {
     int32_t count;
     const int32_t* node;
+    float velocity[3];
 } cloth_pins;
 
 /* Sphere obstacle (cloth-object intersection elimination, Sec. 3.1): after
  * each step a node inside the sphere is moved to the nearest point of its
- * surface and its velocity is set to zero. */
+ * surface.  friction < 0: the node stops (the ball of Sec. 3.2.2 that
+ * absorbs the bounce and whose friction prevents relative motion).
+ * friction >= 0: a Coulomb coefficient mu; with n the outward normal, the
+ * approaching normal speed j = max(-v.n, 0) is absorbed, a separating
+ * normal speed is kept, and the tangential speed loses min(|v_t|, mu j). */
 typedef struct {
     float center[3];
     float radius;
     int32_t enabled;
+    float friction;
 } cloth_sphere;
 
 typedef struct cloth_ctx cloth_ctx;
@@ -152,6 +161,15 @@ typedef struct {
 
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
+
+/* Boundary treatment of cloth b, selectable between steps (Sec. 3.2: BC
+ * types are hard-encoded and selected at run time): the velocity its pinned
+ * nodes move with (host array of 3 floats, as cloth_pins.velocity) and its
+ * sphere's friction (as cloth_sphere.friction; ignored without a sphere).
+ * Every step kernel reads them from the context's descriptors, so cached
+ * graphs stay valid.  CLOTH_EINVAL for a bad b, a NULL pin_velocity or a
+ * non-finite value.  Synchronises `stream`. */
+int cloth_set_boundary(cloth_ctx* ctx, int32_t b, const float* pin_velocity, float sphere_friction, void* stream);
 
 /* Launch shape of the plain step.  Every warp of the launch runs a
  * contiguous range of a work list of (cloth, 120-column strip, row segment)

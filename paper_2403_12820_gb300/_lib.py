@@ -33,11 +33,11 @@ class ClothParams(ctypes.Structure):
 
 
 class ClothPins(ctypes.Structure):
-    _fields_ = [("count", c_int32), ("node", P(c_int32))]
+    _fields_ = [("count", c_int32), ("node", P(c_int32)), ("velocity", c_float * 3)]
 
 
 class ClothSphere(ctypes.Structure):
-    _fields_ = [("center", c_float * 3), ("radius", c_float), ("enabled", c_int32)]
+    _fields_ = [("center", c_float * 3), ("radius", c_float), ("enabled", c_int32), ("friction", c_float)]
 
 
 class RolloutOpts(ctypes.Structure):
@@ -61,6 +61,7 @@ SIGNATURES = {
     "cloth_topology": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "cloth_set_launch": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
     "cloth_get_launch": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int32)]),
+    "cloth_set_boundary": (c_int32, [c_void_p, c_int32, P(c_float), c_float, c_void_p]),
     "cloth_tune_launch": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32), c_int32, c_int32, P(c_float),
                                     P(c_int32), c_void_p]),
     "cloth_status": (c_int32, [c_void_p, P(c_int32), c_int32, c_void_p]),

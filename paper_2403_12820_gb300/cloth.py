@@ -3,8 +3,9 @@
 Torch supplies device memory and the stream; every step runs in libcloth's
 CUDA kernels.  A cloth is described by a dict with keys rows, cols, h, m,
 k_struct, k_shear, k_bend, mu, drag, p, g (3 floats), and optionally
-sphere = {center: (3 floats), radius}; the time step dt is shared by the
-batch.  States are float32 CUDA tensors of shape (total_nodes, 3), cloths
+sphere = {center: (3 floats), radius, friction (< 0 or absent: the node
+stops; >= 0: Coulomb mu)} and pin_v (3 floats, the velocity the pinned nodes
+move with; default 0); the time step dt is shared by the batch.  States are float32 CUDA tensors of shape (total_nodes, 3), cloths
 packed back to back, node (r, c) of a cloth at row r * cols + c.
 """
 from __future__ import annotations
@@ -60,11 +61,13 @@ class ClothBatch:
             sph = s.get("sphere")
             if sph is not None:
                 spheres[b] = ClothSphere((ctypes.c_float * 3)(*[float(a) for a in sph["center"]]),
-                                         float(sph["radius"]), 1)
+                                         float(sph["radius"]), 1, float(sph.get("friction", -1.0)))
             pl = list(pins[b]) if pins is not None else []
             arr = (ctypes.c_int32 * max(1, len(pl)))(*pl)
             pin_arrs.append(arr)
-            pin_structs[b] = ClothPins(len(pl), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)))
+            pv = s.get("pin_v", (0.0, 0.0, 0.0))
+            pin_structs[b] = ClothPins(len(pl), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)),
+                                       (ctypes.c_float * 3)(*[float(a) for a in pv]))
         nbytes = ctypes.c_size_t()
         _lib.check("cloth_workspace_size", self.lib.cloth_workspace_size(B, grids, ctypes.byref(nbytes)))
         with torch.cuda.device(self.device):
@@ -134,6 +137,12 @@ class ClothBatch:
         _lib.call("cloth_tune_launch", self.handle, n, seg, wps, int(warmup), int(steps), us, ctypes.byref(best),
                   self._s())
         return best.value, [float(v) for v in us]
+
+    def set_boundary(self, b: int, pin_v=(0.0, 0.0, 0.0), friction: float = -1.0) -> None:
+        """Cloth b's pins move with pin_v (m/s) from the next step on, and its
+        sphere contact takes `friction` (< 0: stick; >= 0: Coulomb mu)."""
+        _lib.call("cloth_set_boundary", self.handle, int(b), (ctypes.c_float * 3)(*[float(a) for a in pin_v]),
+                  ctypes.c_float(friction), self._s())
 
     def get_launch(self) -> tuple[int, int, int]:
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

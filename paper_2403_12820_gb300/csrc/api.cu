@@ -784,7 +784,10 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
         d.gy = p.gravity[1];
         d.gz = p.gravity[2];
         if (p.mu_spring != 0.f) c->damp = true;
+        d.sph_mu = -1.f;
         if (spheres && spheres[b].enabled) {
+            if (!std::isfinite(spheres[b].friction)) { delete c; return CLOTH_EINVAL; }
+            d.sph_mu = spheres[b].friction;
             d.sph_on = 1;
             d.sph_cx = spheres[b].center[0];
             d.sph_cy = spheres[b].center[1];
@@ -793,6 +796,13 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
             d.sph_r2 = spheres[b].radius * spheres[b].radius;
         }
         int64_t pinned = 0;
+        if (pins) {
+            for (int a = 0; a < 3; ++a)
+                if (!std::isfinite(pins[b].velocity[a])) { delete c; return CLOTH_EINVAL; }
+            d.pin_vx = pins[b].velocity[0];
+            d.pin_vy = pins[b].velocity[1];
+            d.pin_vz = pins[b].velocity[2];
+        }
         if (pins && pins[b].count > 0) {
             if (!pins[b].node) { delete c; return CLOTH_EINVAL; }
             for (int i = 0; i < pins[b].count; ++i) {
@@ -981,6 +991,22 @@ int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const in
     *best = b;
     rc = apply(b);
     if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    return CLOTH_OK;
+}
+
+int cloth_set_boundary(cloth_ctx* c, int32_t b, const float* pin_velocity, float sphere_friction, void* stream)
+{
+    if (!c || b < 0 || b >= c->B || !pin_velocity || !std::isfinite(sphere_friction)) return CLOTH_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(pin_velocity[a])) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ClothDesc& d = c->desc[b];
+    d.pin_vx = pin_velocity[0];
+    d.pin_vy = pin_velocity[1];
+    d.pin_vz = pin_velocity[2];
+    d.sph_mu = sphere_friction;
+    CK(cudaMemcpyAsync(c->d_desc() + b, &d, sizeof(ClothDesc), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return CLOTH_OK;
 }

@@ -33,8 +33,53 @@ struct __align__(16) ClothDesc {
     float drag, p_quarter, gx, gy;
     float gz, sph_cx, sph_cy, sph_cz;
     float sph_r, sph_r2;
-    int32_t sph_on, pad0;
+    int32_t sph_on;
+    float sph_mu;                         // contact friction: < 0 stick, else Coulomb mu
+    float pin_vx, pin_vy, pin_vz;         // velocity of the pinned nodes (m/s)
+    float pad0;
 };
+
+// Component c of the pinned nodes' velocity.
+__host__ __device__ __forceinline__ float pin_v(const ClothDesc& D, int c)
+{
+    return c == 0 ? D.pin_vx : (c == 1 ? D.pin_vy : D.pin_vz);
+}
+
+// Sphere contact after the update (intersection elimination, Sec. 3.1): a
+// node found inside the sphere moves to the nearest point of its surface.
+// Its velocity stops (sph_mu < 0), or, with n the outward normal, loses the
+// approaching normal speed j = max(-v.n, 0), keeps a separating one, and
+// loses min(|v_t|, sph_mu j) of its tangential speed (Coulomb friction).
+// (col, row): the node's lattice position (rest position (col h, row h, 0));
+// u = x - X.
+__device__ __forceinline__ void sphere_contact(const ClothDesc& D, int col, int row, float h, float& ux, float& uy,
+                                               float& uz, float& vx, float& vy, float& vz)
+{
+    const float rx = fmaf((float)col, h, -D.sph_cx) + ux;
+    const float ry = fmaf((float)row, h, -D.sph_cy) + uy;
+    const float rz = uz - D.sph_cz;
+    const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    if (!(dd < D.sph_r2 && dd > 0.f)) return;
+    const float inv = rsqrtf(dd);
+    const float sc = D.sph_r * inv;
+    ux = fmaf(sc, rx, ux - rx);
+    uy = fmaf(sc, ry, uy - ry);
+    uz = fmaf(sc, rz, uz - rz);
+    if (D.sph_mu < 0.f) {
+        vx = vy = vz = 0.f;
+        return;
+    }
+    const float nx = rx * inv, ny = ry * inv, nz = rz * inv;
+    const float vn = fmaf(vx, nx, fmaf(vy, ny, vz * nz));
+    const float tx = fmaf(-vn, nx, vx), ty = fmaf(-vn, ny, vy), tz = fmaf(-vn, nz, vz);
+    const float tl = sqrtf(fmaf(tx, tx, fmaf(ty, ty, tz * tz)));
+    const float j = fmaxf(-vn, 0.f);
+    const float keep = tl > D.sph_mu * j ? 1.f - D.sph_mu * j / tl : 0.f;
+    const float vo = fmaxf(vn, 0.f);
+    vx = fmaf(vo, nx, keep * tx);
+    vy = fmaf(vo, ny, keep * ty);
+    vz = fmaf(vo, nz, keep * tz);
+}
 
 // One warp's work: cloth `b`, strip starting at output column c0, output
 // rows [r0, r1).

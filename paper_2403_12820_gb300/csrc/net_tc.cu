@@ -451,22 +451,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 float vn[3], un[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    vn[c] = pinned ? 0.f : fmaf(D.dt, acc[c], v[c]);
+                    vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt, acc[c], v[c]);
                     un[c] = fmaf(D.dt, vn[c], u[c]);
                 }
-                if (D.sph_on) {
-                    const float rx = fmaf((float)x, D.h, -D.sph_cx) + un[0];
-                    const float ry = fmaf((float)y, D.h, -D.sph_cy) + un[1];
-                    const float rz = un[2] - D.sph_cz;
-                    const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    if (dd < D.sph_r2 && dd > 0.f) {
-                        const float sc = D.sph_r * rsqrtf(dd);
-                        un[0] = fmaf(sc, rx, un[0] - rx);
-                        un[1] = fmaf(sc, ry, un[1] - ry);
-                        un[2] = fmaf(sc, rz, un[2] - rz);
-                        vn[0] = vn[1] = vn[2] = 0.f;
-                    }
-                }
+                if (D.sph_on) sphere_contact(D, x, y, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
                 if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);
                 float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
 #pragma unroll

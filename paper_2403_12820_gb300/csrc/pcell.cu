@@ -170,22 +170,10 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
             float un[3], vn[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                vn[k] = pinned ? 0.f : fmaf(D.dt, a3[k], sU[3 + k][yy][sx]);
+                vn[k] = pinned ? pin_v(D, k) : fmaf(D.dt, a3[k], sU[3 + k][yy][sx]);
                 un[k] = fmaf(D.dt, vn[k], sU[k][yy][sx]);
             }
-            if (D.sph_on) {
-                const float rx = fmaf((float)x, h, -D.sph_cx) + un[0];
-                const float ry = fmaf((float)y, h, -D.sph_cy) + un[1];
-                const float rz = un[2] - D.sph_cz;
-                const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                if (dd < D.sph_r2 && dd > 0.f) {
-                    const float sc = D.sph_r * rsqrtf(dd);
-                    un[0] = fmaf(sc, rx, un[0] - rx);
-                    un[1] = fmaf(sc, ry, un[1] - ry);
-                    un[2] = fmaf(sc, rz, un[2] - rz);
-                    vn[0] = vn[1] = vn[2] = 0.f;
-                }
-            }
+            if (D.sph_on) sphere_contact(D, x, y, h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
             if (!isfinite(un[0] + un[1] + un[2])) atomicOr(A.status, kStatusNonfinite);
             float* out = A.dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
 #pragma unroll

@@ -127,6 +127,7 @@ __device__ __forceinline__ float shdn(float v) { return __shfl_down_sync(kFull, 
 // in global memory after every row's stores.
 struct UnitConst {
     float dt, dtm, keep, dtg[3];   // dt, dt/m, 1 - dt d/m, dt g
+    float pin_v[3];                // velocity of the pinned nodes
     int32_t pin_wpr, sph_on;
     const uint32_t* pins;          // the cloth's pin bitmask
 };
@@ -183,6 +184,9 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             uc->dtg[0] = D.dt * D.gx;
             uc->dtg[1] = D.dt * D.gy;
             uc->dtg[2] = D.dt * D.gz;
+            uc->pin_v[0] = D.pin_vx;
+            uc->pin_v[1] = D.pin_vy;
+            uc->pin_v[2] = D.pin_vz;
             uc->pin_wpr = D.pin_wpr;
             uc->sph_on = D.sph_on;
             uc->pins = a.pinmask + D.pin_off;
@@ -434,13 +438,14 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                     }
                     const uint32_t pw = __ldg(uc->pins + (int64_t)r * uc->pin_wpr + (c4 >> 5));
                     const unsigned pb = (pw >> (c4 & 31)) & 0xfu;
-                    if (pb) {   // Dirichlet nodes: C holds their velocity at zero
+                    if (pb) {   // pinned nodes: C sets the velocity of the object they move with
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            if (pb & 1u) vn.A[c].x = 0.f;
-                            if (pb & 4u) vn.A[c].y = 0.f;
-                            if (pb & 2u) vn.B[c].x = 0.f;
-                            if (pb & 8u) vn.B[c].y = 0.f;
+                            const float pv = uc->pin_v[c];
+                            if (pb & 1u) vn.A[c].x = pv;
+                            if (pb & 4u) vn.A[c].y = pv;
+                            if (pb & 2u) vn.B[c].x = pv;
+                            if (pb & 8u) vn.B[c].y = pv;
                         }
                     }
 #pragma unroll
@@ -457,18 +462,10 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                             float& ux = (k >> 1) ? U[0].y : U[0].x;
                             float& uy = (k >> 1) ? U[1].y : U[1].x;
                             float& uz = (k >> 1) ? U[2].y : U[2].x;
-                            const float rx = fmaf((float)(c4 + k), hs, -D.sph_cx) + ux;
-                            const float ry = fmaf((float)r, hs, -D.sph_cy) + uy;
-                            const float rz = uz - D.sph_cz;
-                            const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                            if (dd < D.sph_r2 && dd > 0.f) {
-                                const float sc = D.sph_r * rsqrtf(dd);
-                                ux = fmaf(sc, rx, ux - rx);
-                                uy = fmaf(sc, ry, uy - ry);
-                                uz = fmaf(sc, rz, uz - rz);
-                                if (k >> 1) { Vv[0].y = 0.f; Vv[1].y = 0.f; Vv[2].y = 0.f; }
-                                else { Vv[0].x = 0.f; Vv[1].x = 0.f; Vv[2].x = 0.f; }
-                            }
+                            float& vx = (k >> 1) ? Vv[0].y : Vv[0].x;
+                            float& vy = (k >> 1) ? Vv[1].y : Vv[1].x;
+                            float& vz = (k >> 1) ? Vv[2].y : Vv[2].x;
+                            sphere_contact(D, c4 + k, r, hs, ux, uy, uz, vx, vy, vz);
                         }
                     }
                     // non-finite check over the 4 nodes' positions (a NaN or

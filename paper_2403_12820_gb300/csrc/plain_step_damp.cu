@@ -281,22 +281,13 @@ __global__ void __launch_bounds__(128, 3) plain_step_damp_kernel(StepArgs a)
                     for (int k = 0; k < 4; ++k) {
                         const bool pinned = (pbits >> k) & 1u;
                         float nvx = fmaf(dtm, fx[k], vx[k]), nvy = fmaf(dtm, fy[k], vy[k]), nvz = fmaf(dtm, fz[k], vz[k]);
-                        if (pinned) nvx = nvy = nvz = 0.f;
-                        float nux = fmaf(dt, nvx, P1.c[0][k]), nuy = fmaf(dt, nvy, P1.c[1][k]), nuz = fmaf(dt, nvz, P1.c[2][k]);
-                        if (Dd.sph_on) {
-                            // position relative to the centre: (X - c) + u
-                            const float rx = fmaf((float)(c4 + k), h, -Dd.sph_cx) + nux;
-                            const float ry = fmaf((float)r, h, -Dd.sph_cy) + nuy;
-                            const float rz = nuz - Dd.sph_cz;
-                            const float dd = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                            if (dd < Dd.sph_r2 && dd > 0.f) {
-                                const float s = Dd.sph_r * rsqrtf(dd);
-                                nux = fmaf(s, rx, nux - rx);
-                                nuy = fmaf(s, ry, nuy - ry);
-                                nuz = fmaf(s, rz, nuz - rz);
-                                nvx = nvy = nvz = 0.f;
-                            }
+                        if (pinned) {   // C: the velocity of the object the node moves with
+                            nvx = Dd.pin_vx;
+                            nvy = Dd.pin_vy;
+                            nvz = Dd.pin_vz;
                         }
+                        float nux = fmaf(dt, nvx, P1.c[0][k]), nuy = fmaf(dt, nvy, P1.c[1][k]), nuz = fmaf(dt, nvz, P1.c[2][k]);
+                        if (Dd.sph_on) sphere_contact(Dd, c4 + k, r, h, nux, nuy, nuz, nvx, nvy, nvz);
                         un[0][k] = nux; un[1][k] = nuy; un[2][k] = nuz;
                         vn[0][k] = nvx; vn[1][k] = nvy; vn[2][k] = nvz;
                         if ((cm >> (k + 1)) & 1u)

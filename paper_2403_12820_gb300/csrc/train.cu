@@ -109,7 +109,7 @@ __global__ void train_euler_kernel(const ClothDesc* __restrict__ desc, const uin
     const bool fr = is_free(D, pinmask, r, c);
     for (int k = 0; k < 3; ++k) {
         const float acc = a[((int64_t)n * 3 + k) * HW + i] + D.p_quarter * fp[k] * D.inv_m;
-        const float vn = fr ? fmaf(D.dt, acc, zi[(3 + k) * HW + i]) : 0.f;
+        const float vn = fr ? fmaf(D.dt, acc, zi[(3 + k) * HW + i]) : pin_v(D, k);   // pins move with pin_v
         zn[((int64_t)n * 6 + 3 + k) * HW + i] = vn;
         zn[((int64_t)n * 6 + k) * HW + i] = fmaf(D.dt, vn, zi[k * HW + i]);
     }

@@ -36,8 +36,10 @@ def f32(v) -> float:
 
 
 def cloth_spec(rows: int, cols: int, h=H_DEFAULT, m=M_DEFAULT, k=K_DEFAULT, mu=0.0, drag=DRAG_DEFAULT,
-               p=0.0, g=G_DEFAULT, dt=DT_DEFAULT, sphere=None) -> dict:
-    """One cloth's parameters, every float rounded to float32."""
+               p=0.0, g=G_DEFAULT, dt=DT_DEFAULT, sphere=None, pin_v=None) -> dict:
+    """One cloth's parameters, every float rounded to float32.  sphere:
+    {center, radius[, friction]}; pin_v: the velocity the pinned nodes move
+    with (absent: they stay in place)."""
     spec = {
         "rows": int(rows), "cols": int(cols), "h": f32(h), "m": f32(m),
         "k_struct": f32(k[0]), "k_shear": f32(k[1]), "k_bend": f32(k[2]),
@@ -45,6 +47,10 @@ def cloth_spec(rows: int, cols: int, h=H_DEFAULT, m=M_DEFAULT, k=K_DEFAULT, mu=0
     }
     if sphere is not None:
         spec["sphere"] = {"center": [f32(a) for a in sphere["center"]], "radius": f32(sphere["radius"])}
+        if "friction" in sphere:
+            spec["sphere"]["friction"] = f32(sphere["friction"])
+    if pin_v is not None:
+        spec["pin_v"] = [f32(a) for a in pin_v]
     return spec
 
 
