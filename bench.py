@@ -471,12 +471,19 @@ def run_mixed(args, dev):
     status = cb.status()
     unchecked = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100))
     plain = timed(lambda k: cb.rollout(k, graph_chunk=100))
+    # the same rollouts with Coulomb contact (mu 0.3) in place of the
+    # stopping contact, selected at run time (same graphs; this batch has no pins)
+    for b in range(cb.B):
+        cb.set_boundary(b, (0.0, 0.0, 0.0), 0.3)
+    friction_net = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100))
+    friction_plain = timed(lambda k: cb.rollout(k, graph_chunk=100))
     out = {"workload": f"mixed_batch: 16 cloths, sides U{{256..1024}} (seed 1005), {nodes / 1e6:.2f}M nodes, "
                        "sphere R = 0.3 w, BF16 network (Kaiming weights, seed 2003), FP32 state",
            "value": checked, "unit": "node-steps/s", "steps": steps, "check_every": 10, "residual_bound_m": 1e-3,
            "graph_chunk": 100, "switched_to_plain": int(mode.sum().item()),
            "largest_residual_m": float(resid.max().item()), "network_unchecked": unchecked,
            "plain_same_cloths": plain, "ratio_to_plain": checked / plain, "status_word": status,
+           "coulomb_contact": {"network_unchecked": friction_net, "plain": friction_plain, "friction": 0.3},
            "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
     net.close()
     cb.close()
