@@ -162,6 +162,19 @@ typedef struct {
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
 
+/* Larger-step network (Sec. 5: larger-step time integration with the
+ * cell): from now on one network step (cloth_step_net, cloth_step_pcell,
+ * cloth_rollout_net) advances k plain-step time steps, dt_net = k dt, in
+ * the Euler update of Fig. 2; the plain step keeps dt.  The training loss
+ * (cloth_train_loss*) unrolls with dt_net: its targets are then the
+ * positions k, 2k, ... S k plain steps after the window start, and its
+ * physics target is the mean acceleration of the k plain steps from the
+ * window start, (v_k - v_0) / dt_net, less the start's pressure term.
+ * k = 1 restores the plain time step.  cloth_rollout_net with a residual
+ * check needs k = 1 (CLOTH_EUNSUPPORTED otherwise).  CLOTH_EINVAL for k
+ * outside 1..1000.  Synchronises `stream`. */
+int cloth_set_net_stride(cloth_ctx* ctx, int32_t k, void* stream);
+
 /* Boundary treatment of cloth b, selectable between steps (Sec. 3.2: BC
  * types are hard-encoded and selected at run time): the velocity its pinned
  * nodes move with (host array of 3 floats, as cloth_pins.velocity) and its

@@ -227,6 +227,14 @@ def update(c: dict, x, v, acc, pins=()):
     return x, v
 
 
+def mean_accel(c: dict, x0, v0, pins=(), k: int = 1) -> np.ndarray:
+    """Physics target of a network step spanning k plain steps: the mean
+    acceleration (v_k - v_0) / (k dt) of k oracle steps from (x0, v0), less
+    the pressure acceleration at x0 (which the network step adds itself)."""
+    _, vk = step(c, x0, v0, pins=pins, steps=k)
+    return (vk - np.asarray(v0, dtype=np.float64)) / (k * float(c["dt"])) - pressure_force(c, x0) / float(c["m"])
+
+
 def energy(c: dict, x, v) -> float:
     rows, cols = int(c["rows"]), int(c["cols"])
     x = _state(x, rows, cols)

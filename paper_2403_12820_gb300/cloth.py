@@ -138,6 +138,11 @@ class ClothBatch:
                   self._s())
         return best.value, [float(v) for v in us]
 
+    def set_net_stride(self, k: int) -> None:
+        """One network step advances k plain time steps (dt_net = k dt)."""
+        _lib.call("cloth_set_net_stride", self.handle, int(k), self._s())
+        self.net_stride = int(k)
+
     def set_boundary(self, b: int, pin_v=(0.0, 0.0, 0.0), friction: float = -1.0) -> None:
         """Cloth b's pins move with pin_v (m/s) from the next step on, and its
         sphere contact takes `friction` (< 0: stick; >= 0: Coulomb mu)."""

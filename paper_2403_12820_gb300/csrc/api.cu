@@ -20,6 +20,7 @@ thread_local int g_last_cuda = 0;
 
 constexpr int kMinSegRows = 4;       // smallest row segment the work list may use
 constexpr int kMaxWarps = 1 << 16;   // bound on the warps of one plain-step launch
+constexpr int kMaxNetStride = 1000;  // bound on the plain steps one network step may span
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -111,6 +112,7 @@ struct cloth_ctx {
     int n_warps = 0;                   // warps of one plain-step launch that have work
     int grid = 0, block = 128;
     int warps_per_sm = 0;              // 0: the plain-step kernel's occupancy
+    int net_stride = 1;                // plain steps one network step spans
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
@@ -318,7 +320,7 @@ int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wor
 
 // Workspace of cloth_train_loss (float offsets).
 struct TrainWs {
-    size_t z, a, at, ga0, gu, gv, ga, gfp, ge, gn, gz, saved, fabi, coef, part, ppart, total;
+    size_t z, a, at, ga0, gu, gv, ga, gfp, ge, gn, gz, saved, fabi, coef, part, ppart, kstate, total;
 };
 TrainWs train_ws(const cloth_ctx* c, int S)
 {
@@ -335,6 +337,7 @@ TrainWs train_ws(const cloth_ctx* c, int S)
     w.coef = take((size_t)2 * B);
     w.part = take((size_t)(S + 1) * train_blocks(c->grids[0].rows, c->grids[0].cols, c->B));
     w.ppart = take((size_t)40 * pcell_train_blocks(c->grids[0].rows, c->grids[0].cols, c->B));
+    w.kstate = take((size_t)c->L.state_floats);   // plain steps of a stride > 1 (physics target)
     w.total = off * sizeof(float);
     return w;
 }
@@ -395,11 +398,25 @@ int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha
     }
     CK(cudaMemcpyAsync(COEF, coef.data(), sizeof(float) * 2 * B, cudaMemcpyHostToDevice, s));
 
-    // targets of the physics term: the plain step's acceleration without pressure
-    int rc = launch_step(c, true, FABI, s);
-    if (rc) return rc;
+    // targets of the physics term: the plain step's acceleration without
+    // pressure; for a network stride k > 1 the mean acceleration of k plain
+    // steps from the window start (ping-pong between the spare state buffer
+    // and the workspace; the current state is not touched)
     CK(launch_state_to_z(D, c->d_state(c->cur), Zt(0), B, H, W, s));
-    CK(launch_a_true(D, FABI, Zt(0), AT, B, H, W, s));
+    if (c->net_stride == 1) {
+        const int rc = launch_step(c, true, FABI, s);
+        if (rc) return rc;
+        CK(launch_a_true(D, FABI, Zt(0), AT, B, H, W, s));
+    } else {
+        float* bufs[2] = {c->d_state(c->cur ^ 1), ws + L.kstate};
+        const float* from = c->d_state(c->cur);
+        for (int i = 0; i < c->net_stride; ++i) {
+            const int rc = launch_plain(c, from, bufs[i & 1], nullptr, s);
+            if (rc) return rc;
+            from = bufs[i & 1];
+        }
+        CK(launch_a_true_stride(D, from, Zt(0), AT, B, H, W, s));
+    }
 
     // forward unroll: a_t, z_{t+1}, loss terms
     for (int t = 0; t < S; ++t) {
@@ -573,6 +590,7 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
 {
     if (!c || !net || !o || !d_work || o->steps < 0 || o->check_every < 0 || o->graph_chunk < 0) return CLOTH_EINVAL;
     if (o->check_every > 0 && !(o->residual_bound >= 0.f)) return CLOTH_EINVAL;
+    if (o->check_every > 0 && c->net_stride != 1) return CLOTH_EUNSUPPORTED;   // the check compares one plain step
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (net->precision != CLOTH_NET_BF16) {
         if (o->check_every > 0) return CLOTH_EUNSUPPORTED;
@@ -774,6 +792,7 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
         d.m = g.mass;
         d.inv_m = 1.f / g.mass;
         d.dt = dt;
+        d.dt_net = dt;
         d.k_struct = p.k_struct;
         d.k_shear = p.k_shear;
         d.k_bend = p.k_bend;
@@ -1007,6 +1026,17 @@ int cloth_set_boundary(cloth_ctx* c, int32_t b, const float* pin_velocity, float
     d.pin_vz = pin_velocity[2];
     d.sph_mu = sphere_friction;
     CK(cudaMemcpyAsync(c->d_desc() + b, &d, sizeof(ClothDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return CLOTH_OK;
+}
+
+int cloth_set_net_stride(cloth_ctx* c, int32_t k, void* stream)
+{
+    if (!c || k < 1 || k > kMaxNetStride) return CLOTH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (auto& d : c->desc) d.dt_net = (float)k * d.dt;
+    c->net_stride = k;
+    CK(cudaMemcpyAsync(c->d_desc(), c->desc.data(), sizeof(ClothDesc) * c->B, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     return CLOTH_OK;
 }

@@ -36,7 +36,7 @@ struct __align__(16) ClothDesc {
     int32_t sph_on;
     float sph_mu;                         // contact friction: < 0 stick, else Coulomb mu
     float pin_vx, pin_vy, pin_vz;         // velocity of the pinned nodes (m/s)
-    float pad0;
+    float dt_net;                         // time step of the network step: stride x dt
 };
 
 // Component c of the pinned nodes' velocity.

@@ -468,8 +468,8 @@ __global__ void net_update_kernel(const ClothDesc* __restrict__ desc, const int3
     const bool pinned = (pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
     float vn[3], un[3];
     for (int c = 0; c < 3; ++c) {
-        vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt, acc[c], v[c]);
-        un[c] = fmaf(D.dt, vn[c], u[c]);
+        vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt_net, acc[c], v[c]);
+        un[c] = fmaf(D.dt_net, vn[c], u[c]);
     }
     if (D.sph_on) sphere_contact(D, x, y, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
     if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(status, 1);

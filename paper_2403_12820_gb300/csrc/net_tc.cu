@@ -451,8 +451,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 float vn[3], un[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt, acc[c], v[c]);
-                    un[c] = fmaf(D.dt, vn[c], u[c]);
+                    vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt_net, acc[c], v[c]);
+                    un[c] = fmaf(D.dt_net, vn[c], u[c]);
                 }
                 if (D.sph_on) sphere_contact(D, x, y, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
                 if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(A.status, kStatusNonfinite);

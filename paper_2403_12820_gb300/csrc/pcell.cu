@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
             float un[3], vn[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                vn[k] = pinned ? pin_v(D, k) : fmaf(D.dt, a3[k], sU[3 + k][yy][sx]);
-                un[k] = fmaf(D.dt, vn[k], sU[k][yy][sx]);
+                vn[k] = pinned ? pin_v(D, k) : fmaf(D.dt_net, a3[k], sU[3 + k][yy][sx]);
+                un[k] = fmaf(D.dt_net, vn[k], sU[k][yy][sx]);
             }
             if (D.sph_on) sphere_contact(D, x, y, h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
             if (!isfinite(un[0] + un[1] + un[2])) atomicOr(A.status, kStatusNonfinite);

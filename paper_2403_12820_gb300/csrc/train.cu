@@ -90,6 +90,31 @@ __global__ void a_true_kernel(const ClothDesc* __restrict__ desc, const float* _
         a_true[((int64_t)n * 3 + k) * HW + i] = (f_abi[(D.abi_off + i) * 3 + k] - D.p_quarter * fp[k]) * D.inv_m;
 }
 
+// Physics target of a network step of stride k (dt_net = k dt): the mean
+// acceleration of the k plain steps from the window start, (v_k - v_0) /
+// dt_net, less the pressure acceleration at the start (the network step adds
+// that itself).  state_k: the packed state after the k plain steps.
+__global__ void a_true_stride_kernel(const ClothDesc* __restrict__ desc, const float* __restrict__ state_k,
+                                     const float* __restrict__ z, float* __restrict__ a_true, int H, int W)
+{
+    const int n = blockIdx.y;
+    const ClothDesc& D = desc[n];
+    const int64_t HW = (int64_t)H * W, i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= HW) return;
+    const int r = (int)(i / W), c = (int)(i % W);
+    const float* zi = z + (int64_t)n * 6 * HW;
+    float fp[3] = {0.f, 0.f, 0.f};
+    if (D.p_quarter != 0.f) {
+        const EN v = pressure_vectors(zi, HW, r, c, H, W, D.h);
+        cross(v.e, v.n, fp);
+    }
+    const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
+    for (int k = 0; k < 3; ++k) {
+        const float vk = state_k[o + (3 + k) * D.plane_stride];
+        a_true[((int64_t)n * 3 + k) * HW + i] = (vk - zi[(3 + k) * HW + i]) / D.dt_net - D.p_quarter * fp[k] * D.inv_m;
+    }
+}
+
 // Fig. 2 update without contact: v' = C(v + dt (a + f_p / m)), u' = u + dt v'.
 __global__ void train_euler_kernel(const ClothDesc* __restrict__ desc, const uint32_t* __restrict__ pinmask,
                                    const float* __restrict__ z, const float* __restrict__ a, float* __restrict__ zn,
@@ -109,9 +134,9 @@ __global__ void train_euler_kernel(const ClothDesc* __restrict__ desc, const uin
     const bool fr = is_free(D, pinmask, r, c);
     for (int k = 0; k < 3; ++k) {
         const float acc = a[((int64_t)n * 3 + k) * HW + i] + D.p_quarter * fp[k] * D.inv_m;
-        const float vn = fr ? fmaf(D.dt, acc, zi[(3 + k) * HW + i]) : pin_v(D, k);   // pins move with pin_v
+        const float vn = fr ? fmaf(D.dt_net, acc, zi[(3 + k) * HW + i]) : pin_v(D, k);   // pins move with pin_v
         zn[((int64_t)n * 6 + 3 + k) * HW + i] = vn;
-        zn[((int64_t)n * 6 + k) * HW + i] = fmaf(D.dt, vn, zi[k * HW + i]);
+        zn[((int64_t)n * 6 + k) * HW + i] = fmaf(D.dt_net, vn, zi[k * HW + i]);
     }
 }
 
@@ -196,10 +221,10 @@ __global__ void euler_adjoint_kernel(const ClothDesc* __restrict__ desc, const u
     const bool fr = is_free(D, pinmask, r, c);
     for (int k = 0; k < 3; ++k) {
         const int64_t j = ((int64_t)n * 3 + k) * HW + i;
-        const float w = fr ? fmaf(D.dt, gu[j], gv[j]) : 0.f;
+        const float w = fr ? fmaf(D.dt_net, gu[j], gv[j]) : 0.f;
         gv[j] = w;
-        ga[j] = D.dt * w + (ga0 ? ga0[j] : 0.f);
-        gfp[j] = D.dt * w * D.inv_m;
+        ga[j] = D.dt_net * w + (ga0 ? ga0[j] : 0.f);
+        gfp[j] = D.dt_net * w * D.inv_m;
     }
 }
 
@@ -284,6 +309,12 @@ int train_blocks(int H, int W, int B) { const dim3 g = grid2(H, W, B); return (i
 cudaError_t launch_state_to_z(const ClothDesc* d, const float* state, float* z, int B, int H, int W, cudaStream_t s)
 {
     state_to_z_kernel<<<grid2(H, W, B), TB, 0, s>>>(d, state, z, H, W);
+    return cudaGetLastError();
+}
+cudaError_t launch_a_true_stride(const ClothDesc* d, const float* state_k, const float* z, float* at, int B, int H,
+                                 int W, cudaStream_t s)
+{
+    a_true_stride_kernel<<<grid2(H, W, B), TB, 0, s>>>(d, state_k, z, at, H, W);
     return cudaGetLastError();
 }
 cudaError_t launch_a_true(const ClothDesc* d, const float* f_abi, const float* z, float* at, int B, int H, int W,

@@ -10,6 +10,8 @@ namespace cloth {
 
 int train_blocks(int H, int W, int B);
 cudaError_t launch_state_to_z(const ClothDesc* d, const float* state, float* z, int B, int H, int W, cudaStream_t s);
+cudaError_t launch_a_true_stride(const ClothDesc* d, const float* state_k, const float* z, float* at, int B, int H,
+                                 int W, cudaStream_t s);
 cudaError_t launch_a_true(const ClothDesc* d, const float* f_abi, const float* z, float* at, int B, int H, int W,
                           cudaStream_t s);
 cudaError_t launch_train_euler(const ClothDesc* d, const uint32_t* pins, const float* z, const float* a, float* zn,

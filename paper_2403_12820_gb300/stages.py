@@ -155,7 +155,7 @@ class WindowLoss:
     +inf."""
 
     def __init__(self, cell: str, w0, specs, pins, x0, v0, targets, alpha: float = 0.5, g_norm: float = 9.81,
-                 device="cuda"):
+                 device="cuda", stride: int = 1):
         import torch
 
         from .cloth import ClothBatch
@@ -167,6 +167,8 @@ class WindowLoss:
         self.targets = targets
         self.cb = ClothBatch(specs, pins, device=device)
         self.cb.set_state(x0, v0)
+        if stride != 1:
+            self.cb.set_net_stride(stride)
         self.net = Net(self.w0, FP32, device=device) if cell == "cnn" else None
         self.device = device
         self.calls = 0

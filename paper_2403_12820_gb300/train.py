@@ -46,13 +46,18 @@ class Trainer:
     FP32) or "pcell" (the literal cell: 39 trainable weights, alpha fixed).
     `lr_schedule` (a callable of the 0-based iteration, e.g. stages.StepLR or
     stages.CosineLR) replaces the constant lr; `trainable` (group names of
-    stages.mask_groups) freezes every other group (branch-wise fine-tuning)."""
+    stages.mask_groups) freezes every other group (branch-wise fine-tuning).
+    `stride` k > 1 trains a larger-step cell: each network step spans k plain
+    steps, so the window's targets are k plain steps apart."""
 
     def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
                  alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn", lr_schedule=None,
-                 trainable=None):
+                 trainable=None, stride: int = 1):
         if cell not in ("cnn", "pcell"):
             raise ValueError("cell must be 'cnn' or 'pcell'")
+        if stride < 1 or unroll * stride > data.steps:
+            raise ValueError("need 1 <= stride and unroll * stride <= the recorded steps")
+        self.stride = int(stride)
         self.data, self.batch, self.unroll, self.lr, self.alpha = data, batch, unroll, lr, alpha
         self.cell = cell
         self.rng = np.random.default_rng(seed)
@@ -88,7 +93,7 @@ class Trainer:
         and restart Adam's moments.  Returns the DE record."""
         specs, pins, x0, v0, tg = self.sample()
         obj = stages.WindowLoss(self.cell, self.w.detach().cpu().numpy(), specs, pins, x0, v0, tg,
-                                alpha=self.alpha, device=self.device)
+                                alpha=self.alpha, device=self.device, stride=self.stride)
         try:
             res = stages.de_preprocess(obj, draws, bounds=bounds, F=F, CR=CR)
         finally:
@@ -103,7 +108,7 @@ class Trainer:
         """Windows (trajectory, start) and a ClothBatch holding their cloths."""
         d = self.data
         traj = self.rng.choice(d.count, size=self.batch, replace=d.count < self.batch)
-        start = self.rng.integers(0, d.steps - self.unroll + 1, size=self.batch)
+        start = self.rng.integers(0, d.steps - self.unroll * self.stride + 1, size=self.batch)
         specs = [d.cfg["specs"][i] for i in traj]
         pins = [d.cfg["pins"][i] for i in traj]
         nn = d.nodes
@@ -111,13 +116,15 @@ class Trainer:
         st = torch.from_numpy(np.repeat(start, nn)).to(self.device)
         x0 = d.x[st, idx].contiguous()
         v0 = d.v[st, idx].contiguous()
-        tg = torch.stack([d.x[st + s, idx] for s in range(1, self.unroll + 1)]).contiguous()
+        tg = torch.stack([d.x[st + s * self.stride, idx] for s in range(1, self.unroll + 1)]).contiguous()
         return specs, pins, x0, v0, tg
 
     def step(self) -> float:
         specs, pins, x0, v0, tg = self.sample()
         cb = ClothBatch(specs, pins, device=self.device)
         cb.set_state(x0, v0)
+        if self.stride != 1:
+            cb.set_net_stride(self.stride)
         if self.cell == "cnn":
             self.net.set_weights(self.w)
             loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
