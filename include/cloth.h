@@ -170,8 +170,11 @@ int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* st
  * positions k, 2k, ... S k plain steps after the window start, and its
  * physics target is the mean acceleration of the k plain steps from the
  * window start, (v_k - v_0) / dt_net, less the start's pressure term.
- * k = 1 restores the plain time step.  cloth_rollout_net with a residual
- * check needs k = 1 (CLOTH_EUNSUPPORTED otherwise).  CLOTH_EINVAL for k
+ * k = 1 restores the plain time step.  In cloth_rollout_net a cloth on the
+ * plain step (fallback) advances k plain steps per network step, and the
+ * residual check compares the network step with k plain steps from the same
+ * state; its workspace (cloth_net_rollout_workspace_size, to be queried
+ * after this call) then holds a second scratch state.  CLOTH_EINVAL for k
  * outside 1..1000.  Synchronises `stream`. */
 int cloth_set_net_stride(cloth_ctx* ctx, int32_t k, void* stream);
 

@@ -581,7 +581,9 @@ int cloth_net_rollout_workspace_size(const cloth_ctx* c, int32_t precision, size
     size_t tiles = 0;
     int rc = cloth_net_workspace_size(c, precision, &tiles);
     if (rc) return rc;
-    *bytes = align_up(tiles, kAlign) + (c->L.state[1] - c->L.state[0]);   // + one scratch state buffer
+    // + one scratch state buffer, two when a network step spans several
+    // plain steps (the checked steps' plain reference ping-pongs)
+    *bytes = align_up(tiles, kAlign) + (c->net_stride > 1 ? 2 : 1) * (c->L.state[1] - c->L.state[0]);
     return CLOTH_OK;
 }
 
@@ -590,7 +592,6 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
 {
     if (!c || !net || !o || !d_work || o->steps < 0 || o->check_every < 0 || o->graph_chunk < 0) return CLOTH_EINVAL;
     if (o->check_every > 0 && !(o->residual_bound >= 0.f)) return CLOTH_EINVAL;
-    if (o->check_every > 0 && c->net_stride != 1) return CLOTH_EUNSUPPORTED;   // the check compares one plain step
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (net->precision != CLOTH_NET_BF16) {
         if (o->check_every > 0) return CLOTH_EUNSUPPORTED;
@@ -604,6 +605,21 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
     const std::vector<int4> tiles = tc_tiles(c);
     int4* d_tiles = static_cast<int4*>(d_work);
     float* scratch = reinterpret_cast<float*>(static_cast<char*>(d_work) + align_up(sizeof(int4) * tiles.size(), kAlign));
+    float* scratch2 = c->net_stride > 1 ? scratch + (c->L.state[1] - c->L.state[0]) / sizeof(float) : nullptr;
+    const int k = c->net_stride;
+    // k plain steps from src ending in dst, through `other` in between
+    // (with `mode`, only the cloths in plain mode): step i writes dst when
+    // k - i is even, `other` when it is odd
+    auto plain_k = [&](const float* src, float* dst, float* other, const int32_t* mode, cudaStream_t ss) -> int {
+        const float* from = src;
+        for (int i = 1; i <= k; ++i) {
+            float* to = (k - i) % 2 == 0 ? dst : other;
+            const int r = launch_plain(c, from, to, mode, ss);
+            if (r) return r;
+            from = to;
+        }
+        return CLOTH_OK;
+    };
     if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_BF16) {
         CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -616,19 +632,22 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
         const float* src = c->d_state(c->cur);
         float* dst = c->d_state(c->cur ^ 1);
         if (ce > 0 && st % ce == 0) {
-            // both steps from the same state: plain into dst, network into the
-            // scratch buffer, then keep, or latch to plain, per cloth
-            int r = launch_plain(c, src, dst, nullptr, ss);
-            if (r) return r;
+            // both from the same state: the network step into the scratch
+            // buffer, its k plain steps into dst, then keep, or latch to
+            // plain, per cloth
             CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, scratch,
                                   c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
+            int r = plain_k(src, dst, scratch2, nullptr, ss);
+            if (r) return r;
             CK(launch_fallback_check(c->d_desc(), c->B, c->max_nodes, c->d_mode(), c->d_resid(), c->d_last(),
                                      o->residual_bound, scratch, dst, ss));
         } else {
-            int r = launch_plain(c, src, dst, c->d_mode(), ss);
-            if (r) return r;
+            // cloths on the network: one network step; cloths on the plain
+            // step: k plain steps (each kernel skips the other mode's cloths)
             CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, dst,
                                   c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
+            int r = plain_k(src, dst, scratch, c->d_mode(), ss);
+            if (r) return r;
         }
         c->cur ^= 1;
         return CLOTH_OK;

@@ -122,9 +122,7 @@ def test_stride_limits_and_reset():
         with pytest.raises(_lib.ClothError):
             cb.set_net_stride(bad)
     cb.set_net_stride(4)
-    with pytest.raises(_lib.ClothError):
-        cb.rollout_net(net, 10, check_every=5, residual_bound=1e-3)
-    cb.rollout_net(net, 10)                   # unchecked rollouts run at any stride
+    cb.rollout_net(net, 10)
     cb.set_net_stride(1)
     cb.set_state(x0, v0)
     cb.step_net(net, 4)
@@ -142,3 +140,39 @@ def test_trainer_with_stride_runs():
     assert all(np.isfinite(losses))
     with pytest.raises(ValueError):
         Trainer(data, batch=2, unroll=5, cell="pcell", stride=4)
+
+
+@pytest.mark.parametrize("chunk", [0, 4])
+def test_checked_rollout_at_stride(chunk):
+    """Residual check at stride k: bound 0 switches every cloth at the first
+    check, after which each network step is k plain steps (the plain rollout
+    bit for bit); an infinite bound keeps the network (the unchecked rollout
+    bit for bit)."""
+    k = 3
+    specs, pins, xs, vs = batch(613, [(16, 33), (9, 20), (40, 41)])
+    w = blob(614)
+    net = Net(w, BF16)
+    x0, v0 = pack(xs).cuda(), pack(vs).cuda()
+
+    def run(fn, stride):
+        cb = ClothBatch(specs, pins)
+        cb.set_state(x0, v0)
+        if stride != 1:
+            cb.set_net_stride(stride)
+        fn(cb)
+        out = cb.get_state()
+        modes = cb.modes()[0].cpu().numpy()
+        assert cb.status() == 0
+        cb.close()
+        return out, modes
+
+    (xa, va), ma = run(lambda cb: cb.rollout_net(net, 8, check_every=2, residual_bound=0.0, graph_chunk=chunk), k)
+    (xb, vb), _ = run(lambda cb: cb.rollout(8 * k), 1)
+    assert ma.tolist() == [1, 1, 1]
+    assert torch.equal(xa, xb) and torch.equal(va, vb)
+    (xa, va), ma = run(lambda cb: cb.rollout_net(net, 8, check_every=2, residual_bound=float("inf"),
+                                                 graph_chunk=chunk), k)
+    (xb, vb), _ = run(lambda cb: cb.step_net(net, 8), k)
+    assert ma.tolist() == [0, 0, 0]
+    assert torch.equal(xa, xb) and torch.equal(va, vb)
+    net.close()
