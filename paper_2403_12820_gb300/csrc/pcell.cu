@@ -15,6 +15,8 @@
 // displacements u = x - X (l_c the lattice offset), which keeps the
 // difference exact to the rounding of u.  Step mode adds the hard-encoded
 // pressure (Eq. 3) and runs Eq. 5 with pins and sphere contact.
+#include <type_traits>
+
 #include "cloth_internal.cuh"
 
 // Resident blocks of 256 threads per SM the register budget is sized for.
@@ -121,22 +123,37 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
         vi[k] = U2(3 + k, 0, 0);
     }
     f2 acc[3] = {F2(sW[36]), F2(sW[37]), F2(sW[38])};
+    // the 12 channels; a tile whose 2-node margin lies inside the grid has
+    // every neighbour of both nodes (no existence masks)
+    auto channels = [&](auto interior_tag) {
+        constexpr bool kInterior = decltype(interior_tag)::value;
 #pragma unroll
-    for (int ch = 0; ch < 12; ++ch) {
-        const int dy = ch_dy(ch), dx = ch_dx(ch);
-        const bool cx = dx == 0 ? true : (dx == 1 ? c_p1 : (dx == -1 ? c_m1 : (dx == 2 ? c_p2 : c_m2)));
-        const f2 m = make_float2(cx && rowok(ya, dy) ? 1.f : 0.f, cx && hb && rowok(yb, dy) ? 1.f : 0.f);
-        const f2 wl = mul2(m, F2(sW[ch])), wn = mul2(m, F2(sW[12 + ch])), wd = mul2(m, F2(sW[24 + ch]));
+        for (int ch = 0; ch < 12; ++ch) {
+            const int dy = ch_dy(ch), dx = ch_dx(ch);
+            f2 wl = F2(sW[ch]), wn = F2(sW[12 + ch]), wd = F2(sW[24 + ch]);
+            if constexpr (!kInterior) {
+                const bool cx = dx == 0 ? true : (dx == 1 ? c_p1 : (dx == -1 ? c_m1 : (dx == 2 ? c_p2 : c_m2)));
+                const f2 m = make_float2(cx && rowok(ya, dy) ? 1.f : 0.f, cx && hb && rowok(yb, dy) ? 1.f : 0.f);
+                wl = mul2(m, wl);
+                wn = mul2(m, wn);
+                wd = mul2(m, wd);
+            }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
-            const f2 phi = add2(F2(lat), sub2(U2(k, dy, dx), ui[k]));
-            const f2 xi = sub2(U2(3 + k, dy, dx), vi[k]);
-            const f2 q = fma2(mul2(alpha, phi), phi, F2(1.f));
-            const f2 s = mul2(phi, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
-            acc[k] = fma2(wl, phi, fma2(s, fma2(wd, xi, wn), acc[k]));
+            for (int k = 0; k < 3; ++k) {
+                const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
+                const f2 phi = add2(F2(lat), sub2(U2(k, dy, dx), ui[k]));
+                const f2 xi = sub2(U2(3 + k, dy, dx), vi[k]);
+                // 1 + alpha phi^2 >= 1: never subnormal, the flushing form is exact here
+                const f2 q = fma2(mul2(alpha, phi), phi, F2(1.f));
+                const f2 s = mul2(phi, make_float2(rsqrt_ftz(q.x), rsqrt_ftz(q.y)));
+                acc[k] = fma2(wl, phi, fma2(s, fma2(wd, xi, wn), acc[k]));
+            }
         }
-    }
+    };
+    if (y0 >= HALO && y0 + TH + HALO <= H && x0 >= HALO && x0 + TW + HALO <= W)
+        channels(std::true_type{});
+    else
+        channels(std::false_type{});
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         if (half == 1 && !hb) break;

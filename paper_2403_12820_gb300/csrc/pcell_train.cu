@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(TB) pcell_fwd_z_kernel(const ClothDesc* __rest
             const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
             const float phi = lat + (zn[k * HW + j] - ui);
             const float xi = zn[(3 + k) * HW + j] - vi;
-            const float s = phi * rsqrtf(fmaf(alpha * phi, phi, 1.f));
+            const float s = phi * rsqrt_ftz(fmaf(alpha * phi, phi, 1.f));   // the argument is >= 1
             acc = fmaf(sw[ch], phi, fmaf(s, fmaf(sw[24 + ch], xi, sw[12 + ch]), acc));
         }
         a[((int64_t)n * 3 + k) * HW + i] = acc;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TB) pcell_bwd_z_kernel(const ClothDesc* __rest
                 const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
                 const float phi = lat + (zn[k * HW + j] - ui);
                 const float xi = zn[(3 + k) * HW + j] - vi;
-                const float rq = rsqrtf(fmaf(alpha * phi, phi, 1.f));
+                const float rq = rsqrt_ftz(fmaf(alpha * phi, phi, 1.f));   // the argument is >= 1
                 const float s = phi * rq, ds = rq * rq * rq;
                 gw[ch] = fmaf(gi, phi, gw[ch]);
                 gw[12 + ch] = fmaf(gi, s, gw[12 + ch]);
