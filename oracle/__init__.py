@@ -14,7 +14,8 @@ composes those primitives into the network step of Fig. 2 and the training
 loss of Eq. 8, step by step.  ``stages.py`` (numpy) holds the training
 stages around that loss (Sec. 3.2.1, Table 1): the differential-evolution
 pre-process, the learning-rate schedules and the masked Adam update of
-branch-wise fine-tuning.
+branch-wise fine-tuning; ``implicit.py`` (numpy, scipy.sparse) the
+linearised backward Euler step, solved directly.
 
 Array conventions: a cloth state is ``x, v`` of shape ``(rows, cols, 3)``
 float64; node (r, c) rests at ``X = (c h, r h, 0)``.
@@ -419,5 +420,6 @@ def adam_step(theta, grad, m, v, t: int, lr: float, beta1=0.9, beta2=0.999, eps=
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+from .implicit import implicit_step, springs, stiffness  # noqa: E402,F401
 from .stages import (CNN_GROUPS, PCELL_GROUPS, adam_step_masked, de_minimize, group_mask,  # noqa: E402,F401
                      lr_cosine, lr_step, scaled_blob)
