@@ -162,6 +162,23 @@ typedef struct {
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
 
+/* Implicit plain step (Sec. 3.1: implicit integration is the stable choice
+ * for large time steps; Sec. 5: the comparison for a larger-step cell):
+ * `steps` linearised backward Euler steps of h = stride dt.  Per step, with
+ * the elastic springs (Eq. 1) and the air drag (Eq. 4) implicit and the
+ * rest (Eq. 2 damping, Eq. 3 pressure, gravity) explicit:
+ *   (m + h d) dv - h^2 K dv = h f(x, v) + h^2 K v,  v' = C(v + dv),
+ *   x' = x + h v', then sphere contact,
+ * K the springs' stiffness matrix (per spring k [n n^T + max(0, 1 - L/l)
+ * (I - n n^T)], n the unit spring vector, l its length), solved per cloth
+ * by cg_iters conjugate-gradient iterations (matrix-free, pinned nodes
+ * dv = pin_v - v).  d_work: cloth_implicit_workspace_size bytes, 256-byte
+ * aligned.  Bitwise reproducible.  CLOTH_EINVAL for steps < 0, stride
+ * outside 1..1000 or cg_iters < 0; CLOTH_ENOMEM for a short workspace. */
+int cloth_implicit_workspace_size(const cloth_ctx* ctx, size_t* bytes);
+int cloth_step_implicit(cloth_ctx* ctx, int32_t steps, int32_t stride, int32_t cg_iters, void* d_work, size_t bytes,
+                        void* stream);
+
 /* Larger-step network (Sec. 5: larger-step time integration with the
  * cell): from now on one network step (cloth_step_net, cloth_step_pcell,
  * cloth_rollout_net) advances k plain-step time steps, dt_net = k dt, in

@@ -138,6 +138,17 @@ class ClothBatch:
                   self._s())
         return best.value, [float(v) for v in us]
 
+    def step_implicit(self, steps: int, stride: int = 1, cg_iters: int = 20) -> None:
+        """`steps` implicit (linearised backward Euler) plain steps of stride x dt."""
+        n = ctypes.c_size_t()
+        _lib.call("cloth_implicit_workspace_size", self.handle, ctypes.byref(n))
+        ws = getattr(self, "_impl_ws", None)
+        if ws is None or ws.numel() < n.value:
+            ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._impl_ws = ws
+        _lib.call("cloth_step_implicit", self.handle, int(steps), int(stride), int(cg_iters), _ptr(ws), ws.numel(),
+                  self._s())
+
     def set_net_stride(self, k: int) -> None:
         """One network step advances k plain time steps (dt_net = k dt)."""
         _lib.call("cloth_set_net_stride", self.handle, int(k), self._s())

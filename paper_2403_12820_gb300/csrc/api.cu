@@ -1049,6 +1049,53 @@ int cloth_set_boundary(cloth_ctx* c, int32_t b, const float* pin_velocity, float
     return CLOTH_OK;
 }
 
+namespace {
+struct ImplWs {
+    size_t vecs, fabi, part, scal, total;
+};
+ImplWs impl_ws(const cloth_ctx* c)
+{
+    ImplWs w{};
+    size_t off = 0;
+    auto take = [&](size_t floats) { const size_t o = off; off = align_up(off + floats, kAlign / sizeof(float)); return o; };
+    w.vecs = take((size_t)4 * c->L.state_floats);
+    w.fabi = take((size_t)3 * c->total_nodes);
+    w.part = take((size_t)c->B * implicit_grid_x(c->max_nodes));
+    w.scal = take((size_t)3 * c->B);
+    w.total = off * sizeof(float);
+    return w;
+}
+}  // namespace
+
+int cloth_implicit_workspace_size(const cloth_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return CLOTH_EINVAL;
+    *bytes = impl_ws(c).total;
+    return CLOTH_OK;
+}
+
+int cloth_step_implicit(cloth_ctx* c, int32_t steps, int32_t stride, int32_t cg_iters, void* d_work, size_t bytes,
+                        void* stream)
+{
+    if (!c || steps < 0 || stride < 1 || stride > kMaxNetStride || cg_iters < 0 || cg_iters > 100000 || !d_work)
+        return CLOTH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    const ImplWs w = impl_ws(c);
+    if (bytes < w.total) return CLOTH_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* ws = static_cast<float*>(d_work);
+    const float h = (float)stride * c->desc[0].dt;
+    for (int i = 0; i < steps; ++i) {
+        const int rc = launch_step(c, true, ws + w.fabi, s);   // explicit forces at the current state
+        if (rc) return rc;
+        CK(launch_implicit_step(c->d_desc(), c->d_pins(), c->B, c->max_nodes, c->d_state(c->cur), ws + w.fabi,
+                                c->d_state(c->cur ^ 1), ws + w.vecs, c->L.state_floats, ws + w.part, ws + w.scal, h,
+                                cg_iters, c->d_status(), s));
+        c->cur ^= 1;
+    }
+    return CLOTH_OK;
+}
+
 int cloth_set_net_stride(cloth_ctx* c, int32_t k, void* stream)
 {
     if (!c || k < 1 || k > kMaxNetStride) return CLOTH_EINVAL;
