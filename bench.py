@@ -54,6 +54,7 @@ def parse_args(argv=None):
     p.add_argument("--mixed-steps", type=int, default=400)
     p.add_argument("--no-train", action="store_true")
     p.add_argument("--no-pcell", action="store_true")
+    p.add_argument("--no-larger-step", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
     p.add_argument("--de-generations", type=int, default=6)
     return p.parse_args(argv)
@@ -343,6 +344,8 @@ def run_plain(args, rank, world, local):
         out["mixed_fallback"] = run_mixed(args, dev)
     if not args.no_pcell:
         out["pcell"] = run_pcell(args, dev, value / world)
+    if not args.no_larger_step:
+        out["larger_step"] = run_larger_step(args, dev, value / world)
     if not args.no_train:
         out["train"] = run_train(args, dev)
 
@@ -505,6 +508,70 @@ def run_mixed(args, dev):
            "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
     net.close()
     cb.close()
+    return out
+
+
+def run_larger_step(args, dev, plain_rate: float):
+    """Larger time steps on the 64-cloth plain batch (Sec. 5: larger-step and
+    implicit integration): the implicit plain step (linearised backward
+    Euler, 20 CG iterations) and the BF16 network step, both at 10 dt, in
+    node-steps/s of their own steps and of the plain steps they stand for,
+    and the implicit step's mean node distance to the explicit rollout after
+    the same simulated time (100 plain steps), relative to cloth width."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import BF16, Net
+
+    k, iters = 10, 20
+    cfg = wl.plain_batch()
+    x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    nodes = cb.total_nodes
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    cb.set_state(x0, v0)
+    cb.rollout(10 * k, graph_chunk=10 * k)
+    xe, _ = cb.get_state()
+    cb.set_state(x0, v0)
+    cb.step_implicit(10, stride=k, cg_iters=iters)
+    xi, _ = cb.get_state()
+    widths = torch.tensor([(s["cols"] - 1) * s["h"] for s in cfg["specs"]], device=dev)
+    err = torch.stack([(a - b).norm(dim=1).mean() for a, b in zip(cb.split(xi), cb.split(xe))]) / widths
+    t_impl = timed(lambda n: cb.step_implicit(n, stride=k, cg_iters=iters), 10)
+    impl_rate = nodes * 10 / t_impl
+    net = Net(cnn_blob(cfg["specs"][0]["h"]), BF16, device=dev)
+    cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cn.set_net_stride(k)
+    cn.set_state(x0, v0)
+    cn.step_net(net, 3)
+    t_net = timed(lambda n: cn.step_net(net, n), 50)
+    net_rate = nodes * 50 / t_net
+    out = {"workload": f"plain_batch: 64 cloths, sides U{{64..512}} (seed 1002), {nodes / 1e6:.2f}M nodes; "
+                       f"steps of {k} dt",
+           "stride": k,
+           "implicit": {"value": impl_rate, "unit": "node-steps/s (implicit steps of 10 dt)", "cg_iters": iters,
+                        "ms_per_step": t_impl / 10 * 1e3, "plain_equivalent_node_steps_per_s": k * impl_rate,
+                        "ratio_to_explicit": k * impl_rate / plain_rate,
+                        "mean_error_rel_width_after_100_dt": float(err.mean().item()),
+                        "max_cloth_error_rel_width": float(err.max().item()), "status_word": cb.status()},
+           "bf16_network": {"value": net_rate, "unit": "node-steps/s (network steps of 10 dt)",
+                            "ms_per_step": t_net / 50 * 1e3, "plain_equivalent_node_steps_per_s": k * net_rate,
+                            "ratio_to_explicit": k * net_rate / plain_rate, "status_word": cn.status()},
+           "explicit_plain": plain_rate}
+    cb.close()
+    cn.close()
+    net.close()
     return out
 
 
