@@ -138,8 +138,9 @@ int cloth_forces(cloth_ctx* ctx, float* d_f, void* stream);
 
 /* Advance every cloth `steps` plain steps (steps >= 0): the forces above,
  * then the semi-implicit Euler update of Eq. 5, v <- C(v + dt f / m),
- * x <- x + dt v, with pinned velocities held at zero, then sphere contact.
- * One batched launch per step. */
+ * x <- x + dt v, with pinned velocities set to their pins' velocity (zero
+ * unless cloth_pins.velocity or cloth_set_boundary says otherwise), then
+ * sphere contact.  One batched launch per step. */
 int cloth_step_plain(cloth_ctx* ctx, int32_t steps, void* stream);
 
 /* Rollout options.
