@@ -71,12 +71,15 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
 {
     __shared__ float sU[6][SH][SW];
     __shared__ float sW[kPcellBlob];
+    // per channel (w_L, w_N, w_D, 0): one 16-byte shared load per channel
+    __shared__ float4 sW4[12];
     const int4 t = A.tiles[blockIdx.x];
     const ClothDesc& D = A.desc[t.x];
     const int H = D.rows, W = D.cols;
     const int y0 = t.y, x0 = t.z;
     const int tid = threadIdx.x;
     if (tid < kPcellBlob) sW[tid] = A.w[tid];
+    if (tid < 12) sW4[tid] = make_float4(A.w[tid], A.w[12 + tid], A.w[24 + tid], 0.f);
     const float* src = A.src + D.plane_off;
     const int pitch = D.pitch;
     const int64_t pstride = D.plane_stride;
@@ -130,7 +133,8 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
 #pragma unroll
         for (int ch = 0; ch < 12; ++ch) {
             const int dy = ch_dy(ch), dx = ch_dx(ch);
-            f2 wl = F2(sW[ch]), wn = F2(sW[12 + ch]), wd = F2(sW[24 + ch]);
+            const float4 w4 = sW4[ch];
+            f2 wl = F2(w4.x), wn = F2(w4.y), wd = F2(w4.z);
             if constexpr (!kInterior) {
                 const bool cx = dx == 0 ? true : (dx == 1 ? c_p1 : (dx == -1 ? c_m1 : (dx == 2 ? c_p2 : c_m2)));
                 const f2 m = make_float2(cx && rowok(ya, dy) ? 1.f : 0.f, cx && hb && rowok(yb, dy) ? 1.f : 0.f);
