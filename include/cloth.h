@@ -175,7 +175,8 @@ int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* st
  * by cg_iters conjugate-gradient iterations (matrix-free, pinned nodes
  * dv = pin_v - v).  d_work: cloth_implicit_workspace_size bytes, 256-byte
  * aligned.  Bitwise reproducible.  CLOTH_EINVAL for steps < 0, stride
- * outside 1..1000 or cg_iters < 0; CLOTH_ENOMEM for a short workspace. */
+ * outside 1..1000 or cg_iters < 0; CLOTH_ENOMEM for a short workspace;
+ * CLOTH_EUNSUPPORTED for a cloth of 2^31 / 6 padded nodes or more. */
 int cloth_implicit_workspace_size(const cloth_ctx* ctx, size_t* bytes);
 int cloth_step_implicit(cloth_ctx* ctx, int32_t steps, int32_t stride, int32_t cg_iters, void* d_work, size_t bytes,
                         void* stream);

@@ -117,6 +117,7 @@ struct cloth_ctx {
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
     std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
+    std::vector<int32_t> impl_blk;     // implicit step: first block of each cloth, then the total
     std::vector<NetGroup> groups;      // network step: cloths grouped by size
     int64_t group_max_nodes = 0;       // largest group's node count
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
@@ -1051,7 +1052,7 @@ int cloth_set_boundary(cloth_ctx* c, int32_t b, const float* pin_velocity, float
 
 namespace {
 struct ImplWs {
-    size_t vecs, fabi, part, scal, total;
+    size_t vecs, fabi, part, scal, blk, total;
 };
 ImplWs impl_ws(const cloth_ctx* c)
 {
@@ -1062,6 +1063,7 @@ ImplWs impl_ws(const cloth_ctx* c)
     w.fabi = take((size_t)3 * c->total_nodes);
     w.part = take((size_t)c->B * implicit_grid_x(c->max_nodes));
     w.scal = take((size_t)3 * c->B);
+    w.blk = take((size_t)c->B + 1);   // int32 block starts
     w.total = off * sizeof(float);
     return w;
 }
@@ -1082,13 +1084,25 @@ int cloth_step_implicit(cloth_ctx* c, int32_t steps, int32_t stride, int32_t cg_
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
     const ImplWs w = impl_ws(c);
     if (bytes < w.total) return CLOTH_ENOMEM;
+    for (const ClothDesc& d : c->desc)   // the kernels index a cloth's 6 planes in 32 bits
+        if (6 * d.plane_stride >= ((int64_t)1 << 31)) return CLOTH_EUNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     float* ws = static_cast<float*>(d_work);
     const float h = (float)stride * c->desc[0].dt;
+    if (c->impl_blk.empty()) {   // the flat grid's first block of each cloth
+        const int64_t tb = implicit_block_nodes();
+        c->impl_blk.push_back(0);
+        for (int b = 0; b < c->B; ++b)
+            c->impl_blk.push_back(c->impl_blk.back() +
+                                  (int32_t)(((int64_t)c->grids[b].rows * c->grids[b].cols + tb - 1) / tb));
+    }
+    int32_t* blk = reinterpret_cast<int32_t*>(ws + w.blk);
+    CK(cudaMemcpyAsync(blk, c->impl_blk.data(), sizeof(int32_t) * (c->B + 1), cudaMemcpyHostToDevice, s));
     for (int i = 0; i < steps; ++i) {
         const int rc = launch_step(c, true, ws + w.fabi, s);   // explicit forces at the current state
         if (rc) return rc;
-        CK(launch_implicit_step(c->d_desc(), c->d_pins(), c->B, c->max_nodes, c->d_state(c->cur), ws + w.fabi,
+        CK(launch_implicit_step(c->d_desc(), c->d_pins(), c->B, c->max_nodes, blk, c->impl_blk.back(),
+                                c->d_state(c->cur), ws + w.fabi,
                                 c->d_state(c->cur ^ 1), ws + w.vecs, c->L.state_floats, ws + w.part, ws + w.scal, h,
                                 cg_iters, c->d_status(), s));
         c->cur ^= 1;

@@ -145,10 +145,13 @@ cudaError_t launch_fallback_check(const ClothDesc* desc, int B, int64_t max_node
                                   float* last, float bound, const float* net, float* dst, cudaStream_t s);
 // Implicit plain step (implicit.cu): one linearised backward Euler step of
 // h from `state` into `dst`; f_abi holds the explicit forces at `state`.
+// blk[b]: the first of cloth b's blocks of implicit_block_nodes() nodes in
+// a flat grid of n_blocks blocks over all cloths.
 int implicit_grid_x(int64_t max_nodes);
+int implicit_block_nodes();
 cudaError_t launch_implicit_step(const ClothDesc* desc, const uint32_t* pinmask, int B, int64_t max_nodes,
-                                 const float* state, const float* f_abi, float* dst, float* vecs,
-                                 int64_t state_floats, float* part, float* scal, float h, int cg_iters,
+                                 const int32_t* blk, int n_blocks, const float* state, const float* f_abi, float* dst,
+                                 float* vecs, int64_t state_floats, float* part, float* scal, float h, int cg_iters,
                                  int32_t* status, cudaStream_t s);
 cudaError_t launch_topology(const ClothDesc* desc, int32_t b, int32_t rows, int32_t cols, uint16_t* mask,
                             cudaStream_t s);

@@ -37,9 +37,24 @@ struct ImplArgs {
     float* rr;               // [B]: r . r
     float* rr_new;           // [B]
     float* pap;              // [B]: p . A p
-    int gx;
+    const int32_t* blk;      // [B + 1]: first block of each cloth (blocks of TB nodes)
+    int B;
+    int gx;                  // partial sums per cloth (the most blocks of one cloth)
     float h;                 // the step
 };
+
+// The cloth b of this block and the block's index k within the cloth.
+__device__ __forceinline__ void locate(const ImplArgs& A, int& b, int& k)
+{
+    const int x = (int)blockIdx.x;
+    int lo = 0, hi = A.B - 1;
+    while (lo < hi) {   // last b with blk[b] <= x
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.blk[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    b = lo;
+    k = x - A.blk[lo];
+}
 
 __device__ __forceinline__ bool pinned_at(const ClothDesc& D, const uint32_t* pm, int r, int c)
 {
@@ -51,31 +66,36 @@ __device__ __forceinline__ int nb_dy(int s) { return s == 1 || s == 4 || s == 5 
 __device__ __forceinline__ int nb_dx(int s) { return s == 0 || s == 4 || s == 7 ? 1 : (s == 2 || s == 5 || s == 6 ? -1 : (s == 8 ? 2 : (s == 10 ? -2 : 0))); }
 __device__ __forceinline__ int nb_type(int s) { return s < 4 ? 0 : (s < 8 ? 1 : 2); }
 
-// sum_j K_s(ij) (w_j - w_i) at node (r, c); w is read through `wat`
+// sum_j K_s(ij) (w_j - w_i) at node (r, c) of a cloth whose u planes start
+// at U (plane stride ps, offsets within the cloth in 32 bits); w is read
+// through wat(offset, row, column, w)
 template <class W>
-__device__ __forceinline__ void kw(const ClothDesc& D, const float* st, int r, int c, W wat, float (&out)[3])
+__device__ __forceinline__ void kw(const ClothDesc& D, const float* __restrict__ U, int ps, int r, int c, W wat,
+                                   float (&out)[3])
 {
-    const int64_t oi = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
-    const float ui[3] = {st[oi], st[oi + D.plane_stride], st[oi + 2 * D.plane_stride]};
+    const int rows = D.rows, cols = D.cols, pitch = D.pitch;
+    const float h = D.h, kst = D.k_struct, ksh = D.k_shear, kbe = D.k_bend;
+    const int oi = r * pitch + col_pos(c);
+    const float ui[3] = {U[oi], U[oi + ps], U[oi + 2 * ps]};
     float wi[3];
-    wat(r, c, wi);
+    wat(oi, r, c, wi);
     out[0] = out[1] = out[2] = 0.f;
 #pragma unroll
     for (int s = 0; s < 12; ++s) {
         const int dy = nb_dy(s), dx = nb_dx(s), rj = r + dy, cj = c + dx;
-        if (rj < 0 || rj >= D.rows || cj < 0 || cj >= D.cols) continue;
+        if (rj < 0 || rj >= rows || cj < 0 || cj >= cols) continue;
         const int t = nb_type(s);
-        const float k = t == 0 ? D.k_struct : (t == 1 ? D.k_shear : D.k_bend);
-        const float L = t == 0 ? D.h : (t == 1 ? 1.41421356237309515f * D.h : 2.f * D.h);
-        const int64_t oj = D.plane_off + (int64_t)rj * D.pitch + col_pos(cj);
-        const float d0 = fmaf((float)dx, D.h, st[oj] - ui[0]);
-        const float d1 = fmaf((float)dy, D.h, st[oj + D.plane_stride] - ui[1]);
-        const float d2 = st[oj + 2 * D.plane_stride] - ui[2];
+        const float k = t == 0 ? kst : (t == 1 ? ksh : kbe);
+        const float L = t == 0 ? h : (t == 1 ? 1.41421356237309515f * h : 2.f * h);
+        const int oj = rj * pitch + col_pos(cj);
+        const float d0 = fmaf((float)dx, h, U[oj] - ui[0]);
+        const float d1 = fmaf((float)dy, h, U[oj + ps] - ui[1]);
+        const float d2 = U[oj + 2 * ps] - ui[2];
         const float rl = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
         const float n0 = d0 * rl, n1 = d1 * rl, n2 = d2 * rl;
         const float cc = fmaxf(0.f, 1.f - L * rl);
         float wj[3];
-        wat(rj, cj, wj);
+        wat(oj, rj, cj, wj);
         const float e0 = wj[0] - wi[0], e1 = wj[1] - wi[1], e2 = wj[2] - wi[2];
         const float ne = fmaf(n0, e0, fmaf(n1, e1, n2 * e2));
         // k [c e + (1 - c) (n . e) n]
@@ -104,32 +124,30 @@ __device__ __forceinline__ float block_sum(float v, float* red)
 __global__ void __launch_bounds__(TB) impl_rhs_kernel(ImplArgs A)
 {
     __shared__ float red[TB / 32];
-    const int b = blockIdx.y;
+    int b, kb;
+    locate(A, b, kb);
     const ClothDesc& D = A.desc[b];
-    const int64_t n = (int64_t)D.rows * D.cols;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if ((int64_t)blockIdx.x * TB >= n) return;   // whole block past the cloth
+    const int n = D.rows * D.cols, ps = (int)D.plane_stride;
+    const int i = kb * TB + (int)threadIdx.x;
     float rr = 0.f;
     if (i < n) {
-        const int r = (int)(i / D.cols), c = (int)(i % D.cols);
-        const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
-        const float* st = A.state;
-        auto vat = [&](int rr_, int cc_, float (&w)[3]) {
-            const int64_t q = D.plane_off + (int64_t)rr_ * D.pitch + col_pos(cc_) + 3 * D.plane_stride;
-            w[0] = st[q]; w[1] = st[q + D.plane_stride]; w[2] = st[q + 2 * D.plane_stride];
-        };
-        auto dv0 = [&](int rr_, int cc_, float (&w)[3]) {
+        const int r = i / D.cols, c = i % D.cols;
+        const int64_t o = D.plane_off + r * D.pitch + col_pos(c);
+        const float* U = A.state + D.plane_off;
+        const float* V = U + 3 * D.plane_stride;
+        auto vat = [&](int q, int, int, float (&w)[3]) { w[0] = V[q]; w[1] = V[q + ps]; w[2] = V[q + 2 * ps]; };
+        auto dv0 = [&](int q, int rr_, int cc_, float (&w)[3]) {
             float v[3];
-            vat(rr_, cc_, v);
+            vat(q, rr_, cc_, v);
             const bool pj = pinned_at(D, A.pinmask, rr_, cc_);
 #pragma unroll
             for (int k = 0; k < 3; ++k) w[k] = pj ? pin_v(D, k) - v[k] : 0.f;
         };
         const bool pi = pinned_at(D, A.pinmask, r, c);
         float kv[3], kd[3], d0[3];
-        kw(D, st, r, c, vat, kv);
-        kw(D, st, r, c, dv0, kd);
-        dv0(r, c, d0);
+        kw(D, U, ps, r, c, vat, kv);
+        kw(D, U, ps, r, c, dv0, kd);
+        dv0(r * D.pitch + col_pos(c), r, c, d0);
         const float hh = A.h * A.h, md = D.m + A.h * D.drag;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -144,30 +162,29 @@ __global__ void __launch_bounds__(TB) impl_rhs_kernel(ImplArgs A)
         }
     }
     const float s = block_sum(rr, red);
-    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + blockIdx.x] = s;
+    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + kb] = s;
 }
 
 // A p (filtered: 0 at pinned nodes) and block partials of p . A p
 __global__ void __launch_bounds__(TB) impl_matvec_kernel(ImplArgs A)
 {
     __shared__ float red[TB / 32];
-    const int b = blockIdx.y;
+    int b, kb;
+    locate(A, b, kb);
     const ClothDesc& D = A.desc[b];
-    const int64_t n = (int64_t)D.rows * D.cols;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if ((int64_t)blockIdx.x * TB >= n) return;
+    const int n = D.rows * D.cols, ps = (int)D.plane_stride;
+    const int i = kb * TB + (int)threadIdx.x;
     float pap = 0.f;
     if (i < n) {
-        const int r = (int)(i / D.cols), c = (int)(i % D.cols);
-        const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
-        auto pat = [&](int rr_, int cc_, float (&w)[3]) {
-            const int64_t q = D.plane_off + (int64_t)rr_ * D.pitch + col_pos(cc_);
-            w[0] = A.p[q]; w[1] = A.p[q + D.plane_stride]; w[2] = A.p[q + 2 * D.plane_stride];
-        };
+        const int r = i / D.cols, c = i % D.cols;
+        const int oi = r * D.pitch + col_pos(c);
+        const int64_t o = D.plane_off + oi;
+        const float* P = A.p + D.plane_off;
+        auto pat = [&](int q, int, int, float (&w)[3]) { w[0] = P[q]; w[1] = P[q + ps]; w[2] = P[q + 2 * ps]; };
         const bool pi = pinned_at(D, A.pinmask, r, c);
         float kp[3], pv[3];
-        kw(D, A.state, r, c, pat, kp);
-        pat(r, c, pv);
+        kw(D, A.state + D.plane_off, ps, r, c, pat, kp);
+        pat(oi, r, c, pv);
         const float hh = A.h * A.h, md = D.m + A.h * D.drag;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -177,7 +194,7 @@ __global__ void __launch_bounds__(TB) impl_matvec_kernel(ImplArgs A)
         }
     }
     const float s = block_sum(pap, red);
-    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + blockIdx.x] = s;
+    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + kb] = s;
 }
 
 // out[b] = sum of cloth b's block partials, in block order (one warp per cloth)
@@ -198,16 +215,16 @@ __global__ void impl_reduce_kernel(const ClothDesc* __restrict__ desc, const flo
 __global__ void __launch_bounds__(TB) impl_update_kernel(ImplArgs A)
 {
     __shared__ float red[TB / 32];
-    const int b = blockIdx.y;
+    int b, kb;
+    locate(A, b, kb);
     const ClothDesc& D = A.desc[b];
-    const int64_t n = (int64_t)D.rows * D.cols;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if ((int64_t)blockIdx.x * TB >= n) return;
+    const int n = D.rows * D.cols;
+    const int i = kb * TB + (int)threadIdx.x;
     const float pap = A.pap[b];
     const float alpha = pap > 0.f ? A.rr[b] / pap : 0.f;
     float rr = 0.f;
     if (i < n) {
-        const int r = (int)(i / D.cols), c = (int)(i % D.cols);
+        const int r = i / D.cols, c = i % D.cols;
         const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -219,21 +236,22 @@ __global__ void __launch_bounds__(TB) impl_update_kernel(ImplArgs A)
         }
     }
     const float s = block_sum(rr, red);
-    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + blockIdx.x] = s;
+    if (threadIdx.x == 0) A.part[(int64_t)b * A.gx + kb] = s;
 }
 
 // p = r + beta p with beta = rr_new / rr; then rr <- rr_new (thread 0 of
 // each cloth's first block, after its own use)
 __global__ void __launch_bounds__(TB) impl_dir_kernel(ImplArgs A)
 {
-    const int b = blockIdx.y;
+    int b, kb;
+    locate(A, b, kb);
     const ClothDesc& D = A.desc[b];
-    const int64_t n = (int64_t)D.rows * D.cols;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    const int n = D.rows * D.cols;
+    const int i = kb * TB + (int)threadIdx.x;
     if (i >= n) return;
     const float rr = A.rr[b];
     const float beta = rr > 0.f ? A.rr_new[b] / rr : 0.f;
-    const int r = (int)(i / D.cols), c = (int)(i % D.cols);
+    const int r = i / D.cols, c = i % D.cols;
     const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -251,12 +269,13 @@ __global__ void impl_swap_kernel(int B, float* __restrict__ rr, const float* __r
 // v' = C(v + dv), x' = x + h v', sphere contact, into dst
 __global__ void __launch_bounds__(TB) impl_finish_kernel(ImplArgs A, float* __restrict__ dst, int32_t* status)
 {
-    const int b = blockIdx.y;
+    int b, kb;
+    locate(A, b, kb);
     const ClothDesc& D = A.desc[b];
-    const int64_t n = (int64_t)D.rows * D.cols;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    const int n = D.rows * D.cols;
+    const int i = kb * TB + (int)threadIdx.x;
     if (i >= n) return;
-    const int r = (int)(i / D.cols), c = (int)(i % D.cols);
+    const int r = i / D.cols, c = i % D.cols;
     const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
     const bool pi = pinned_at(D, A.pinmask, r, c);
     float un[3], vn[3];
@@ -278,10 +297,11 @@ __global__ void __launch_bounds__(TB) impl_finish_kernel(ImplArgs A, float* __re
 }  // namespace
 
 int implicit_grid_x(int64_t max_nodes) { return (int)((max_nodes + TB - 1) / TB); }
+int implicit_block_nodes() { return TB; }
 
 cudaError_t launch_implicit_step(const ClothDesc* desc, const uint32_t* pinmask, int B, int64_t max_nodes,
-                                 const float* state, const float* f_abi, float* dst, float* vecs,
-                                 int64_t state_floats, float* part, float* scal, float h, int cg_iters,
+                                 const int32_t* blk, int n_blocks, const float* state, const float* f_abi, float* dst,
+                                 float* vecs, int64_t state_floats, float* part, float* scal, float h, int cg_iters,
                                  int32_t* status, cudaStream_t s)
 {
     ImplArgs a{};
@@ -297,9 +317,11 @@ cudaError_t launch_implicit_step(const ClothDesc* desc, const uint32_t* pinmask,
     a.rr = scal;
     a.rr_new = scal + B;
     a.pap = scal + 2 * B;
+    a.blk = blk;
+    a.B = B;
     a.gx = implicit_grid_x(max_nodes);
     a.h = h;
-    const dim3 grid((unsigned)a.gx, (unsigned)B);
+    const dim3 grid((unsigned)n_blocks);
     impl_rhs_kernel<<<grid, TB, 0, s>>>(a);
     impl_reduce_kernel<<<B, 32, 0, s>>>(desc, part, a.gx, a.rr);
     for (int it = 0; it < cg_iters; ++it) {
