@@ -208,6 +208,30 @@ def oracle_plain_rate(cfg, steps: int, cores: int):
     return nodes * steps / wall, wall
 
 
+def oracle_single_rates():
+    """Single-thread FP64 oracle rates: the plain step on the batch's largest
+    cloth (4 steps) and the C-cell network step on one 128 x 128 cloth."""
+    import numpy as np
+
+    import oracle
+    from paper_2403_12820_gb300 import workloads as wl
+    cfg = wl.plain_batch()
+    b = max(range(len(cfg["specs"])), key=lambda i: cfg["specs"][i]["rows"] * cfg["specs"][i]["cols"])
+    s = cfg["specs"][b]
+    t = time.perf_counter()
+    oracle.step(s, cfg["x"][b], cfg["v"][b], pins=cfg["pins"][b], steps=4)
+    plain = s["rows"] * s["cols"] * 4 / (time.perf_counter() - t)
+    cc = wl.cnn_batch(count=1)
+    w = cnn_blob(cc["specs"][0]["h"]).astype(np.float64)
+    t = time.perf_counter()
+    oracle.net_step(w, cc["specs"][0], cc["x"][0], cc["v"][0], pins=cc["pins"][0], steps=1)
+    cnn = cc["specs"][0]["rows"] * cc["specs"][0]["cols"] / (time.perf_counter() - t)
+    return {"single_thread_plain_node_steps_per_s": plain,
+            "single_thread_cnn_node_steps_per_s": cnn,
+            "single_thread_sample": f"plain: one {s['rows']} x {s['cols']} cloth x 4 steps; "
+                                    "C-cell network step: one 128 x 128 cloth x 1 step"}
+
+
 # ------------------------------------------------------------------ runs
 def run_reference(args, rank, world):
     if rank != 0:
@@ -355,6 +379,7 @@ def run_plain(args, rank, world, local):
         out["cpu_baseline"] = {"value": rate, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
                                "sample": f"all 64 cloths x 24 steps (143M node-steps), FP64 oracle, "
                                          f"{cores} processes, {wall:.1f} s wall"}
+        out["cpu_baseline"].update(oracle_single_rates())
     cb.close()
     return out
 
