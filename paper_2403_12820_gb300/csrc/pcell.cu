@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(NT, CLOTH_PCELL_MINB) pcell_kernel(PcellArgs A
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float lat = k == 0 ? (float)dx * h : (k == 1 ? (float)dy * h : 0.f);
-                const f2 phi = add2(F2(lat), sub2(U2(k, dy, dx), ui[k]));
+                // the lattice offset along coordinate k (none along z, nor
+                // across the channel's direction: no add there)
+                const int lk = k == 0 ? dx : (k == 1 ? dy : 0);
+                const f2 du = sub2(U2(k, dy, dx), ui[k]);
+                const f2 phi = lk == 0 ? du : add2(F2((float)lk * h), du);
                 const f2 xi = sub2(U2(3 + k, dy, dx), vi[k]);
                 // 1 + alpha phi^2 >= 1: never subnormal, the flushing form is exact here
                 const f2 q = fma2(mul2(alpha, phi), phi, F2(1.f));
