@@ -226,10 +226,16 @@ def oracle_single_rates():
     t = time.perf_counter()
     oracle.net_step(w, cc["specs"][0], cc["x"][0], cc["v"][0], pins=cc["pins"][0], steps=1)
     cnn = cc["specs"][0]["rows"] * cc["specs"][0]["cols"] / (time.perf_counter() - t)
+    sc = wl.single_cloth(n=32)
+    t = time.perf_counter()
+    oracle.step(sc["specs"][0], sc["x"][0], sc["v"][0], pins=sc["pins"][0], steps=2000)
+    single_us = (time.perf_counter() - t) / 2000 * 1e6
     return {"single_thread_plain_node_steps_per_s": plain,
+            "single_cloth_32x32_us_per_step": single_us,
             "single_thread_cnn_node_steps_per_s": cnn,
             "single_thread_sample": f"plain: one {s['rows']} x {s['cols']} cloth x 4 steps; "
-                                    "C-cell network step: one 128 x 128 cloth x 1 step"}
+                                    "C-cell network step: one 128 x 128 cloth x 1 step; "
+                                    "single cloth: 32 x 32 x 2000 steps"}
 
 
 # ------------------------------------------------------------------ runs
@@ -362,6 +368,7 @@ def run_plain(args, rank, world, local):
                       "d2h_bytes_per_step": hout.numel() * 4 / per_call,
                       "steps_per_call": per_call, "calls": calls}
 
+    out["single_cloth"] = run_single_cloth(dev)
     if not args.no_cnn:
         out["cnn"] = run_cnn(args, dev)
     if not args.no_mixed:
@@ -532,6 +539,38 @@ def run_mixed(args, dev):
            "coulomb_contact": {"network_unchecked": friction_net, "plain": friction_plain, "friction": 0.3},
            "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
     net.close()
+    cb.close()
+    return out
+
+
+def run_single_cloth(dev):
+    """One 32 x 32 cloth (the single-cloth workload: two corners pinned,
+    1e-4 m noise), 2000 plain steps: a latency-bound case (the 24 KB state
+    fits one SM), reported as microseconds per step (the CPU baseline times
+    the oracle on it), with the paper's own step rates (100 x 100 cloths,
+    other hardware) as context."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+
+    cfg = wl.single_cloth(n=32)
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cb.set_state(pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev))
+    cb.rollout(200, graph_chunk=100)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cb.rollout(2000, graph_chunk=100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / 2000 * 1e3
+    out = {"workload": "single_cloth: 32 x 32 (seed 1001), 2000 plain steps in CUDA graphs of 100",
+           "us_per_step": us, "node_steps_per_s": 1024 / us * 1e6, "status_word": cb.status(),
+           "paper_context": {"nn_framework_node_steps_per_s": 2.32e6, "pbs_cpu_node_steps_per_s": 2.01e6,
+                             "note": "Table 2: 232 and 201 steps/s on 100 x 100 cloths (RTX 2080 Ti; "
+                                     "a CPU of unstated model)"}}
     cb.close()
     return out
 
