@@ -554,9 +554,12 @@ def run_single_cloth(dev):
     from paper_2403_12820_gb300 import workloads as wl
     from paper_2403_12820_gb300.cloth import ClothBatch, pack
 
+    from paper_2403_12820_gb300 import tune
+
     cfg = wl.single_cloth(n=32)
     cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cb.set_state(pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev))
+    rec = tune.autotune(cb, candidates=((4, -1), (8, -1), (16, -1), (32, -1), (-1, -1)), warmup=3, steps=50)
     cb.rollout(200, graph_chunk=100)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -568,6 +571,8 @@ def run_single_cloth(dev):
     us = e0.elapsed_time(e1) / 2000 * 1e3
     out = {"workload": "single_cloth: 32 x 32 (seed 1001), 2000 plain steps in CUDA graphs of 100",
            "us_per_step": us, "node_steps_per_s": 1024 / us * 1e6, "status_word": cb.status(),
+           "launch": {"seg_rows": rec["seg_rows"], "warps_per_sm": rec["warps_per_sm"],
+                      "candidates_us": {f"{R},{w}": round(t, 2) for R, w, t in rec["candidates"]}},
            "paper_context": {"nn_framework_node_steps_per_s": 2.32e6, "pbs_cpu_node_steps_per_s": 2.01e6,
                              "note": "Table 2: 232 and 201 steps/s on 100 x 100 cloths (RTX 2080 Ti; "
                                      "a CPU of unstated model)"}}
