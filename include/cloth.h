@@ -163,6 +163,15 @@ typedef struct {
 /* Plain-step rollout under the options above. */
 int cloth_rollout_plain(cloth_ctx* ctx, const cloth_rollout_opts* opts, void* stream);
 
+/* Memory of the Eq. 8 unroll (cloth_train_loss*): with k >= 1 only every
+ * k-th unrolled state is kept, and the backward sweep recomputes the others
+ * of a segment from its checkpoint when it reaches the segment: (S / k + k)
+ * states instead of S + 1, about one more cell forward per unrolled step
+ * (k near sqrt(S) minimises the memory).  k = 0 (the default) keeps every
+ * state.  Loss and gradient are bitwise the same either way.  Query
+ * cloth_train_workspace_size after this call.  CLOTH_EINVAL for k < 0. */
+int cloth_set_train_segment(cloth_ctx* ctx, int32_t k);
+
 /* Implicit plain step (Sec. 3.1: implicit integration is the stable choice
  * for large time steps; Sec. 5: the comparison for a larger-step cell):
  * `steps` linearised backward Euler steps of h = stride dt.  Per step, with

@@ -149,6 +149,11 @@ class ClothBatch:
         _lib.call("cloth_step_implicit", self.handle, int(steps), int(stride), int(cg_iters), _ptr(ws), ws.numel(),
                   self._s())
 
+    def set_train_segment(self, k: int) -> None:
+        """Keep every k-th unrolled state of the Eq. 8 loss (0: all) and
+        recompute the rest in the backward sweep."""
+        _lib.call("cloth_set_train_segment", self.handle, int(k))
+
     def set_net_stride(self, k: int) -> None:
         """One network step advances k plain time steps (dt_net = k dt)."""
         _lib.call("cloth_set_net_stride", self.handle, int(k), self._s())

@@ -113,6 +113,7 @@ struct cloth_ctx {
     int grid = 0, block = 128;
     int warps_per_sm = 0;              // 0: the plain-step kernel's occupancy
     int net_stride = 1;                // plain steps one network step spans
+    int train_seg = 0;                 // Eq. 8 unroll: keep every train_seg-th state (0: all)
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
@@ -329,7 +330,10 @@ TrainWs train_ws(const cloth_ctx* c, int S)
     TrainWs w{};
     size_t off = 0;
     auto take = [&](size_t floats) { const size_t o = off; off = align_up(off + floats, kAlign / sizeof(float)); return o; };
-    w.z = take((size_t)(S + 1) * B * 6 * HW);
+    // unrolled states kept: all S + 1, or with segments of k the checkpoints
+    // t = 0, k, 2k, ... and one segment's k - 1 others
+    const int k = c->train_seg;
+    w.z = take((size_t)(k > 0 ? S / k + k : S + 1) * B * 6 * HW);
     w.a = take(n3); w.at = take(n3); w.ga0 = take(n3); w.gu = take(n3); w.gv = take(n3);
     w.ga = take(n3); w.gfp = take(n3); w.ge = take(n3); w.gn = take(n3);
     w.gz = take((size_t)B * 6 * HW);
@@ -381,7 +385,15 @@ int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha
     const int64_t HW = (int64_t)H * W, NHW = (int64_t)B * HW;
     float* ws = static_cast<float*>(d_work);
     float* Z = ws + L.z;
-    auto Zt = [&](int t) { return Z + (size_t)t * B * 6 * HW; };
+    // state t of the unroll: every state is kept (train_seg 0), or the
+    // checkpoints t = 0, k, 2k, ... and, for the other t, the slot of its
+    // place in the segment (one segment at a time)
+    const int k = c->train_seg;
+    const int n_ck = k > 0 ? S / k + 1 : S + 1;
+    auto Zt = [&](int t) {
+        const size_t slot = (k == 0 || t % k == 0) ? (size_t)(k ? t / k : t) : (size_t)(n_ck + t % k - 1);
+        return Z + slot * B * 6 * HW;
+    };
     float *A = ws + L.a, *AT = ws + L.at, *GA0 = ws + L.ga0, *GU = ws + L.gu, *GV = ws + L.gv;
     float *GA = ws + L.ga, *GFP = ws + L.gfp, *GE = ws + L.ge, *GN = ws + L.gn, *GZ = ws + L.gz;
     float *FABI = ws + L.fabi, *COEF = ws + L.coef, *PART = ws + L.part;
@@ -430,10 +442,20 @@ int train_loss_impl(cloth_ctx* c, int32_t S, const float* d_targets, float alpha
     CK(launch_sum_partials(PART, (S + 1) * blocks, d_loss, s));
     if (!with_grad) return CLOTH_OK;
 
-    // backward sweep, recomputing each step's activations (step checkpointing)
+    // backward sweep, recomputing each step's activations (step checkpointing);
+    // with segments, the states of a segment are recomputed from its
+    // checkpoint when the sweep enters it (the same kernels: the same bits)
     CK(cudaMemsetAsync(GU, 0, sizeof(float) * 3 * NHW, s));
     CK(cudaMemsetAsync(GV, 0, sizeof(float) * 3 * NHW, s));
+    int seg_loaded = -1;
     for (int t = S; t >= 1; --t) {
+        if (k > 0 && (t - 1) / k != seg_loaded) {
+            seg_loaded = (t - 1) / k;
+            for (int q = seg_loaded * k; q < std::min(seg_loaded * k + k - 1, S); ++q) {
+                CK(forward(Zt(q), A));
+                CK(launch_train_euler(D, P, Zt(q), A, Zt(q + 1), B, H, W, s));
+            }
+        }
         CK(launch_data_term(D, P, Zt(t), d_targets + (size_t)(t - 1) * 3 * c->total_nodes, COEF + B, GU, nullptr,
                             B, H, W, s));
         CK(launch_euler_adjoint(D, P, GU, GV, t == 1 ? GA0 : nullptr, GA, GFP, B, H, W, s));
@@ -1107,6 +1129,13 @@ int cloth_step_implicit(cloth_ctx* c, int32_t steps, int32_t stride, int32_t cg_
                                 cg_iters, c->d_status(), s));
         c->cur ^= 1;
     }
+    return CLOTH_OK;
+}
+
+int cloth_set_train_segment(cloth_ctx* c, int32_t k)
+{
+    if (!c || k < 0) return CLOTH_EINVAL;
+    c->train_seg = k;
     return CLOTH_OK;
 }
 
