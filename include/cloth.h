@@ -260,6 +260,13 @@ int cloth_topology(cloth_ctx* ctx, int32_t b, uint16_t* d_mask, void* stream);
  * status word; with clear != 0 it is reset to 0 afterwards. */
 int cloth_status(cloth_ctx* ctx, int32_t* h_status, int32_t clear, void* stream);
 
+/* Self-test of the bounded waits: one warp waits `polls` polls on an
+ * mbarrier that nothing completes, then gives up, sets
+ * CLOTH_STATUS_TIMEOUT in the context's status word and returns (the path a
+ * tensor-core wait that runs out takes).  The context stays usable.
+ * CLOTH_EINVAL for polls < 1. */
+int cloth_selftest_wait_timeout(cloth_ctx* ctx, int32_t polls, void* stream);
+
 /* Number of cloths and total nodes of the context. */
 int cloth_info(const cloth_ctx* ctx, int32_t* B, int64_t* total_nodes);
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "cloth_set_boundary": (c_int32, [c_void_p, c_int32, P(c_float), c_float, c_void_p]),
     "cloth_set_net_stride": (c_int32, [c_void_p, c_int32, c_void_p]),
     "cloth_set_train_segment": (c_int32, [c_void_p, c_int32]),
+    "cloth_selftest_wait_timeout": (c_int32, [c_void_p, c_int32, c_void_p]),
     "cloth_implicit_workspace_size": (c_int32, [c_void_p, P(c_size_t)]),
     "cloth_step_implicit": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_size_t, c_void_p]),
     "cloth_tune_launch": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32), c_int32, c_int32, P(c_float),

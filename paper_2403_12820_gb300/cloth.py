@@ -295,6 +295,10 @@ class ClothBatch:
         _lib.call("cloth_topology", self.handle, int(b), _ptr(m), self._s())
         return m
 
+    def selftest_wait_timeout(self, polls: int = 1000) -> None:
+        """Run the bounded-wait self-test (sets the timeout bit of the status word)."""
+        _lib.call("cloth_selftest_wait_timeout", self.handle, int(polls), self._s())
+
     def status(self, clear: bool = False) -> int:
         st = ctypes.c_int32()
         _lib.call("cloth_status", self.handle, ctypes.byref(st), int(clear), self._s())

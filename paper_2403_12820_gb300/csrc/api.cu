@@ -1166,6 +1166,13 @@ int cloth_topology(cloth_ctx* c, int32_t b, uint16_t* d_mask, void* stream)
     return CLOTH_OK;
 }
 
+int cloth_selftest_wait_timeout(cloth_ctx* c, int32_t polls, void* stream)
+{
+    if (!c || polls < 1) return CLOTH_EINVAL;
+    CK(launch_wait_timeout_selftest(c->d_status(), (uint32_t)polls, static_cast<cudaStream_t>(stream)));
+    return CLOTH_OK;
+}
+
 int cloth_status(cloth_ctx* c, int32_t* h_status, int32_t clear, void* stream)
 {
     if (!c || !h_status) return CLOTH_EINVAL;

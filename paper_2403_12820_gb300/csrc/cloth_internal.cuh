@@ -143,6 +143,9 @@ cudaError_t launch_get_state(const ClothDesc* desc, int32_t B, int64_t total_nod
                              const float* state, float* x, float* v, cudaStream_t s);
 cudaError_t launch_fallback_check(const ClothDesc* desc, int B, int64_t max_nodes, int32_t* mode, float* resid,
                                   float* last, float bound, const float* net, float* dst, cudaStream_t s);
+// Bounded-wait self-test (selftest.cu): a wait that cannot complete gives up
+// after `polls` polls and sets kStatusTimeout.
+cudaError_t launch_wait_timeout_selftest(int32_t* status, uint32_t polls, cudaStream_t s);
 // Implicit plain step (implicit.cu): one linearised backward Euler step of
 // h from `state` into `dst`; f_abi holds the explicit forces at `state`.
 // blk[b]: the first of cloth b's blocks of implicit_block_nodes() nodes in

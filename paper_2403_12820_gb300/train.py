@@ -84,6 +84,28 @@ class Trainer:
         m = stages.freeze_mask(self.cell, trainable, self.n_params)
         self.mask = torch.from_numpy(m).to(self.device)
 
+    def save(self, path: str) -> None:
+        """Checkpoint: weights, Adam moments and step, the window sampler's
+        random state and the cell kind, as one .npz file (the dataset and
+        schedules are the caller's)."""
+        import json
+        np.savez(path, w=self.w.detach().cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
+                 t=np.int64(self.t), rng=np.array(json.dumps(self.rng.bit_generator.state)),
+                 cell=np.array(self.cell))
+
+    def load(self, path: str) -> None:
+        """Resume from save(): the same cell on the same dataset continues
+        bit for bit."""
+        import json
+        with np.load(path) as f:
+            if str(f["cell"]) != self.cell:
+                raise ValueError(f"checkpoint of the {f['cell']} cell, trainer of the {self.cell} cell")
+            self.w.copy_(torch.from_numpy(f["w"]).to(self.device))
+            self.m.copy_(torch.from_numpy(f["m"]).to(self.device))
+            self.v.copy_(torch.from_numpy(f["v"]).to(self.device))
+            self.t = int(f["t"])
+            self.rng.bit_generator.state = json.loads(str(f["rng"]))
+
     def lr_at(self, t: int) -> float:
         return float(self.lr_schedule(t)) if self.lr_schedule is not None else self.lr
 
