@@ -52,7 +52,7 @@ enum {
 enum {
     CLOTH_STATUS_NONFINITE = 1,   /* a step produced a non-finite x or v */
     CLOTH_STATUS_TIMEOUT = 2,     /* a bounded device wait ran out       */
-    CLOTH_STATUS_BOUNDS = 4       /* an index check failed (debug build) */
+    CLOTH_STATUS_BOUNDS = 4       /* reserved for index checks; no kernel of this library sets it */
 };
 
 /* Lattice of one cloth: rows x cols nodes, spacing h (m), node mass m (kg).
