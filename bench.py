@@ -619,6 +619,16 @@ def run_larger_step(args, dev, plain_rate: float):
     err = torch.stack([(a - b).norm(dim=1).mean() for a, b in zip(cb.split(xi), cb.split(xe))]) / widths
     t_impl = timed(lambda n: cb.step_implicit(n, stride=k, cg_iters=iters), 10)
     impl_rate = nodes * 10 / t_impl
+    # the explicit plain rollout again with every cloth's pins moving (0.05 m/s
+    # along x), selected at run time: the moving-boundary path's cost
+    cb.set_state(x0, v0)
+    for b in range(cb.B):
+        cb.set_boundary(b, (0.05, 0.0, 0.0), -1.0)
+    cb.rollout(100, graph_chunk=100)
+    t_mv = timed(lambda n: cb.rollout(n, graph_chunk=100), 1000)
+    moving_rate = nodes * 1000 / t_mv
+    for b in range(cb.B):
+        cb.set_boundary(b, (0.0, 0.0, 0.0), -1.0)
     net = Net(cnn_blob(cfg["specs"][0]["h"]), BF16, device=dev)
     cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cn.set_net_stride(k)
@@ -637,7 +647,9 @@ def run_larger_step(args, dev, plain_rate: float):
            "bf16_network": {"value": net_rate, "unit": "node-steps/s (network steps of 10 dt)",
                             "ms_per_step": t_net / 50 * 1e3, "plain_equivalent_node_steps_per_s": k * net_rate,
                             "ratio_to_explicit": k * net_rate / plain_rate, "status_word": cn.status()},
-           "explicit_plain": plain_rate}
+           "explicit_plain": plain_rate,
+           "explicit_plain_moving_pins": {"value": moving_rate, "unit": "node-steps/s",
+                                          "pin_velocity_m_s": [0.05, 0.0, 0.0]}}
     cb.close()
     cn.close()
     net.close()
