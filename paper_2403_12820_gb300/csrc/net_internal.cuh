@@ -89,7 +89,7 @@ inline NetLayout net_layout()
     size_t off = 0;
     L.blob = off; off = al(off + sizeof(float) * kBlob);
     L.part = off; off = al(off + sizeof(float) * (size_t)kWgradBlocks * kParams);
-    L.pack = off; off = al(off + 65536);          // packed BF16 tensor-core operands
+    L.pack = off; off = al(off + 131072);         // packed tensor-core operands
     L.status = off; off = al(off + 64);
     L.total = off;
     return L;

@@ -2,36 +2,47 @@
 // into one kernel on the tcgen05 tensor cores: BF16 operands in shared
 // memory, FP32 accumulators in tensor memory.
 //
-// One CTA (8 warps) per SM loops over tiles of R x WO output nodes.  Every
-// layer region of a tile is stored at the pitch PT = WO + 6, so node
-// (ry, rx) of a region has the linear index ry * PT + rx, an M = 128 MMA
-// covers 128 consecutive linear indices ("a chunk"), and a 3x3 tap (ky, kx)
-// is the same buffer shifted by ky * PT + kx rows — a descriptor offset,
-// never a copy (implicit GEMM).  Per tile:
-//   1. stage u, v of the (R+6)-row input region as BF16, 8 channels per
-//      node and field (in_scale u | 0, in_scale v | 0);
-//   2. layer 1 (Eq. 6): per chunk and field, 5 MMAs of K = 16, each pairing
-//      two taps (the second core-matrix column of K sits LBO = the taps'
-//      row distance further) against W1[:, field] -> phi1, xi1 (BF16, zero
-//      outside the cloth), K-major core-matrix layout;
-//   3. layer 2: per chunk and tap two MMAs of K = 16 over the shifted
-//      layer-1 buffers.  The position field multiplies by
-//      [P.W2 | WL_tap.W2] (N = 64): it yields t = P phi (the pre-activation
-//      of s) and the 27 partial sums q_tap,co = sum_c WL[co][c][tap] phi_c
-//      directly, since phi enters Eq. 7 only linearly through P and WL; the
-//      velocity field multiplies by W2 (N = 32) -> xi.  Accumulators are
-//      double-buffered in tensor memory so chunk c+1 runs during the
-//      epilogue of chunk c;
-//   4. epilogue per layer-2 node: s = tanh(t), N + D = WN s + WD (xi . s),
-//      q kept in smem (zero outside the cloth: WL's zero padding);
-//   5. per output node: L = bL + sum_tap q_tap at the tap's neighbour,
+// The trunk W2 (*) (W1 (*) z) is linear and bias-free, and its output phi
+// enters Eq. 7 only through P (the nonlinear branches) and WL (the linear
+// branch).  Away from the cloth's edge the two 3x3 convolutions are one
+// 5x5 convolution with the composite kernel C_c = sum_{a+b=c} W2_a W1_b,
+// so the kernel evaluates per node, in one implicit GEMM,
+//   t = P C (*) u   (the pre-activation of s),
+//   q_tap = WL_tap C (*) u   (27 partial sums of the linear branch),
+//   xi = C (*) v   (the velocity features),
+// an MMA of N = 96 output columns per 128 nodes.  The layers' zero padding
+// makes the composite differ from the layered trunk only on the cloth's
+// outermost ring of nodes: there the terms through the layer-1 positions
+// outside the cloth are removed again (a 5-tap correction per edge the node
+// lies on, with a single-tap add-back where two edges meet), in FP32 from
+// the same BF16 inputs, so every node gets the layered result.
+//
+// One CTA (16 worker warps + 1 warp that issues the MMAs) per SM loops over
+// tiles of R x WO output nodes.  Every region of a tile is stored at the
+// pitch PT = WO + 6, so node (ry, rx) of a region has the linear index
+// ry * PT + rx, an M = 128 MMA covers 128 consecutive linear indices ("a
+// chunk"), and a 5x5 tap (cy, cx) is the same buffer shifted by
+// cy * PT + cx rows — a descriptor offset, never a copy.  Per tile:
+//   1. stage u, v of the (R+6)-row input region as BF16 (in_scale u,
+//      in_scale v, 0, 0 per node; zero outside the cloth) into one of two
+//      input buffers, and the raw FP32 u, v of the output nodes and their
+//      1-node halo into one of two FP32 tile buffers;
+//   2. per chunk of the (R+2)-row cell region, 13 MMAs of K = 16, each
+//      pairing two of the 25 taps (the second core-matrix column of K sits
+//      LBO = the taps' row distance further), into one of two tensor-memory
+//      accumulators (chunk c+1 runs during the epilogue of chunk c);
+//   3. epilogue per cell-region node: the edge corrections (computed per
+//      tile from the staged input, before its first epilogue), s = tanh(t),
+//      N + D = WN s + WD (xi . s); q kept in shared memory (zero outside the
+//      cloth: WL's zero padding);
+//   4. per output node: L = bL + sum_tap q_tap at the tap's neighbour,
 //      a = out_scale (L + N + D); then (step mode) v <- C(v + dt (a + f_p /
 //      m)), u <- u + dt v, sphere contact, store.
-// Tiles are pipelined: the input of tile t+1 is staged (into the other FP32
-// tile buffer) while the layer-2 MMAs of tile t run, and the final pass of
-// tile t runs while the layer-1 MMAs of tile t+1 do.
-// Every wait on the tensor cores is bounded; a timeout sets a status bit
-// and the kernel returns after releasing its tensor memory.
+// Tiles are pipelined: the input of tile t+1 is staged while the MMAs of
+// tile t run, and the first two chunks of tile t+1 run during the final
+// pass of tile t.  Every wait on the tensor cores is bounded; a timeout
+// sets a status bit and the kernel returns after releasing its tensor
+// memory.
 #include <cuda_bf16.h>
 
 #include "net_internal.cuh"
@@ -40,66 +51,66 @@
 namespace cloth {
 namespace {
 
-constexpr int R = 12, WO = 28, PT = WO + 6;   // output rows, output columns, region pitch
-constexpr int N0 = (R + 6) * PT;                // input-region nodes of a tile
-constexpr int N1 = (R + 4) * PT;                // layer-1 region
-constexpr int N2 = (R + 2) * PT;                // layer-2 region
-constexpr int C1 = (N1 + 127) / 128;            // layer-1 chunks
-constexpr int C2 = (N2 + 127) / 128;            // layer-2 chunks
-constexpr int N1BUF = (C2 * 128 + 2 * PT + 2 + 15) / 16 * 16;   // layer-1 rows layer 2 reads
-constexpr int N0BUF = (C1 * 128 + 2 * PT + 3 + 15) / 16 * 16;   // input rows layer 1 reads
-constexpr int NWORK = 256;                       // 8 worker warps; warps w and w + 4 share TMEM lanes
+constexpr int R = 14, WO = 26, PT = WO + 6;   // output rows, output columns, region pitch
+constexpr int N0 = (R + 6) * PT;                // input-region nodes of a tile (origin y0 - 3, x0 - 3)
+constexpr int N2 = (R + 2) * PT;                // cell region (origin y0 - 1, x0 - 1)
+constexpr int C2 = (N2 + 127) / 128;            // chunks of the cell region
+constexpr int N0BUF = (C2 * 128 + 4 * PT + 4 + 1 + 15) / 16 * 16;   // input rows the MMAs read
+constexpr int NWORK = 512;                       // 16 worker warps; warps w, w + 4, w + 8, w + 12 share TMEM lanes
 constexpr int NTH = NWORK + 32;                  // + 1 warp that issues the MMAs
+constexpr int kNC = 96;                          // MMA N: t [0, 32), q [32, 59), 0 [59, 64), xi [64, 96)
+constexpr int kPairs = 13;                       // 25 taps in K = 16 pairs (the last pair's second tap is 0)
 constexpr uint32_t kWaitLimit = 1u << 24;
-static_assert(N1BUF >= N1 && N0BUF >= N0, "buffers");
+static_assert(N0BUF >= N0 && N0BUF >= C2 * 128 + 4 * PT + 4 + 1, "input buffer");
 
-// Layer-1 tap pairs: MMA p covers taps kPairA[p] and kPairB[p] (-1: none).
-__host__ __device__ constexpr int pair_a(int p) { return 2 * p; }
-__host__ __device__ constexpr int pair_b(int p) { return p < 4 ? 2 * p + 1 : -1; }
-__host__ __device__ constexpr int tap_off(int t) { return (t / 3) * PT + t % 3; }
+// composite tap c = 5 cy + cx reads the input-region row j2 + cy * PT + cx
+// of cell-region node j2
+__host__ __device__ constexpr int ctap_off(int c) { return (c / 5) * PT + c % 5; }
 
-// packed BF16 weights: B1 [pair 5][khalf 2][64][8] (khalf = the pair's
-// first / second tap; n < 32 -> phi1 from input channels 0..2 (u),
-// n >= 32 -> xi1 from channels 3..5 (v)), B2p [tap][plane][64][8],
-// B2x [tap][plane][32][8] (plane = 8 input channels)
-constexpr int kB1 = 5 * 2 * 64 * 16, kB2p = 9 * 4 * 64 * 16, kB2x = 9 * 4 * 32 * 16;
-constexpr int kPack = kB1 + kB2p + kB2x;
+// Packed operands (bytes): BF16 B [pair 13][khalf 2][96][8] (khalf = the
+// pair's first / second tap, 8 = the input slots u0 u1 u2 v0 v1 v2 0 0);
+// FP32 edge corrections KE [edge 4: x = 0, x = W-1, y = 0, y = H-1][tap 5]
+// [channel 3][96] and corner add-backs KC [corner 4][channel 3][96], where
+// output columns below 64 take u's channels and the others v's.
+constexpr int kBc = kPairs * 2 * kNC * 16;
+constexpr int kKE = 4 * 5 * 3 * kNC, kKC = 4 * 3 * kNC;   // floats
+constexpr int kPack = kBc + (kKE + kKC) * 4;
+static_assert(kPack % 16 == 0, "pack");
 
 // FP32 u, v of the output nodes and their 1-node halo, for the update
 constexpr int UH = R + 2, UW = WO + 2;
-// q is kept for the valid layer-2 positions only: (R+2) x (WO+2), one plane
-// per value
+// q is kept for the valid cell-region positions only: (R+2) x (WO+2), one
+// plane per value
 constexpr int NQ = (R + 2) * (WO + 2);
 
 // shared memory map (bytes)
-constexpr int oB1 = 0, oB2p = oB1 + kB1, oB2x = oB2p + kB2p;
-constexpr int oIn = oB2x + kB2x;                    // input [N0BUF][8] bf16: in_scale (u, v), 0, 0
-constexpr int oL1p = oIn + N0BUF * 16;              // phi1 [plane][N1BUF][8] bf16
-constexpr int oL1x = oL1p + 4 * N1BUF * 16;         // xi1
-constexpr int oQ = oL1x + 4 * N1BUF * 16;           // q [27][NQ] float
+constexpr int oBc = 0;
+constexpr int oIn = oBc + kBc;                      // input [2 tiles][N0BUF][8] bf16
+constexpr int oKE = oIn + 2 * N0BUF * 16;           // KE, KC (floats)
+constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);  // edge nodes of a cell region: x = 0, x = W-1, y = 0, y = H-1
+constexpr int oCorr = oKE + (kKE + kKC) * 4;        // the edge nodes' corrections [kSlots][96] float
+constexpr int oQ = oCorr + kSlots * kNC * 4;        // q [27][NQ] float
 constexpr int kUFloats = 6 * UH * UW;
 constexpr int oU = oQ + NQ * 27 * 4;                // u, v [2 tiles][6][UH][UW] float
-constexpr int oND = oU + 2 * kUFloats * 4;          // N + D [R * WO][3] float (both channel halves added)
-constexpr int oPar = oND + R * WO * 3 * 4;          // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
+constexpr int oND = oU + 2 * kUFloats * 4;          // N + D [4 channel groups][R * WO][3] float
+constexpr int oPar = oND + 4 * R * WO * 3 * 4;         // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
 constexpr int oDesc = oPar + (256 + 16) * 4;        // the two tiles' cloth descriptors
 constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
-constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers: layer 1 [C1], layer 2 [2]; TMEM address
-constexpr int kNumBars = C1 + 2;
+constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers of the two accumulators; TMEM address
+constexpr int kNumBars = 2;
 constexpr int oTmemSlot = oBar + 8 * kNumBars;
 constexpr int kSmem = oTmemSlot + 16;
 static_assert(kSmem <= 232448, "shared memory");
-static_assert(oIn % 16 == 0 && oL1p % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 && oND % 16 == 0 &&
+static_assert(oIn % 16 == 0 && oKE % 16 == 0 && oCorr % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 && oND % 16 == 0 &&
                   oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
               "alignment");
 
-// TMEM columns: layer-1 chunk c at [64 c, +64); layer-2 buffer b at
-// [kL2Col + 96 b, +96)
-constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kL2Col = 64 * C1;
-static_assert(kL2Col + 2 * 96 <= kTmemCols, "tensor memory columns");
+// TMEM columns: accumulator b at [96 b, +96)
+constexpr uint32_t kTmemCols = 256;
+static_assert(2 * kNC <= (int)kTmemCols, "tensor memory columns");
 
 struct TcArgs {
-    const uint4* wpack;   // packed BF16 weights (kPack bytes)
+    const uint4* wpack;   // packed operands (kPack bytes)
     const float* w;       // FP32 blob
     int32_t* status;
     // step mode: tiles (cloth, y0, x0, -) over the context's cloths
@@ -125,19 +136,18 @@ __device__ __forceinline__ uint4 pack8(const float* v)
 {
     return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
+__device__ __forceinline__ float bf_lo(uint32_t x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t x) { return __uint_as_float(x & 0xffff0000u); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
 {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <bool STEP>
@@ -147,8 +157,11 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = tid < NWORK, issuer = tid == NWORK;
     const int quarter = warp & 3;                 // TMEM lanes [32 quarter, +32) of this warp
-    const int half = (warp >> 2) & 1;             // worker warps 0-3 and 4-7 split the columns
+    const int cg = (warp >> 2) & 3;               // channel group: columns [8 cg, +8) of t, q and xi
     const uint32_t sbase = tc::smem_u32(sm);
+    const float* sKE = reinterpret_cast<const float*>(sm + oKE);
+    const float* sKC = sKE + kKE;
+    float* sCorr = reinterpret_cast<float*>(sm + oCorr);
     float* sQ = reinterpret_cast<float*>(sm + oQ);
     float* sU = reinterpret_cast<float*>(sm + oU);
     float* sND = reinterpret_cast<float*>(sm + oND);
@@ -160,11 +173,12 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
     uint8_t* sPin = sm + oPin;
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
-    auto bar1 = [&](int c) { return sbase + oBar + 8u * (uint32_t)c; };
-    auto bar2 = [&](int b) { return sbase + oBar + 8u * (uint32_t)(C1 + b); };
+    auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
+    auto sIn = [&](int buf) { return reinterpret_cast<uint4*>(sm + oIn) + buf * N0BUF; };
 
-    // ---- one-time set-up: weights, barriers, tensor memory
-    for (int e = tid; e < kPack / 16; e += NTH) reinterpret_cast<uint4*>(sm)[e] = A.wpack[e];
+    // ---- one-time set-up: operands, barriers, tensor memory
+    for (int e = tid; e < kBc / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBc)[e] = A.wpack[e];
+    for (int e = tid; e < (kKE + kKC) / 4; e += NTH) reinterpret_cast<uint4*>(sm + oKE)[e] = A.wpack[kBc / 16 + e];
     for (int e = tid; e < 32 * 8; e += NTH) {
         const int c = e >> 3, j = e & 7;
         sPar[e] = j < 3 ? A.w[kOffWN + j * kC + c] : (j < 6 ? A.w[kOffWD + (j - 3) * kC + c] : 0.f);
@@ -174,11 +188,11 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         sOut[tid] = A.w[kOffOuts + tid];
     }
     if (tid < 6) sIns[tid] = A.w[kOffIns + tid];
-    for (int e = tid; e < R * WO * 3; e += NTH) sND[e] = 0.f;
-    // input rows N0 .. N0BUF are read only by junk layer-1 positions; keep them zero
-    for (int e = tid; e < N0BUF - N0; e += NTH) reinterpret_cast<uint4*>(sm + oIn)[N0 + e] = make_uint4(0, 0, 0, 0);
+    // input rows N0 .. N0BUF are read only by junk cell-region positions; keep them zero
+    for (int e = tid; e < 2 * (N0BUF - N0); e += NTH)
+        sIn(e / (N0BUF - N0))[N0 + e % (N0BUF - N0)] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int b = 0; b < kNumBars; ++b) tc::mbar_init(sbase + oBar + 8u * (uint32_t)b, 1);
+        for (int b = 0; b < kNumBars; ++b) tc::mbar_init(bar(b), 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -190,47 +204,29 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     tc::fence_after();
     const uint32_t tmem = *sTmem;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    uint32_t ph1 = 0, ph2[2] = {0, 0};
+    uint32_t ph[2] = {0, 0};
     bool timed_out = false;
     const int n_tiles = STEP ? A.n_tiles : A.N * A.tiles_y * A.tiles_x;
 
     // Descriptors of the issuer: a descriptor plus (byte offset >> 4) is the
     // same matrix shifted by that offset (the start-address field is the low
-    // 14 bits and every operand lies below 256 KB).
-    const uint64_t dIn0 = tc::sdesc(sbase + oIn, 16, 128), dIn1 = tc::sdesc(sbase + oIn, 512, 128);
-    const uint64_t dB1 = tc::sdesc(sbase + oB1, 64 * 16, 128);
-    const uint64_t dL1p = tc::sdesc(sbase + oL1p, N1BUF * 16, 128), dL1x = tc::sdesc(sbase + oL1x, N1BUF * 16, 128);
-    const uint64_t dB2p = tc::sdesc(sbase + oB2p, 64 * 16, 128), dB2x = tc::sdesc(sbase + oB2x, 32 * 16, 128);
-
-    auto issue_layer1 = [&]() {   // all chunks at once, chunk c into columns [64 c, +64)
+    // 14 bits and every operand lies below 256 KB).  Taps in one row pair at
+    // LBO = 16 bytes, a row's last tap with the next row's first at LBO =
+    // (PT - 4) rows.
+    const uint64_t dBc = tc::sdesc(sbase + oBc, kNC * 16, 128);
+    auto issue_chunk = [&](int c2, int ib) {   // chunk c2 of input buffer ib into accumulator c2 & 1
         tc::fence_after();
-        for (int c1 = 0; c1 < C1; ++c1) {
+        const uint32_t d = tmem + (uint32_t)kNC * (uint32_t)(c2 & 1);
+        const uint32_t in = sbase + oIn + (uint32_t)(ib * N0BUF * 16);
+        const uint64_t dA = tc::sdesc(in, 16, 128), dAw = tc::sdesc(in, (PT - 4) * 16, 128);
 #pragma unroll
-            for (int p = 0; p < 5; ++p) {
-                const int ta = pair_a(p), tb = pair_b(p);
-                const uint64_t base = (tb >= 0 && tap_off(tb) - tap_off(ta) != 1) ? dIn1 : dIn0;
-                const uint64_t ad = base + (uint64_t)(c1 * 128 + tap_off(ta));
-                const uint64_t bd = dB1 + (uint64_t)(p * 2 * 64);
-                tc::mma_bf16(tmem + 64u * (uint32_t)c1, ad, bd, tc::idesc_bf16(128, 64), p > 0);
-            }
-            tc::mma_commit(bar1(c1));
+        for (int p = 0; p < kPairs; ++p) {
+            const int ta = 2 * p;
+            const bool wrap = p < kPairs - 1 && ta % 5 == 4;
+            const uint64_t ad = (wrap ? dAw : dA) + (uint64_t)(c2 * 128 + ctap_off(ta));
+            tc::mma_bf16(d, ad, dBc + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), p > 0);
         }
-    };
-    auto issue_layer2 = [&](int c2) {   // chunk c2 into buffer c2 & 1
-        tc::fence_after();
-        const uint32_t d = tmem + kL2Col + 96u * (uint32_t)(c2 & 1);
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int row = c2 * 128 + tap_off(tap);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const bool acc = tap > 0 || h > 0;
-                const uint64_t ao = (uint64_t)(2 * h * N1BUF + row);
-                tc::mma_bf16(d, dL1p + ao, dB2p + (uint64_t)((tap * 4 + 2 * h) * 64), tc::idesc_bf16(128, 64), acc);
-                tc::mma_bf16(d + 64, dL1x + ao, dB2x + (uint64_t)((tap * 4 + 2 * h) * 32), tc::idesc_bf16(128, 32), acc);
-            }
-        }
-        tc::mma_commit(bar2(c2 & 1));
+        tc::mma_commit(bar(c2 & 1));
     };
 
     // ---- per-tile pieces
@@ -267,12 +263,13 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         return t;
     };
 
-    // 1. the input region as BF16: node (iy, ix) at iy * PT + ix holds
-    // (in_scale u, in_scale v, 0, 0), zero outside the grid; the raw u, v of
-    // the output nodes and their halo also go to FP32 tile buffer `buf`, and
-    // (step mode) the output nodes' pinned flags to sPin[buf].  Split into a
-    // load of input node j0 into registers and its store to shared memory,
-    // so the loads can be in flight while the thread waits for an MMA.
+    // 1. the input region as BF16: node (iy, ix) at iy * PT + ix of input
+    // buffer `buf` holds (in_scale u, in_scale v, 0, 0), zero outside the
+    // grid; the raw u, v of the output nodes and their halo also go to FP32
+    // tile buffer `buf`, and (step mode) the output nodes' pinned flags to
+    // sPin[buf].  Split into a load of input node j0 into registers and its
+    // store to shared memory, so the loads can be in flight while the thread
+    // waits for an MMA.
     struct Raw {
         float v[6];
         uint32_t pin;     // the node's pin-mask word; its bit is picked at the store
@@ -299,7 +296,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
         for (int c = 0; c < 6; ++c) v[c] = sIns[c] * rw.v[c];
         v[6] = v[7] = 0.f;
-        reinterpret_cast<uint4*>(sm + oIn)[j0] = pack8(v);
+        sIn(buf)[j0] = pack8(v);
         const int uy = iy - 2, ux = ix - 2;
         if (uy >= 0 && uy < UH && ux >= 0 && ux < UW) {
             float* sUb = sU + buf * kUFloats;
@@ -319,47 +316,70 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
     };
     constexpr int kStageParts = (N0 + NWORK - 1) / NWORK;   // input nodes per worker
-    static_assert(kStageParts <= C2, "one staging part per layer-2 chunk");
+    static_assert(kStageParts <= C2, "one staging part per chunk");
 
-    // 2. layer 1 (Eq. 6) store: each chunk's phi1 / xi1 as BF16 as it
-    // completes (workers; false on a timeout)
-    auto repack = [&](const Geo& g) {
-        auto put = [&](int c1, const float (&r)[32]) {
-            const int j1 = c1 * 128 + quarter * 32 + lane, ry1 = j1 / PT, rx1 = j1 % PT;
-            const int y = g.y0 - 2 + ry1, x = g.x0 - 2 + rx1;
-            const bool in = j1 < N1 && rx1 < WO + 4 && y >= 0 && y < g.H && x >= 0 && x < g.W;
-            if (j1 < N1BUF) {
-                uint4* dstb = reinterpret_cast<uint4*>(sm + (half ? oL1x : oL1p));
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float a8[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) a8[e] = in ? r[8 * p + e] : 0.f;
-                    dstb[p * N1BUF + j1] = pack8(a8);
-                }
-            }
+    // The edge terms of a tile, from its staged input (workers, once per
+    // tile, spread over all of them): for each cell-region node on an edge
+    // of the cloth and each of the 96 output columns, the 5 taps of that
+    // edge's correction along the edge, and for a node on an x edge that is
+    // also on a y edge the add-back of the term both corrections removed.
+    // Slots: x = 0 by cell row, x = W-1 by cell row, y = 0 by cell column,
+    // y = H-1 by cell column.
+    auto edge_prep = [&](const Geo& g, const uint4* in) {
+        constexpr int kGroups = NWORK / kNC;   // node groups: thread -> (column n, group gi)
+        if (tid >= kGroups * kNC) return;
+        const int n = tid % kNC, gi = tid / kNC;
+        if (n >= 59 && n < 64) return;   // padding columns: never read
+        const int rxE = g.W - g.x0, ryN = g.H - g.y0;   // cell column of x = W-1, cell row of y = H-1
+        const bool has[4] = {g.x0 == 0, rxE >= 0 && rxE < WO + 2, g.y0 == 0, ryN >= 0 && ryN < R + 2};
+        constexpr int base[4] = {0, R + 2, 2 * (R + 2), 2 * (R + 2) + WO + 2};
+        // the three input slots of column n: u (n < 64) or v
+        auto z3 = [&](int row, float (&z)[3]) {
+            const uint4 r = in[row];
+            if (n < 64) { z[0] = bf_lo(r.x); z[1] = bf_hi(r.x); z[2] = bf_lo(r.y); }
+            else { z[0] = bf_hi(r.y); z[1] = bf_lo(r.z); z[2] = bf_hi(r.z); }
         };
-        // two chunks' tensor-memory loads in flight at a time
-        for (int c1 = 0; c1 < C1; c1 += 2) {
-            const bool two = c1 + 1 < C1;
-            if (!tc::mbar_wait(bar1(c1), ph1, kWaitLimit)) return false;
-            if (two && !tc::mbar_wait(bar1(c1 + 1), ph1, kWaitLimit)) return false;
-            tc::fence_after();
-            float r0[32], r1[32];
-            tc::tmem_ld32(lane_base + 64u * (uint32_t)c1 + 32u * (uint32_t)half, r0);
-            if (two) tc::tmem_ld32(lane_base + 64u * (uint32_t)(c1 + 1) + 32u * (uint32_t)half, r1);
-            tc::tmem_wait_ld();
-            put(c1, r0);
-            if (two) put(c1 + 1, r1);
+#pragma unroll 1
+        for (int ed = 0; ed < 4; ++ed) {
+            if (!has[ed]) continue;
+            float k[15], kc[2][3];
+#pragma unroll
+            for (int j = 0; j < 15; ++j) k[j] = sKE[(ed * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n];
+#pragma unroll
+            for (int yb = 0; yb < 2; ++yb)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) kc[yb][ch] = ed < 2 ? sKC[(2 * yb + ed) * 3 * kNC + ch * kNC + n] : 0.f;
+            const int len = ed < 2 ? R + 2 : WO + 2;
+#pragma unroll 1
+            for (int i = gi; i < len; i += kGroups) {
+                const int ry2 = ed < 2 ? i : (ed == 2 ? 1 : ryN), rx2 = ed < 2 ? (ed == 0 ? 1 : rxE) : i;
+                const int y = g.y0 - 1 + ry2, x = g.x0 - 1 + rx2;
+                if (y < 0 || y >= g.H || x < 0 || x >= g.W) continue;   // not a node of the cloth
+                const int j2 = ry2 * PT + rx2;
+                float acc = 0.f;
+#pragma unroll
+                for (int s5 = 0; s5 < 5; ++s5) {   // x edges: taps along y; y edges: along x
+                    float z[3];
+                    z3(j2 + (ed < 2 ? s5 * PT + 2 : 2 * PT + s5), z);
+                    acc = fmaf(k[3 * s5], z[0], fmaf(k[3 * s5 + 1], z[1], fmaf(k[3 * s5 + 2], z[2], acc)));
+                }
+                if (ed < 2 && (y == 0 || y == g.H - 1)) {   // corners (ay, ax): k4 = 2 (ay / 2) + ax / 2
+                    float z[3];
+                    z3(j2 + 2 * PT + 2, z);
+#pragma unroll
+                    for (int yb = 0; yb < 2; ++yb)
+                        if (yb ? y == g.H - 1 : y == 0)
+                            acc = fmaf(kc[yb][0], z[0], fmaf(kc[yb][1], z[1], fmaf(kc[yb][2], z[2], acc)));
+                }
+                sCorr[(base[ed] + i) * kNC + n] = acc;
+            }
         }
-        tc::fence_async_smem();
-        tc::fence_before();
-        return true;
     };
 
-    // 4. epilogue of layer-2 chunk c2 (TMEM buffer b): s = tanh(t), N + D
-    // over the channel half [16 half, +16) added into sND; q, the WL
-    // partial sums, into sQ (zero outside the cloth: WL's zero padding)
+    // 3. epilogue of chunk c2 (accumulator b): the edge corrections,
+    // s = tanh(t), and N + D over the channel group [8 cg, +8) into its own
+    // plane of sND; q, the WL partial sums, into sQ (zero outside the cloth:
+    // WL's zero padding)
     auto epilogue = [&](const Geo& g, int c2, int b) {
         tc::fence_after();
         const int j2 = c2 * 128 + quarter * 32 + lane;
@@ -368,45 +388,60 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         const bool valid = j2 < N2 && rx2 < WO + 2 && y >= 0 && y < g.H && x >= 0 && x < g.W;
         const int oy = ry2 - 1, ox = rx2 - 1;
         const bool out_node = valid && oy >= 0 && oy < R && ox >= 0 && ox < WO;
-        const uint32_t col = lane_base + kL2Col + 96u * (uint32_t)b;
-        float t[16], xi[16], q[16];
-        tmem_ld16(col + 16 * half, t);
-        tmem_ld16(col + 64 + 16 * half, xi);
-        tmem_ld16(col + 32 + 16 * half, q);   // q_0..15 (half 0) or q_16..26 and padding (half 1)
+        const uint32_t col = lane_base + (uint32_t)kNC * (uint32_t)b + 8u * (uint32_t)cg;
+        float t[8], xi[8], q[8];
+        tmem_ld8(col, t);
+        tmem_ld8(col + 64, xi);
+        tmem_ld8(col + 32, q);   // q_{8 cg} .. q_{8 cg + 7} (group 3: q_24..26 and padding)
         tc::tmem_wait_ld();
-        if (j2 < N2 && rx2 < WO + 2) {
-            float* qr = sQ + 16 * half * NQ + ry2 * (WO + 2) + rx2;
+        if (valid && (x == 0 || y == 0 || x == g.W - 1 || y == g.H - 1)) {
+            auto add = [&](int slot) {
+                const float4* c = reinterpret_cast<const float4*>(sCorr + slot * kNC + 8 * cg);
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < 11 || half == 0) qr[k * NQ] = valid ? q[k] : 0.f;
+                for (int j = 0; j < 2; ++j) {
+                    const float4 a = c[j], e = c[8 + j], d = c[16 + j];
+                    t[4 * j] += a.x; t[4 * j + 1] += a.y; t[4 * j + 2] += a.z; t[4 * j + 3] += a.w;
+                    q[4 * j] += e.x; q[4 * j + 1] += e.y; q[4 * j + 2] += e.z; q[4 * j + 3] += e.w;
+                    xi[4 * j] += d.x; xi[4 * j + 1] += d.y; xi[4 * j + 2] += d.z; xi[4 * j + 3] += d.w;
+                }
+            };
+            if (x == 0) add(ry2);
+            if (x == g.W - 1) add(R + 2 + ry2);
+            if (y == 0) add(2 * (R + 2) + rx2);
+            if (y == g.H - 1) add(2 * (R + 2) + WO + 2 + rx2);
+        }
+        if (j2 < N2 && rx2 < WO + 2) {
+            float* qr = sQ + 8 * cg * NQ + ry2 * (WO + 2) + rx2;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < 3 || cg < 3) qr[k * NQ] = valid ? q[k] : 0.f;
         }
         if (out_node) {
             float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < 8; ++c) {
                 const float sv = tc::tanh_approx(t[c]);
                 const float xs = xi[c] * sv;
-                const float4 w0 = sWND[2 * (16 * half + c)], w1 = sWND[2 * (16 * half + c) + 1];
+                const float4 w0 = sWND[2 * (8 * cg + c)], w1 = sWND[2 * (8 * cg + c) + 1];
                 nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
                 nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
                 nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
             }
-            // the two halves' sums land on zero: x + y == y + x, so the
-            // result does not depend on their order
-            float* o = sND + (oy * WO + ox) * 3;
-            atomicAdd(o + 0, nd0);
-            atomicAdd(o + 1, nd1);
-            atomicAdd(o + 2, nd2);
+            float* o = sND + (cg * R * WO + oy * WO + ox) * 3;
+            o[0] = nd0;
+            o[1] = nd1;
+            o[2] = nd2;
         }
         tc::fence_before();
     };
 
-    // 5. per output node: L, a, and (step mode) the update; sND is zeroed
-    // for the next tile (workers)
+    // 4. per output node: L, a (the channel groups' N + D added in a fixed
+    // order), and (step mode) the update (workers)
     auto final_pass = [&](const Geo& g, int buf) {
         const float* sUb = sU + buf * kUFloats;
         for (int o = tid; o < R * WO; o += NWORK) {
             const int oy = o / WO, ox = o % WO, y = g.y0 + oy, x = g.x0 + ox;
+            if (y >= g.H || x >= g.W) continue;
             float acc[3];
 #pragma unroll
             for (int co = 0; co < 3; ++co) {
@@ -414,10 +449,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap)
                     L += sQ[(tap * 3 + co) * NQ + (oy + tap / 3) * (WO + 2) + ox + tap % 3];
-                acc[co] = sOut[co] * (L + sND[o * 3 + co]);
-                sND[o * 3 + co] = 0.f;
+                const float nd = ((sND[o * 3 + co] + sND[(R * WO + o) * 3 + co]) + sND[(2 * R * WO + o) * 3 + co]) +
+                                 sND[(3 * R * WO + o) * 3 + co];
+                acc[co] = sOut[co] * (L + nd);
             }
-            if (y >= g.H || x >= g.W) continue;
             if constexpr (!STEP) {
 #pragma unroll
                 for (int co = 0; co < 3; ++co) A.a[(((int64_t)g.n * 3 + co) * g.H + y) * g.W + x] = acc[co];
@@ -466,9 +501,9 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
     };
 
-    // ---- the pipeline.  Prologue: stage and run layer 1 of the first tile.
-    // The geometry of the tile after the current one is known one iteration
-    // ahead, so its loads have landed when its input is fetched.
+    // ---- the pipeline.  Prologue: stage the first tile and issue its first
+    // two chunks.  The geometry of the tile after the current one is known
+    // one iteration ahead, so its loads have landed when its input is fetched.
     int tile = skip((int)blockIdx.x);
     int buf = 0;
     Geo g{}, gn{};
@@ -482,24 +517,20 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             tc::fence_async_smem();
         }
         __syncthreads();
-        if (issuer) issue_layer1();
-        bool ok = true;
-        if (worker) ok = repack(g);
-        ph1 ^= 1u;
-        if (__syncthreads_or(!ok)) timed_out = true;
+        if (issuer) {
+            issue_chunk(0, 0);
+            if (C2 > 1) issue_chunk(1, 0);
+        }
+        if (worker) edge_prep(g, sIn(0));
+        __syncthreads();
     }
     while (tile < n_tiles && !timed_out) {
         const bool has_next = tn < n_tiles;
 
-        // 3-4. layer 2 of this tile as implicit GEMM, double-buffered in TMEM
-        // (chunk c+1 runs while the workers read chunk c).  Each worker loads
-        // its input nodes of the next tile up front and stores one after each
-        // of the first chunks' epilogues, so the loads have the MMAs' time to
-        // land.
-        if (issuer) {
-            issue_layer2(0);
-            if (C2 > 1) issue_layer2(1);
-        }
+        // 2-3. the chunks of this tile, double-buffered in TMEM (chunk c+1
+        // runs while the workers read chunk c).  Each worker loads its input
+        // nodes of the next tile up front and stores one after each of the
+        // first chunks' epilogues, so the loads have the MMAs' time to land.
         Raw rw[kStageParts];
         if (worker && has_next) {
 #pragma unroll
@@ -519,30 +550,31 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             const int b = c2 & 1;
             bool ok = true;
             if (worker) {
-                ok = tc::mbar_wait(bar2(b), ph2[b], kWaitLimit);
+                ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
                 if (ok) epilogue(g, c2, b);
 #pragma unroll
                 for (int k = 0; k < kStageParts; ++k)   // register-indexed: k is a constant here
                     if (k == c2 && has_next && tid + k * NWORK < N0) stage_store(gn, buf ^ 1, tid + k * NWORK, rw[k]);
                 if (STEP && c2 == 0 && has_next && tid < kDescV) reinterpret_cast<uint4*>(sD + (buf ^ 1))[tid] = dv;
             }
-            ph2[b] ^= 1u;
+            ph[b] ^= 1u;
             if (__syncthreads_or(!ok)) { timed_out = true; break; }
-            if (issuer && c2 + 2 < C2) issue_layer2(c2 + 2);   // buffer b is free again
+            if (issuer && c2 + 2 < C2) issue_chunk(c2 + 2, buf);   // accumulator b is free again
         }
         if (timed_out) break;
 
-        // layer 1 of the next tile runs during this tile's final pass
+        // the next tile's first two chunks run during this tile's final pass
         if (worker) tc::fence_async_smem();   // the staged input, for the tensor cores
         __syncthreads();
-        if (issuer && has_next) issue_layer1();
-        bool ok = true;
+        if (issuer && has_next) {
+            issue_chunk(0, buf ^ 1);
+            if (C2 > 1) issue_chunk(1, buf ^ 1);
+        }
         if (worker) {
             final_pass(g, buf);
-            if (has_next) ok = repack(gn);
+            if (has_next) edge_prep(gn, sIn(buf ^ 1));   // this tile's epilogues are done
         }
-        if (has_next) ph1 ^= 1u;
-        if (__syncthreads_or(!ok)) { timed_out = true; break; }
+        __syncthreads();
         tile = tn;
         tn = tnn;
         g = gn;
@@ -555,46 +587,88 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     if (timed_out) {
         if (tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
         for (int k = 0; k < 2; ++k)
-            for (int b = 0; b < kNumBars; ++b)
-                tc::mbar_wait(sbase + oBar + 8u * (uint32_t)b, (uint32_t)k, 1u << 18);
+            for (int b = 0; b < kNumBars; ++b) tc::mbar_wait(bar(b), (uint32_t)k, 1u << 18);
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-// Packed BF16 B operands from the FP32 blob: one thread per row of 8 K-values.
-__global__ void pack_bf16_kernel(const float* __restrict__ w, uint4* __restrict__ out)
+// The composite operands from the FP32 blob, one thread per value.
+// G_n is the output map of column n: P's row n (n < 32), WL's tap tl and
+// output co (n = 32 + 3 tl + co < 59) or the identity (n >= 64, xi); the
+// value for a set of (a, b) tap pairs and input channel i is
+//   sum_{(a, b)} G_n W2_a W1_b[:, i].
+__device__ float composite(const float* __restrict__ w, int n, int i, int a, int b)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    constexpr int R1 = 5 * 2 * 64, R2p = 9 * 4 * 64, R2x = 9 * 4 * 32;
-    if (r >= R1 + R2p + R2x) return;
-    float v[8];
-    if (r < R1) {   // W1: tap pair p, the pair's first (kh 0) or second tap; n < 32 phi1 from
-                    // u (channels 0..2 of a node), n >= 32 xi1 from v (channels 3..5)
-        const int p = r / 128, kh = (r / 64) % 2, n = r % 64;
-        const int tap = kh == 0 ? pair_a(p) : pair_b(p);
-        const int f = n / 32, co = n % 32;
-        for (int e = 0; e < 8; ++e)
-            v[e] = (tap >= 0 && e / 3 == f && e < 6) ? w[kOffW1 + (co * 6 + e) * 9 + tap] : 0.f;
-    } else if (r < R1 + R2p) {   // [P.W2 | WL_tap.W2] for the position field
-        const int q = r - R1, tap = q / 256, p = (q / 64) % 4, n = q % 64;
-        for (int e = 0; e < 8; ++e) {
-            const int ci = 8 * p + e;
-            float s = 0.f;
-            if (n < 32) {
-                for (int c = 0; c < kC; ++c) s += w[kOffP + n * kC + c] * w[kOffW2 + (c * kC + ci) * 9 + tap];
-            } else if (n < 32 + 27) {
-                const int m = n - 32, tl = m / 3, co = m % 3;
-                for (int c = 0; c < kC; ++c) s += w[kOffWL + (co * kC + c) * 9 + tl] * w[kOffW2 + (c * kC + ci) * 9 + tap];
-            }
-            v[e] = s;
-        }
-    } else {   // W2 for the velocity field
-        const int q = r - R1 - R2p, tap = q / 128, p = (q / 32) % 4, n = q % 32;
-        for (int e = 0; e < 8; ++e) v[e] = w[kOffW2 + (n * kC + 8 * p + e) * 9 + tap];
+    float s = 0.f;
+    if (n >= 64) {
+        const int k = n - 64;
+        for (int j = 0; j < kC; ++j) s = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], s);
+        return s;
     }
-    out[r] = pack8(v);
+    for (int k = 0; k < kC; ++k) {
+        const float gk = n < 32 ? w[kOffP + n * kC + k] : w[kOffWL + ((n - 32) % 3 * kC + k) * 9 + (n - 32) / 3];
+        float d = 0.f;
+        for (int j = 0; j < kC; ++j) d = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], d);
+        s = fmaf(gk, d, s);
+    }
+    return s;
+}
+
+__global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict__ out)
+{
+    constexpr int nB = kPairs * 2 * kNC * 8;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nB + kKE + kKC) return;
+    auto tap = [](int y, int x) { return 3 * y + x; };
+    if (r < nB) {   // B: tap pair p, the pair's first (kh 0) or second tap, column n, input slot e
+        const int e = r % 8, n = (r / 8) % kNC, kh = (r / (8 * kNC)) % 2, p = r / (16 * kNC);
+        const int c = 2 * p + kh, cy = c / 5, cx = c % 5;
+        float v = 0.f;
+        const bool u_col = n < 59 && e < 3, v_col = n >= 64 && e >= 3 && e < 6;
+        if (c < 25 && (u_col || v_col))
+            for (int ay = 0; ay < 3; ++ay)
+                for (int ax = 0; ax < 3; ++ax) {
+                    const int by = cy - ay, bx = cx - ax;
+                    if (by >= 0 && by < 3 && bx >= 0 && bx < 3) v += composite(w, n, e, tap(ay, ax), tap(by, bx));
+                }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        reinterpret_cast<__nv_bfloat16*>(out)[r] = h;
+        return;
+    }
+    float* fo = reinterpret_cast<float*>(out + kBc);
+    const int q = r - nB;
+    if (q < kKE) {   // edge ed, tap s along the edge, channel ch, column n
+        const int n = q % kNC, ch = (q / kNC) % 3, s = (q / (3 * kNC)) % 5, ed = q / (15 * kNC);
+        float v = 0.f;
+        if (n < 59 || n >= 64) {
+            const int i = n < 64 ? ch : 3 + ch;
+            // x = 0: the layer-1 column x - 1 (a_x = 0) is outside and only
+            // b_x = 2 reaches back into the cloth; x = W - 1: a_x = 2, b_x = 0;
+            // y = 0: a_y = 0, b_y = 2; y = H - 1: a_y = 2, b_y = 0
+            for (int k = 0; k < 3; ++k) {
+                const int m = s - k;
+                if (m < 0 || m > 2) continue;
+                int a, b;
+                if (ed == 0) { a = tap(k, 0); b = tap(m, 2); }
+                else if (ed == 1) { a = tap(k, 2); b = tap(m, 0); }
+                else if (ed == 2) { a = tap(0, k); b = tap(2, m); }
+                else { a = tap(2, k); b = tap(0, m); }
+                v -= composite(w, n, i, a, b);
+            }
+        }
+        fo[q] = v;
+        return;
+    }
+    const int q2 = q - kKE;   // corner k4 = (ay / 2) * 2 + ax / 2, channel ch, column n
+    const int n = q2 % kNC, ch = (q2 / kNC) % 3, k4 = q2 / (3 * kNC);
+    float v = 0.f;
+    if (n < 59 || n >= 64) {
+        const int ay = (k4 >> 1) * 2, ax = (k4 & 1) * 2;
+        v = composite(w, n, n < 64 ? ch : 3 + ch, tap(ay, ax), tap(2 - ay, 2 - ax));
+    }
+    fo[kKE + q2] = v;
 }
 
 }  // namespace
@@ -612,8 +686,8 @@ cudaError_t net_tc_init()
 
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 {
-    constexpr int rows = 5 * 2 * 64 + 9 * 4 * 64 + 9 * 4 * 32;
-    pack_bf16_kernel<<<(rows + 127) / 128, 128, 0, s>>>(w, static_cast<uint4*>(wpack));
+    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC;
+    pack_tc_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, static_cast<uint8_t*>(wpack));
     return cudaGetLastError();
 }
 
