@@ -362,7 +362,7 @@ int net_forward_static(const float* d_blob, const float* d_z, float* d_a, int32_
 void net_destroy(cloth_net* net);
 
 /* Device workspace cloth_step_net needs for this context and network
- * precision (per-step activations of every cloth). */
+ * precision (the list of output tiles of its fused step kernel). */
 int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* bytes);
 
 /* Advance every cloth `steps` network steps (Fig. 2): a = cell(u, v), then
@@ -391,8 +391,8 @@ typedef struct {
 /* Workspace of cloth_rollout_net (tile list and one scratch state). */
 int cloth_net_rollout_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* bytes);
 
-/* Network rollout under the options above.  Residual checks need a BF16
- * (tensor-core) network (CLOTH_EUNSUPPORTED otherwise). */
+/* Network rollout under the options above, for either precision: the
+ * network steps are the fused kernels of cloth_step_net. */
 int cloth_rollout_net(cloth_ctx* ctx, const cloth_net* net, const cloth_net_rollout_opts* opts, void* d_work,
                       size_t bytes, void* stream);
 

@@ -84,11 +84,6 @@ int cuda_fail(cudaError_t e)
 }
 
 // Cloths of one size, stepped by the network as one batch of images.
-struct NetGroup {
-    int H, W;
-    std::vector<int32_t> cloths;
-    size_t list_off;   // int32 offset of its cloth list in the step workspace
-};
 
 #define CK(expr)                                 \
     do {                                         \
@@ -119,8 +114,6 @@ struct cloth_ctx {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
     std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
     std::vector<int32_t> impl_blk;     // implicit step: first block of each cloth, then the total
-    std::vector<NetGroup> groups;      // network step: cloths grouped by size
-    int64_t group_max_nodes = 0;       // largest group's node count
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
     int lists_kind = -1;                   // which list it holds (network precision)
 
@@ -251,70 +244,58 @@ int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s
     return CLOTH_OK;
 }
 
-void make_groups(cloth_ctx* c)
-{
-    if (!c->groups.empty()) return;
-    std::map<std::pair<int, int>, int> idx;
-    size_t off = 0;
-    for (int b = 0; b < c->B; ++b) {
-        const auto key = std::make_pair(c->grids[b].rows, c->grids[b].cols);
-        auto it = idx.find(key);
-        if (it == idx.end()) {
-            it = idx.emplace(key, (int)c->groups.size()).first;
-            c->groups.push_back(NetGroup{key.first, key.second, {}, 0});
-        }
-        c->groups[it->second].cloths.push_back(b);
-    }
-    for (auto& g : c->groups) {
-        g.list_off = off;
-        off += g.cloths.size();
-        c->group_max_nodes = std::max<int64_t>(c->group_max_nodes, (int64_t)g.cloths.size() * g.H * g.W);
-    }
-}
-
-// FP32 network-step workspace: cloth lists, then T1, T2 (64 channels each)
-// and the acceleration (3 channels) of the largest group.
-struct StepWs {
-    size_t lists, t1, t2, a, total;
-};
-StepWs step_ws(const cloth_ctx* c)
-{
-    StepWs w{};
-    size_t off = 0;
-    w.lists = off; off = align_up(off + sizeof(int32_t) * c->B, kAlign);
-    w.t1 = off;    off = align_up(off + sizeof(float) * 64 * c->group_max_nodes, kAlign);
-    w.t2 = off;    off = align_up(off + sizeof(float) * 64 * c->group_max_nodes, kAlign);
-    w.a = off;     off = align_up(off + sizeof(float) * 3 * c->group_max_nodes, kAlign);
-    w.total = off;
-    return w;
-}
-
-// Tiles (cloth, y0, x0, -) of the fused tensor-core network step.
-std::vector<int4> tc_tiles(const cloth_ctx* c)
+// Tiles (cloth, y0, x0, -) of R x WO output nodes over every cloth.
+std::vector<int4> net_tiles(const cloth_ctx* c, int R, int WO)
 {
     std::vector<int4> t;
-    const int R = net_tc_tile_rows(), WO = net_tc_tile_cols();
     for (int b = 0; b < c->B; ++b)
         for (int y0 = 0; y0 < c->grids[b].rows; y0 += R)
             for (int x0 = 0; x0 < c->grids[b].cols; x0 += WO) t.push_back(make_int4(b, y0, x0, 0));
     return t;
 }
+// of the fused tensor-core (BF16) and CUDA-core (FP32) network steps
+std::vector<int4> tc_tiles(const cloth_ctx* c) { return net_tiles(c, net_tc_tile_rows(), net_tc_tile_cols()); }
+std::vector<int4> comp_tiles(const cloth_ctx* c) { return net_tiles(c, net_comp_tile_rows(), net_comp_tile_cols()); }
 
-int step_net_bf16(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, cudaStream_t s)
+// One fused network step over the tile list: the tensor-core kernel for a
+// BF16 network (one CTA per SM), the FP32 composite kernel otherwise (two
+// blocks per SM).  `mode` restricts it to the cloths in network mode.
+int launch_net_step(const cloth_ctx* c, const cloth_net* net, const int4* d_tiles, int n_tiles, const float* src,
+                    float* dst, const int32_t* mode, cudaStream_t s)
 {
-    const std::vector<int4> tiles = tc_tiles(c);
+    if (net->precision == CLOTH_NET_BF16)
+        CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, n_tiles, src, dst, c->d_pins(),
+                              c->d_status(), std::min(n_tiles, c->sm_count), s, mode));
+    else
+        CK(launch_net_comp_step(net->d_w(), net->d_comp(), net->d_edge(), c->d_desc(), d_tiles, n_tiles, src, dst,
+                                c->d_pins(), c->d_status(), std::min(n_tiles, 2 * c->sm_count), s, mode));
+    return CLOTH_OK;
+}
+
+// The network's tile list in the workspace (uploaded once per workspace and precision).
+int net_tile_list(cloth_ctx* c, const cloth_net* net, void* d_work, size_t bytes, int* n_tiles, cudaStream_t s)
+{
+    const std::vector<int4> tiles = net->precision == CLOTH_NET_BF16 ? tc_tiles(c) : comp_tiles(c);
     if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
-    int4* d_tiles = static_cast<int4*>(d_work);
-    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_BF16) {
-        CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    if (c->lists_written != d_work || c->lists_kind != net->precision) {
+        CK(cudaMemcpyAsync(d_work, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         c->lists_written = d_work;
-        c->lists_kind = CLOTH_NET_BF16;
+        c->lists_kind = net->precision;
     }
-    const int grid = std::min<int>((int)tiles.size(), c->sm_count);
+    *n_tiles = (int)tiles.size();
+    return CLOTH_OK;
+}
+
+int step_net_fused(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, cudaStream_t s)
+{
+    int n_tiles = 0;
+    const int rc = net_tile_list(c, net, d_work, bytes, &n_tiles, s);
+    if (rc) return rc;
     for (int st = 0; st < steps; ++st) {
-        CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), c->d_state(c->cur),
-                              c->d_state(c->cur ^ 1), c->d_pins(), c->d_status(), grid, s));
+        const int r = launch_net_step(c, net, static_cast<const int4*>(d_work), n_tiles, c->d_state(c->cur),
+                                      c->d_state(c->cur ^ 1), nullptr, s);
+        if (r) return r;
         c->cur ^= 1;
     }
     return CLOTH_OK;
@@ -600,7 +581,6 @@ int cloth_step_pcell(cloth_ctx* c, const float* d_w, int32_t steps, void* d_work
 int cloth_net_rollout_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes) return CLOTH_EINVAL;
-    if (precision != CLOTH_NET_BF16) return cloth_net_workspace_size(c, precision, bytes);
     size_t tiles = 0;
     int rc = cloth_net_workspace_size(c, precision, &tiles);
     if (rc) return rc;
@@ -616,18 +596,16 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
     if (!c || !net || !o || !d_work || o->steps < 0 || o->check_every < 0 || o->graph_chunk < 0) return CLOTH_EINVAL;
     if (o->check_every > 0 && !(o->residual_bound >= 0.f)) return CLOTH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (net->precision != CLOTH_NET_BF16) {
-        if (o->check_every > 0) return CLOTH_EUNSUPPORTED;
-        return cloth_step_net(c, net, o->steps, d_work, bytes, stream);
-    }
     size_t need = 0;
-    int rc = cloth_net_rollout_workspace_size(c, CLOTH_NET_BF16, &need);
+    int rc = cloth_net_rollout_workspace_size(c, net->precision, &need);
     if (rc) return rc;
     if (bytes < need) return CLOTH_ENOMEM;
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
-    const std::vector<int4> tiles = tc_tiles(c);
-    int4* d_tiles = static_cast<int4*>(d_work);
-    float* scratch = reinterpret_cast<float*>(static_cast<char*>(d_work) + align_up(sizeof(int4) * tiles.size(), kAlign));
+    int n_tiles = 0;
+    rc = net_tile_list(c, net, d_work, bytes, &n_tiles, s);
+    if (rc) return rc;
+    const int4* d_tiles = static_cast<const int4*>(d_work);
+    float* scratch = reinterpret_cast<float*>(static_cast<char*>(d_work) + align_up(sizeof(int4) * n_tiles, kAlign));
     float* scratch2 = c->net_stride > 1 ? scratch + (c->L.state[1] - c->L.state[0]) / sizeof(float) : nullptr;
     const int k = c->net_stride;
     // k plain steps from src ending in dst, through `other` in between
@@ -643,13 +621,6 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
         }
         return CLOTH_OK;
     };
-    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_BF16) {
-        CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-        c->lists_written = d_work;
-        c->lists_kind = CLOTH_NET_BF16;
-    }
-    const int grid = std::min<int>((int)tiles.size(), c->sm_count);
     const int ce = o->check_every;
     auto one_step = [&](int st, cudaStream_t ss) -> int {
         const float* src = c->d_state(c->cur);
@@ -658,18 +629,18 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
             // both from the same state: the network step into the scratch
             // buffer, its k plain steps into dst, then keep, or latch to
             // plain, per cloth
-            CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, scratch,
-                                  c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
-            int r = plain_k(src, dst, scratch2, nullptr, ss);
+            int r = launch_net_step(c, net, d_tiles, n_tiles, src, scratch, c->d_mode(), ss);
+            if (r) return r;
+            r = plain_k(src, dst, scratch2, nullptr, ss);
             if (r) return r;
             CK(launch_fallback_check(c->d_desc(), c->B, c->max_nodes, c->d_mode(), c->d_resid(), c->d_last(),
                                      o->residual_bound, scratch, dst, ss));
         } else {
             // cloths on the network: one network step; cloths on the plain
             // step: k plain steps (each kernel skips the other mode's cloths)
-            CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, (int)tiles.size(), src, dst,
-                                  c->d_pins(), c->d_status(), grid, ss, c->d_mode()));
-            int r = plain_k(src, dst, scratch, c->d_mode(), ss);
+            int r = launch_net_step(c, net, d_tiles, n_tiles, src, dst, c->d_mode(), ss);
+            if (r) return r;
+            r = plain_k(src, dst, scratch, c->d_mode(), ss);
             if (r) return r;
         }
         c->cur ^= 1;
@@ -731,12 +702,7 @@ int cloth_reset_modes(cloth_ctx* c, void* stream)
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
-    if (precision == CLOTH_NET_BF16) {
-        *bytes = align_up(sizeof(int4) * tc_tiles(c).size(), kAlign);
-        return CLOTH_OK;
-    }
-    make_groups(const_cast<cloth_ctx*>(c));
-    *bytes = step_ws(c).total;
+    *bytes = align_up(sizeof(int4) * (precision == CLOTH_NET_BF16 ? tc_tiles(c) : comp_tiles(c)).size(), kAlign);
     return CLOTH_OK;
 }
 
@@ -744,45 +710,7 @@ int cloth_step_net(cloth_ctx* c, const cloth_net* net, int32_t steps, void* d_wo
 {
     if (!c || !net || !d_work || steps < 0) return CLOTH_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
-    if (net->precision == CLOTH_NET_BF16) return step_net_bf16(c, net, steps, d_work, bytes, static_cast<cudaStream_t>(stream));
-    make_groups(c);
-    const StepWs w = step_ws(c);
-    if (bytes < w.total) return CLOTH_ENOMEM;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    char* ws = static_cast<char*>(d_work);
-    int32_t* lists = reinterpret_cast<int32_t*>(ws + w.lists);
-    if (c->lists_written != d_work || c->lists_kind != CLOTH_NET_FP32) {
-        std::vector<int32_t> all;
-        for (const auto& g : c->groups) all.insert(all.end(), g.cloths.begin(), g.cloths.end());
-        CK(cudaMemcpyAsync(lists, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-        c->lists_written = d_work;
-        c->lists_kind = CLOTH_NET_FP32;
-    }
-    float* t1 = reinterpret_cast<float*>(ws + w.t1);
-    float* t2 = reinterpret_cast<float*>(ws + w.t2);
-    float* a = reinterpret_cast<float*>(ws + w.a);
-    for (int st = 0; st < steps; ++st) {
-        for (const auto& g : c->groups) {
-            NetFwdArgs f{};
-            f.src.desc = c->d_desc();
-            f.src.cloth_of = lists + g.list_off;
-            f.src.state = c->d_state(c->cur);
-            f.w = net->d_w();
-            f.t1 = t1;
-            f.t2 = t2;
-            f.s = nullptr;
-            f.a = a;
-            f.N = (int)g.cloths.size();
-            f.H = g.H;
-            f.W = g.W;
-            CK(launch_net_forward_simt(f, s));
-            CK(launch_net_update(c->d_desc(), lists + g.list_off, f.N, g.H, g.W, a, c->d_state(c->cur),
-                                 c->d_state(c->cur ^ 1), c->d_pins(), c->d_status(), s));
-        }
-        c->cur ^= 1;
-    }
-    return CLOTH_OK;
+    return step_net_fused(c, net, steps, d_work, bytes, static_cast<cudaStream_t>(stream));
 }
 
 int cloth_workspace_size(int32_t B, const cloth_grid* grids, size_t* bytes)

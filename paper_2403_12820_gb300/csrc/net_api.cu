@@ -36,6 +36,7 @@ int ensure_init()
     if (!done[dev]) {
         NCK(net_simt_init());
         NCK(net_tc_init());
+        NCK(net_comp_init());
         done[dev] = true;
     }
     return CLOTH_OK;
@@ -84,6 +85,7 @@ int net_create(cloth_net** out, int32_t precision, const float* h_blob, void* d_
     if (e == cudaSuccess) e = cudaMemcpyAsync(n->d_w(), h_blob, sizeof(float) * kBlob, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->d_status(), 0, 64, s);
     if (e == cudaSuccess) e = launch_pack_bf16(n->d_w(), n->d_pack(), s);
+    if (e == cudaSuccess) e = launch_pack_comp(n->d_w(), n->d_comp(), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete n;
@@ -99,6 +101,7 @@ int net_set_weights(cloth_net* n, const float* d_blob, void* stream)
     NCK(cudaMemcpyAsync(n->d_w(), d_blob, sizeof(float) * kBlob, cudaMemcpyDeviceToDevice,
                         static_cast<cudaStream_t>(stream)));
     NCK(launch_pack_bf16(n->d_w(), n->d_pack(), static_cast<cudaStream_t>(stream)));
+    NCK(launch_pack_comp(n->d_w(), n->d_comp(), static_cast<cudaStream_t>(stream)));
     return CLOTH_OK;
 }
 

@@ -36,15 +36,9 @@ constexpr int kWgradBlocks = 512;
 constexpr int64_t kSavT1 = 0, kSavT2 = 64, kSavS = 128, kSavG2 = 160, kSavGT = 224, kSavGY = 256;
 constexpr int64_t kSavedPerNode = 260;
 
-// Where the cell reads its 6 input channels from.
+// Where the cell reads its 6 input channels from: NCHW z [N][6][H][W].
 struct NetSrc {
-    // NCHW input z [N][6][H][W] (net_forward) ...
     const float* z;
-    // ... or the cloth state planes (cloth_step_net): image n is cloth
-    // cloth_of[n]; u = planes 0-2, v = planes 3-5, permuted column order
-    const ClothDesc* desc;
-    const int32_t* cloth_of;
-    const float* state;
 };
 
 struct NetFwdArgs {
@@ -60,14 +54,35 @@ struct NetFwdArgs {
 cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s);
 cudaError_t launch_net_backward_simt(const float* w, const float* z, float* saved, const float* ga, float* gz,
                                      float* partials, float* gw, int N, int H, int W, cudaStream_t s);
-// Network step update: v <- C(v + dt (a + f_p / m)), u <- u + dt v, sphere.
-cudaError_t launch_net_update(const ClothDesc* desc, const int32_t* cloth_of, int n, int H, int W, const float* a,
-                              const float* src, float* dst, const uint32_t* pinmask, int32_t* status, cudaStream_t s);
 cudaError_t net_simt_init();
 int net_last_cuda_error();
+// One column of the trunk's composite kernels (Eq. 6 folded into Eq. 7):
+// G_n W2_a W1_b[:, i] for 3x3 taps a (W2) and b (W1) and input channel i,
+// where G_n is P's row n (n < 32), WL's tap tl and output co
+// (n = 32 + 3 tl + co < 59) or, for n >= 64, the identity on channel n - 64
+// (the velocity features xi).  Summed over a + b = c it is the 5x5
+// composite tap c; single (a, b) pairs give the edge and corner terms.
+__device__ inline float trunk_composite(const float* __restrict__ w, int n, int i, int a, int b)
+{
+    float s = 0.f;
+    if (n >= 64) {
+        const int k = n - 64;
+        for (int j = 0; j < kC; ++j) s = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], s);
+        return s;
+    }
+    for (int k = 0; k < kC; ++k) {
+        const float gk = n < 32 ? w[kOffP + n * kC + k] : w[kOffWL + ((n - 32) % 3 * kC + k) * 9 + (n - 32) / 3];
+        float d = 0.f;
+        for (int j = 0; j < kC; ++j) d = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], d);
+        s = fmaf(gk, d, s);
+    }
+    return s;
+}
+
 // Tensor-core (tcgen05, BF16) fused cell / network step (net_tc.cu).
 cudaError_t net_tc_init();
 int net_tc_pack_bytes();
+int net_tc_edge_offset();   // bytes from the pack's start to the FP32 edge and corner terms
 int net_tc_tile_rows();
 int net_tc_tile_cols();
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s);
@@ -76,6 +91,19 @@ cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDes
                                cudaStream_t s, const int32_t* mode = nullptr);
 cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
                                   int32_t* status, int grid, cudaStream_t s);
+// FP32 fused network step with the composite trunk (net_comp.cu): tiles of
+// net_comp_tile_rows() x net_comp_tile_cols() output nodes; its composite
+// weights (net_comp_pack_floats() floats) follow the tensor-core operands in
+// the pack, and it reads their FP32 edge and corner terms.
+int net_comp_tile_rows();
+int net_comp_tile_cols();
+int net_comp_pack_floats();
+cudaError_t net_comp_init();
+cudaError_t launch_pack_comp(const float* w, float* out, cudaStream_t s);
+cudaError_t launch_net_comp_step(const float* w, const float* wf, const float* ke, const ClothDesc* desc,
+                                 const int4* tiles, int n_tiles, const float* src, float* dst,
+                                 const uint32_t* pinmask, int32_t* status, int grid, cudaStream_t s,
+                                 const int32_t* mode = nullptr);
 
 
 // Host side of a network handle (include/cloth.h: cloth_net).
@@ -89,7 +117,7 @@ inline NetLayout net_layout()
     size_t off = 0;
     L.blob = off; off = al(off + sizeof(float) * kBlob);
     L.part = off; off = al(off + sizeof(float) * (size_t)kWgradBlocks * kParams);
-    L.pack = off; off = al(off + 131072);         // packed tensor-core operands
+    L.pack = off; off = al(off + 131072);         // packed tensor-core and FP32 composite operands
     L.status = off; off = al(off + 64);
     L.total = off;
     return L;
@@ -104,6 +132,10 @@ struct cloth_net {
     float* d_w() const { return reinterpret_cast<float*>(ws + L.blob); }
     float* d_part() const { return reinterpret_cast<float*>(ws + L.part); }
     void* d_pack() const { return ws + L.pack; }
+    // the FP32 composite weights after the tensor-core operands, and the
+    // FP32 edge and corner terms inside them
+    float* d_comp() const { return reinterpret_cast<float*>(ws + L.pack + (cloth::net_tc_pack_bytes() + 255) / 256 * 256); }
+    const float* d_edge() const { return reinterpret_cast<const float*>(ws + L.pack + cloth::net_tc_edge_offset()); }
     int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
     int sm_count = 0;
 };

@@ -1,5 +1,6 @@
 // CNN cell (Sec. 3.2, Eq. 6-7) in FP32 on CUDA cores: forward with saved
-// activations, hand-written backward, and the network-step update (Fig. 2).
+// activations and the hand-written backward (the cell and training path;
+// the FP32 network step is the fused kernel of net_comp.cu).
 //
 // Layer by layer, NCHW FP32 activations, every 3x3 convolution a tiled
 // kernel: a block of 128 threads computes a 32 x 8 tile of nodes for all
@@ -25,9 +26,7 @@ struct InZ {
     {
         const int n = img >> 1, f = img & 1;
         const float sc = w[kOffIns + 3 * f + c];
-        if (src.z) return sc * src.z[(((int64_t)n * 6 + 3 * f + c) * H + y) * W + x];
-        const ClothDesc& D = src.desc[src.cloth_of[n]];
-        return sc * src.state[D.plane_off + (3 * f + c) * D.plane_stride + (int64_t)y * D.pitch + col_pos(x)];
+        return sc * src.z[(((int64_t)n * 6 + 3 * f + c) * H + y) * W + x];
     }
 };
 
@@ -430,56 +429,6 @@ __global__ void reduce_partials_kernel(const float* __restrict__ part, float* __
     gw[j] += s;
 }
 
-// ----------------------------------------------------------------- update
-// v <- C(v + dt (a + f_p / m)), u <- u + dt v, sphere contact; f_p by
-// Eq. 3 (1/4 reading) as (d'_E - d'_W) x (d'_N - d'_S).
-__global__ void net_update_kernel(const ClothDesc* __restrict__ desc, const int32_t* __restrict__ cloth_of, int H,
-                                  int W, const float* __restrict__ a, const float* __restrict__ src,
-                                  float* __restrict__ dst, const uint32_t* __restrict__ pinmask,
-                                  int32_t* __restrict__ status)
-{
-    const int n = blockIdx.z;
-    const ClothDesc& D = desc[cloth_of[n]];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= W) return;
-    const int64_t HW = (int64_t)H * W;
-    const float* S = src + D.plane_off;
-    auto at = [&](int plane, int yy, int xx) { return S[plane * D.plane_stride + (int64_t)yy * D.pitch + col_pos(xx)]; };
-    float u[3], v[3], acc[3];
-    for (int c = 0; c < 3; ++c) {
-        u[c] = at(c, y, x);
-        v[c] = at(3 + c, y, x);
-        acc[c] = a[((int64_t)n * 3 + c) * HW + (int64_t)y * W + x];
-    }
-    if (D.p_quarter != 0.f) {
-        const bool bE = x + 1 < W, bW = x > 0, bN = y + 1 < H, bS = y > 0;
-        float e[3] = {0.f, 0.f, 0.f}, nn[3] = {0.f, 0.f, 0.f};
-        for (int c = 0; c < 3; ++c) {
-            if (bE) e[c] += at(c, y, x + 1) - u[c] + (c == 0 ? D.h : 0.f);
-            if (bW) e[c] -= at(c, y, x - 1) - u[c] - (c == 0 ? D.h : 0.f);
-            if (bN) nn[c] += at(c, y + 1, x) - u[c] + (c == 1 ? D.h : 0.f);
-            if (bS) nn[c] -= at(c, y - 1, x) - u[c] - (c == 1 ? D.h : 0.f);
-        }
-        const float sc = D.p_quarter * D.inv_m;
-        acc[0] = fmaf(sc, e[1] * nn[2] - e[2] * nn[1], acc[0]);
-        acc[1] = fmaf(sc, e[2] * nn[0] - e[0] * nn[2], acc[1]);
-        acc[2] = fmaf(sc, e[0] * nn[1] - e[1] * nn[0], acc[2]);
-    }
-    const bool pinned = (pinmask[D.pin_off + (int64_t)y * D.pin_wpr + (x >> 5)] >> (x & 31)) & 1u;
-    float vn[3], un[3];
-    for (int c = 0; c < 3; ++c) {
-        vn[c] = pinned ? pin_v(D, c) : fmaf(D.dt_net, acc[c], v[c]);
-        un[c] = fmaf(D.dt_net, vn[c], u[c]);
-    }
-    if (D.sph_on) sphere_contact(D, x, y, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
-    if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(status, 1);
-    float* O = dst + D.plane_off + (int64_t)y * D.pitch + col_pos(x);
-    for (int c = 0; c < 3; ++c) {
-        O[c * D.plane_stride] = un[c];
-        O[(3 + c) * D.plane_stride] = vn[c];
-    }
-}
-
 }  // namespace
 
 cudaError_t net_simt_init()
@@ -561,14 +510,6 @@ cudaError_t launch_net_backward_simt(const float* w, const float* z, float* save
     if (gz)
         return conv3x3<kC, 3>(View{G1, kC * HW, HW, W, 1, 0}, WtW1T{w}, OutGz{gz, w, H, W}, H, W, 2 * N, s);
     return cudaSuccess;
-}
-
-cudaError_t launch_net_update(const ClothDesc* desc, const int32_t* cloth_of, int n, int H, int W, const float* a,
-                              const float* src, float* dst, const uint32_t* pinmask, int32_t* status, cudaStream_t s)
-{
-    dim3 grid((W + 127) / 128, H, n);
-    net_update_kernel<<<grid, 128, 0, s>>>(desc, cloth_of, H, W, a, src, dst, pinmask, status);
-    return cudaGetLastError();
 }
 
 }  // namespace cloth

@@ -594,28 +594,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
-// The composite operands from the FP32 blob, one thread per value.
-// G_n is the output map of column n: P's row n (n < 32), WL's tap tl and
-// output co (n = 32 + 3 tl + co < 59) or the identity (n >= 64, xi); the
-// value for a set of (a, b) tap pairs and input channel i is
-//   sum_{(a, b)} G_n W2_a W1_b[:, i].
-__device__ float composite(const float* __restrict__ w, int n, int i, int a, int b)
-{
-    float s = 0.f;
-    if (n >= 64) {
-        const int k = n - 64;
-        for (int j = 0; j < kC; ++j) s = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], s);
-        return s;
-    }
-    for (int k = 0; k < kC; ++k) {
-        const float gk = n < 32 ? w[kOffP + n * kC + k] : w[kOffWL + ((n - 32) % 3 * kC + k) * 9 + (n - 32) / 3];
-        float d = 0.f;
-        for (int j = 0; j < kC; ++j) d = fmaf(w[kOffW2 + (k * kC + j) * 9 + a], w[kOffW1 + (j * 6 + i) * 9 + b], d);
-        s = fmaf(gk, d, s);
-    }
-    return s;
-}
-
+// The composite operands from the FP32 blob, one thread per value (the
+// algebra is trunk_composite).
 __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict__ out)
 {
     constexpr int nB = kPairs * 2 * kNC * 8;
@@ -631,7 +611,7 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
             for (int ay = 0; ay < 3; ++ay)
                 for (int ax = 0; ax < 3; ++ax) {
                     const int by = cy - ay, bx = cx - ax;
-                    if (by >= 0 && by < 3 && bx >= 0 && bx < 3) v += composite(w, n, e, tap(ay, ax), tap(by, bx));
+                    if (by >= 0 && by < 3 && bx >= 0 && bx < 3) v += trunk_composite(w, n, e, tap(ay, ax), tap(by, bx));
                 }
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         reinterpret_cast<__nv_bfloat16*>(out)[r] = h;
@@ -655,7 +635,7 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
                 else if (ed == 1) { a = tap(k, 2); b = tap(m, 0); }
                 else if (ed == 2) { a = tap(0, k); b = tap(2, m); }
                 else { a = tap(2, k); b = tap(0, m); }
-                v -= composite(w, n, i, a, b);
+                v -= trunk_composite(w, n, i, a, b);
             }
         }
         fo[q] = v;
@@ -666,7 +646,7 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
     float v = 0.f;
     if (n < 59 || n >= 64) {
         const int ay = (k4 >> 1) * 2, ax = (k4 & 1) * 2;
-        v = composite(w, n, n < 64 ? ch : 3 + ch, tap(ay, ax), tap(2 - ay, 2 - ax));
+        v = trunk_composite(w, n, n < 64 ? ch : 3 + ch, tap(ay, ax), tap(2 - ay, 2 - ax));
     }
     fo[kKE + q2] = v;
 }
@@ -674,6 +654,7 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
 }  // namespace
 
 int net_tc_pack_bytes() { return kPack; }
+int net_tc_edge_offset() { return kBc; }
 int net_tc_tile_rows() { return R; }
 int net_tc_tile_cols() { return WO; }
 

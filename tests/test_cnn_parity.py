@@ -146,3 +146,31 @@ def test_net_step_inference_batch_sampled():
     cloths compared with the oracle."""
     cfg = wl.cnn_batch()
     _net_step_case(cfg["specs"], cfg["pins"], cfg["x"], cfg["v"], blob(46), steps=2, sample=[0, 31])
+
+
+def test_net_step_velocity_matches_oracle_on_every_edge():
+    """One FP32 network step on cloths of uneven sizes in one launch (single
+    nodes, single rows and columns, an exact 14 x 14 tile, ragged tiles):
+    the velocity change dt (a + f_p / m) against the oracle's, normwise to
+    the cell's 1e-4.  Every edge and corner term of the fused composite step
+    is on this path."""
+    rng = np.random.default_rng(47)
+    shapes = [(1, 1), (1, 2), (3, 1), (2, 3), (14, 14), (15, 29), (30, 16), (5, 5)]
+    specs, pins, xs, vs = [], [], [], []
+    for (r, c) in shapes:
+        sp = wl.cloth_spec(r, c, p=rng.normal(0, 0.5))
+        x, v = wl.sag_state(sp, rng, amp=0.02, vamp=0.1)
+        specs.append(sp); xs.append(x); vs.append(v); pins.append([])
+    w = blob(48)
+    cb = ClothBatch(specs, pins)
+    cb.set_state(pack(xs).cuda(), pack(vs).cuda())
+    cb.step_net(Net(w, FP32), 1)
+    _, v1 = cb.get_state()
+    got = [t.cpu().numpy().astype(np.float64) for t in cb.split(v1)]
+    for b, sp in enumerate(specs):
+        _, vr = oracle.net_step(w.astype(np.float64), sp, xs[b], vs[b], pins=[], steps=1)
+        dv_ref = vr - vs[b].astype(np.float64)
+        dv = got[b] - vs[b].astype(np.float64)
+        assert normwise(dv, dv_ref) <= 1e-4, (shapes[b], normwise(dv, dv_ref))
+    assert cb.status() == 0
+

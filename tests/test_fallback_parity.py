@@ -46,10 +46,11 @@ def make(specs, pins, xs, vs):
     return cb
 
 
+@pytest.mark.parametrize("precision", [BF16, FP32])
 @pytest.mark.parametrize("chunk", [0, 8])
-def test_bound_zero_is_the_plain_rollout(chunk):
+def test_bound_zero_is_the_plain_rollout(chunk, precision):
     sb = sphere_batch()
-    net = Net(blob(72), BF16)
+    net = Net(blob(72), precision)
     a = make(*sb)
     a.rollout_net(net, 30, check_every=1, residual_bound=0.0, graph_chunk=chunk)
     b = make(*sb)
@@ -63,10 +64,11 @@ def test_bound_zero_is_the_plain_rollout(chunk):
     assert a.status() == 0
 
 
+@pytest.mark.parametrize("precision", [BF16, FP32])
 @pytest.mark.parametrize("check_every,chunk", [(3, 0), (3, 6), (1, 4), (0, 0)])
-def test_infinite_bound_is_the_network_rollout(check_every, chunk):
+def test_infinite_bound_is_the_network_rollout(check_every, chunk, precision):
     sb = sphere_batch()
-    net = Net(blob(73), BF16)
+    net = Net(blob(73), precision)
     a = make(*sb)
     a.rollout_net(net, 20, check_every=check_every, residual_bound=float("inf"), graph_chunk=chunk)
     b = make(*sb)
@@ -80,7 +82,8 @@ def test_infinite_bound_is_the_network_rollout(check_every, chunk):
         assert bool(torch.isfinite(resid).all()) and bool((resid > 0).all())
 
 
-def test_switch_follows_the_oracle():
+@pytest.mark.parametrize("precision", [BF16, FP32])
+def test_switch_follows_the_oracle(precision):
     specs, pins, xs, vs = sphere_batch()
     w = blob(74)
     w64 = w.astype(np.float64)
@@ -104,7 +107,7 @@ def test_switch_follows_the_oracle():
     assert 0 < expect.sum() < B
 
     cb = make(specs, pins, xs, vs)
-    net = Net(w, BF16)
+    net = Net(w, precision)
     cb.rollout_net(net, 1, check_every=1, residual_bound=bound)
     mode, resid = cb.modes()
     assert mode.cpu().numpy().tolist() == expect.tolist()
@@ -126,12 +129,9 @@ def test_switch_follows_the_oracle():
     assert cb.status() == 0
 
 
-def test_checks_need_the_tensor_core_network():
+@pytest.mark.parametrize("precision", [BF16, FP32])
+def test_a_negative_bound_is_rejected(precision):
     sb = sphere_batch(sides=(16, 16), sigmas=(1e-4, 1e-4))
     cb = make(*sb)
-    net = Net(blob(75), FP32)
-    with pytest.raises(ClothError, match="EUNSUPPORTED"):
-        cb.rollout_net(net, 2, check_every=1, residual_bound=1.0)
     with pytest.raises(ClothError, match="EINVAL"):
-        cb.rollout_net(Net(blob(75), BF16), 2, check_every=1, residual_bound=-1.0)
-    cb.rollout_net(net, 2)   # no checks: the FP32 network step
+        cb.rollout_net(Net(blob(75), precision), 2, check_every=1, residual_bound=-1.0)
