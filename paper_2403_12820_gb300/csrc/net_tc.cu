@@ -40,7 +40,10 @@
 //      m)), u <- u + dt v, sphere contact, store.
 // Tiles are pipelined: the input of tile t+1 is staged while the MMAs of
 // tile t run, and the first two chunks of tile t+1 run during the final
-// pass of tile t.  Every wait on the tensor cores is bounded; a timeout
+// pass of tile t.  Between the chunks there is no CTA barrier: each worker
+// warp arrives on an accumulator's "free" mbarrier once it has read it, and
+// the issuing thread waits there before it reuses the accumulator; a tile
+// has two CTA barriers (before and after its final pass).  Every wait on the tensor cores is bounded; a timeout
 // sets a status bit and the kernel returns after releasing its tensor
 // memory.
 #include <cuda_bf16.h>
@@ -97,7 +100,7 @@ constexpr int oPar = oND + 4 * R * WO * 3 * 4;         // WND[32][8] (WN0..2 WD0
 constexpr int oDesc = oPar + (256 + 16) * 4;        // the two tiles' cloth descriptors
 constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
 constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers of the two accumulators; TMEM address
-constexpr int kNumBars = 2;
+constexpr int kNumBars = 4;   // accumulator b full (MMAs done) at b, free (16 warps read it) at 2 + b
 constexpr int oTmemSlot = oBar + 8 * kNumBars;
 constexpr int kSmem = oTmemSlot + 16;
 static_assert(kSmem <= 232448, "shared memory");
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     uint8_t* sPin = sm + oPin;
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
     auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
+    auto bar_free = [&](int b) { return sbase + oBar + 8u * (uint32_t)(2 + b); };
     auto sIn = [&](int buf) { return reinterpret_cast<uint4*>(sm + oIn) + buf * N0BUF; };
 
     // ---- one-time set-up: operands, barriers, tensor memory
@@ -192,7 +196,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     for (int e = tid; e < 2 * (N0BUF - N0); e += NTH)
         sIn(e / (N0BUF - N0))[N0 + e % (N0BUF - N0)] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int b = 0; b < kNumBars; ++b) tc::mbar_init(bar(b), 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(bar(b), 1);
+            tc::mbar_init(bar_free(b), NWORK / 32);
+        }
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -214,7 +221,17 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // LBO = 16 bytes, a row's last tap with the next row's first at LBO =
     // (PT - 4) rows.
     const uint64_t dBc = tc::sdesc(sbase + oBc, kNC * 16, 128);
+    // the issuer's view of the accumulators: every use but the first waits
+    // for the 16 worker warps' reads of the previous one
+    bool used[2] = {false, false};
+    uint32_t pfree[2] = {0, 0};
     auto issue_chunk = [&](int c2, int ib) {   // chunk c2 of input buffer ib into accumulator c2 & 1
+        const int b = c2 & 1;
+        if (used[b]) {
+            if (!tc::mbar_wait(bar_free(b), pfree[b], kWaitLimit)) return false;
+            pfree[b] ^= 1u;
+        }
+        used[b] = true;
         tc::fence_after();
         const uint32_t d = tmem + (uint32_t)kNC * (uint32_t)(c2 & 1);
         const uint32_t in = sbase + oIn + (uint32_t)(ib * N0BUF * 16);
@@ -227,6 +244,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             tc::mma_bf16(d, ad, dBc + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), p > 0);
         }
         tc::mma_commit(bar(c2 & 1));
+        return true;
     };
 
     // ---- per-tile pieces
@@ -546,35 +564,38 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         const int tnn = has_next ? skip(tn + (int)gridDim.x) : n_tiles;
         Geo gnn{};
         if (tnn < n_tiles) gnn = geo(tnn);
+        // No CTA barrier between the chunks: each worker warp reports its
+        // reads of an accumulator on that accumulator's "free" barrier, and
+        // the issuer waits there before it reuses the accumulator.
+        bool ok = true;
         for (int c2 = 0; c2 < C2; ++c2) {
             const int b = c2 & 1;
-            bool ok = true;
             if (worker) {
-                ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
+                if (ok) ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
                 if (ok) epilogue(g, c2, b);
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(bar_free(b));   // also after a timeout: the issuer's wait ends
 #pragma unroll
                 for (int k = 0; k < kStageParts; ++k)   // register-indexed: k is a constant here
                     if (k == c2 && has_next && tid + k * NWORK < N0) stage_store(gn, buf ^ 1, tid + k * NWORK, rw[k]);
                 if (STEP && c2 == 0 && has_next && tid < kDescV) reinterpret_cast<uint4*>(sD + (buf ^ 1))[tid] = dv;
             }
             ph[b] ^= 1u;
-            if (__syncthreads_or(!ok)) { timed_out = true; break; }
-            if (issuer && c2 + 2 < C2) issue_chunk(c2 + 2, buf);   // accumulator b is free again
+            if (issuer && ok && c2 + 2 < C2) ok = issue_chunk(c2 + 2, buf);
         }
-        if (timed_out) break;
 
         // the next tile's first two chunks run during this tile's final pass
         if (worker) tc::fence_async_smem();   // the staged input, for the tensor cores
-        __syncthreads();
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (issuer && has_next) {
-            issue_chunk(0, buf ^ 1);
-            if (C2 > 1) issue_chunk(1, buf ^ 1);
+            ok = issue_chunk(0, buf ^ 1);
+            if (ok && C2 > 1) ok = issue_chunk(1, buf ^ 1);
         }
         if (worker) {
             final_pass(g, buf);
             if (has_next) edge_prep(gn, sIn(buf ^ 1));   // this tile's epilogues are done
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tile = tn;
         tn = tnn;
         g = gn;
@@ -587,7 +608,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     if (timed_out) {
         if (tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
         for (int k = 0; k < 2; ++k)
-            for (int b = 0; b < kNumBars; ++b) tc::mbar_wait(bar(b), (uint32_t)k, 1u << 18);
+            for (int b = 0; b < 2; ++b) tc::mbar_wait(bar(b), (uint32_t)k, 1u << 18);
     }
     tc::fence_before();
     __syncthreads();
