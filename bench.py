@@ -249,7 +249,7 @@ def run_reference(args, rank, world):
     sample_steps = 1
     # warm-up, then each timed bench step is one plain step of the whole batch
     steps = max(1, min(args.steps, 10))
-    warm = max(0, min(args.warmup, 1))
+    warm = max(0, min(args.warmup, 3))
     if warm:
         oracle_plain_rate(cfg, 1, cores)
     rate, wall = oracle_plain_rate(cfg, steps * sample_steps, cores)
