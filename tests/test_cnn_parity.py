@@ -174,3 +174,33 @@ def test_net_step_velocity_matches_oracle_on_every_edge():
         assert normwise(dv, dv_ref) <= 1e-4, (shapes[b], normwise(dv, dv_ref))
     assert cb.status() == 0
 
+
+def test_net_step_maximum_size_cloth_sampled():
+    """One 2048 x 2048 cloth through the FP32 network step: sampled nodes
+    (corners, edges, random) equal the oracle's network step on the window of
+    radius 3 (the receptive field of the two 3x3 trunk convolutions and the
+    3x3 linear branch) around them."""
+    n = 2048
+    rng = np.random.default_rng(49)
+    sp = wl.cloth_spec(n, n, p=0.3)
+    x, v = wl.noisy_flat_state(sp, 1e-3, rng)
+    v = (v + rng.normal(0, 0.05, v.shape)).astype(np.float32)
+    w = blob(50)
+    cb = ClothBatch([sp], [[0]])
+    cb.set_state(pack([x]).cuda(), pack([v]).cuda())
+    cb.step_net(Net(w, FP32), 1)
+    xg = cb.get_state()[0].cpu().numpy().reshape(n, n, 3)
+    x64, v64 = x.astype(np.float64), v.astype(np.float64)
+    samples = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (1, 1), (0, 700), (1500, n - 1)] + \
+              [tuple(int(t) for t in rng.integers(0, n, 2)) for _ in range(30)]
+    for (r, c) in samples:
+        r0, r1, c0, c1 = max(0, r - 3), min(n, r + 4), max(0, c - 3), min(n, c + 4)
+        ws = dict(sp)
+        ws["rows"], ws["cols"] = r1 - r0, c1 - c0
+        sh = np.array([c0 * sp["h"], r0 * sp["h"], 0.0])
+        wpins = [0] if (r0, c0) == (0, 0) else []
+        xr, _ = oracle.net_step(w.astype(np.float64), ws, x64[r0:r1, c0:c1] - sh, v64[r0:r1, c0:c1],
+                                pins=wpins, steps=1)
+        assert np.abs(xg[r, c] - (xr[r - r0, c - c0] + sh)).max() <= 1e-5, (r, c)
+    assert cb.status() == 0
+
