@@ -15,14 +15,15 @@
 //   0. stage the 20 x 20 input region (scaled z, and the raw u, v of the
 //      16 x 16 cell region for the update), zero outside the cloth;
 //   1. the composite convolution over the 16 x 16 cell region: a thread
-//      takes two cell positions 8 rows apart and one of four column groups
-//      (t and xi channels [8 g, +8), q values [7 g, +7)), accumulates the 24
-//      columns in paired FP32 (f32x2) FMAs with the weights read from shared
-//      memory (the same address for the whole warp), adds the edge terms,
-//      stores q and its channels' share of N + D = WN s + WD (xi . s), s =
-//      tanh(t);
+//      takes four cell positions 4 rows apart and one of eight column groups
+//      (t and xi channels [4 g, +4), q values [4 g, +4) below 27),
+//      accumulates the 12 columns of the 4 positions in paired FP32 (f32x2)
+//      FMAs with the weights read from shared memory (the same address for
+//      the whole warp, each load feeding the 4 positions), adds the edge
+//      terms, stores q and its channels' share of N + D = WN s + WD (xi . s),
+//      s = tanh(t);
 //   2. per output node: L = bL + sum_tap q_tap at the tap's neighbour, the
-//      four shares of N + D added in a fixed order, a = out_scale (L + N +
+//      eight shares of N + D added in a fixed order, a = out_scale (L + N +
 //      D), then v <- C(v + dt (a + f_p / m)), u <- u + dt v, sphere contact,
 //      store.
 #include "net_internal.cuh"
@@ -35,13 +36,15 @@ constexpr int CR = TR + 2, CC = TC + 2;    // cell region, origin (y0 - 1, x0 - 
 constexpr int IR = TR + 6, IC = TC + 6;    // input region, origin (y0 - 3, x0 - 3)
 constexpr int NCELL = CR * CC, NIN = IR * IC, NOUT = TR * TC;
 constexpr int NTHR = 256;
-constexpr int kGroups = 4, kGW = 24;       // column groups; weights per (group, tap, channel)
+constexpr int kGroups = 8, kGW = 12;       // column groups; weights per (group, tap, channel)
+constexpr int kPos = 4;                    // cell positions per item, 4 rows apart
+constexpr int kQuads = NCELL / kPos;       // 64
 constexpr int kWF = kGroups * 25 * 3 * kGW;
-static_assert(NCELL == 2 * 128 && kGroups * 128 == 2 * NTHR, "two items of two positions per thread");
+static_assert(kGroups * kQuads == 2 * NTHR && kQuads % 32 == 0, "two items of four positions per thread, one group per warp");
 static_assert(NOUT <= NTHR, "one output node per thread in the final pass");
 
 // shared memory (bytes)
-constexpr int oW = 0;                                  // composite weights [g][tap][ch][24]
+constexpr int oW = 0;                                  // composite weights [g][tap][ch][12]
 constexpr int oZ = oW + kWF * 4;                       // scaled z: [NIN] float4 u0 u1 u2 v0, then [NIN] float2 v1 v2
 constexpr int oRaw = oZ + NIN * 24;                    // raw u, v [6][NCELL]
 constexpr int oQ = oRaw + 6 * NCELL * 4;               // q [27][NCELL]
@@ -136,51 +139,54 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
         __syncthreads();
 
         // 1. the composite convolution, two items per thread: column group g
-        // (the same for a whole warp) and cell positions p0, p0 + 128
+        // (the same for a whole warp) and cell positions p0 + 64 k, k < 4
 #pragma unroll 1
         for (int r = 0; r < 2; ++r) {
-            const int item = r * NTHR + tid, g = item >> 7, p0 = item & 127;
+            const int item = r * NTHR + tid, g = item / kQuads, p0 = item % kQuads;
             const int cy0 = p0 / CC, cx = p0 % CC;
-            float2 acc[2][12];
+            float2 acc[kPos][6];   // t pairs 0-1, xi pairs 2-3, q pairs 4-5
 #pragma unroll
-            for (int k = 0; k < 12; ++k) acc[0][k] = acc[1][k] = F2(0.f);
+            for (int p = 0; p < kPos; ++p)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) acc[p][k] = F2(0.f);
 #pragma unroll 1
             for (int ty = 0; ty < 5; ++ty) {
-#pragma unroll
+#pragma unroll 1
                 for (int tx = 0; tx < 5; ++tx) {
-                    const int i0 = (cy0 + ty) * IC + cx + tx, i1 = i0 + 8 * IC;
-                    const float4 a0 = sZa[i0], a1 = sZa[i1];
-                    const float2 b0 = sZb[i0], b1 = sZb[i1];
-                    const float zu[2][3] = {{a0.x, a0.y, a0.z}, {a1.x, a1.y, a1.z}};
-                    const float zv[2][3] = {{a0.w, b0.x, b0.y}, {a1.w, b1.x, b1.y}};
+                    const int i0 = (cy0 + ty) * IC + cx + tx;
+                    float zu[kPos][3], zv[kPos][3];
+#pragma unroll
+                    for (int p = 0; p < kPos; ++p) {
+                        const float4 a = sZa[i0 + 4 * p * IC];
+                        const float2 b = sZb[i0 + 4 * p * IC];
+                        zu[p][0] = a.x; zu[p][1] = a.y; zu[p][2] = a.z;
+                        zv[p][0] = a.w; zv[p][1] = b.x; zv[p][2] = b.y;
+                    }
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        const float4* wp = sW + ((g * 25 + ty * 5 + tx) * 3 + ch) * 6;
-                        const float4 w[6] = {wp[0], wp[1], wp[2], wp[3], wp[4], wp[5]};
+                        const float4* wp = sW + ((g * 25 + ty * 5 + tx) * 3 + ch) * 3;
+                        const float4 wt = wp[0], wx = wp[1], wq = wp[2];
 #pragma unroll
-                        for (int p = 0; p < 2; ++p) {
+                        for (int p = 0; p < kPos; ++p) {
                             const float2 u = F2(zu[p][ch]), vv = F2(zv[p][ch]);
-#pragma unroll
-                            for (int k = 0; k < 2; ++k) {
-                                acc[p][2 * k] = fma2(make_float2(w[k].x, w[k].y), u, acc[p][2 * k]);
-                                acc[p][2 * k + 1] = fma2(make_float2(w[k].z, w[k].w), u, acc[p][2 * k + 1]);
-                                acc[p][4 + 2 * k] = fma2(make_float2(w[2 + k].x, w[2 + k].y), vv, acc[p][4 + 2 * k]);
-                                acc[p][5 + 2 * k] = fma2(make_float2(w[2 + k].z, w[2 + k].w), vv, acc[p][5 + 2 * k]);
-                                acc[p][8 + 2 * k] = fma2(make_float2(w[4 + k].x, w[4 + k].y), u, acc[p][8 + 2 * k]);
-                                acc[p][9 + 2 * k] = fma2(make_float2(w[4 + k].z, w[4 + k].w), u, acc[p][9 + 2 * k]);
-                            }
+                            acc[p][0] = fma2(make_float2(wt.x, wt.y), u, acc[p][0]);
+                            acc[p][1] = fma2(make_float2(wt.z, wt.w), u, acc[p][1]);
+                            acc[p][2] = fma2(make_float2(wx.x, wx.y), vv, acc[p][2]);
+                            acc[p][3] = fma2(make_float2(wx.z, wx.w), vv, acc[p][3]);
+                            acc[p][4] = fma2(make_float2(wq.x, wq.y), u, acc[p][4]);
+                            acc[p][5] = fma2(make_float2(wq.z, wq.w), u, acc[p][5]);
                         }
                     }
                 }
             }
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const int cy = cy0 + 8 * p, cell = cy * CC + cx;
+            for (int p = 0; p < kPos; ++p) {
+                const int cy = cy0 + 4 * p, cell = cy * CC + cx;
                 const int y = y0 - 1 + cy, x = x0 - 1 + cx;
                 const bool valid = y >= 0 && y < H && x >= 0 && x < W;
-                float* col = reinterpret_cast<float*>(acc[p]);   // t [0, 8), xi [8, 16), q [16, 23)
+                float* col = reinterpret_cast<float*>(acc[p]);   // t [0, 4), xi [4, 8), q [8, 12)
                 if (valid && (x == 0 || y == 0 || x == W - 1 || y == H - 1)) {
-                    // the edge terms of this node's 24 columns: z at input (cy + 2 + dy, cx + 2 + dx)
+                    // the edge terms of this node's 12 columns: z at input (cy + 2 + dy, cx + 2 + dx)
                     const bool e[4] = {x == 0, x == W - 1, y == 0, y == H - 1};
                     auto add = [&](const float* K, int zi) {   // K = [3][96] of one tap
                         const float4 a = sZa[zi];
@@ -190,21 +196,19 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
                         for (int ch = 0; ch < 3; ++ch) {
                             const float* k = K + ch * 96;
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                col[j] = fmaf(__ldg(k + 8 * g + j), zu3[ch], col[j]);
-                                col[8 + j] = fmaf(__ldg(k + 64 + 8 * g + j), zv3[ch], col[8 + j]);
+                            for (int j = 0; j < 4; ++j) {
+                                col[j] = fmaf(__ldg(k + 4 * g + j), zu3[ch], col[j]);
+                                col[4 + j] = fmaf(__ldg(k + 64 + 4 * g + j), zv3[ch], col[4 + j]);
+                                if (4 * g + j < 27) col[8 + j] = fmaf(__ldg(k + 32 + 4 * g + j), zu3[ch], col[8 + j]);
                             }
-#pragma unroll
-                            for (int j = 0; j < 7; ++j)
-                                if (7 * g + j < 27) col[16 + j] = fmaf(__ldg(k + 32 + 7 * g + j), zu3[ch], col[16 + j]);
                         }
                     };
 #pragma unroll 1
                     for (int ed = 0; ed < 4; ++ed) {
                         if (!e[ed]) continue;
 #pragma unroll 1
-                        for (int s = 0; s < 5; ++s)
-                            add(A.ke + (ed * 5 + s) * 3 * 96, ed < 2 ? (cy + s) * IC + cx + 2 : (cy + 2) * IC + cx + s);
+                        for (int s5 = 0; s5 < 5; ++s5)
+                            add(A.ke + (ed * 5 + s5) * 3 * 96, ed < 2 ? (cy + s5) * IC + cx + 2 : (cy + 2) * IC + cx + s5);
                     }
 #pragma unroll 1
                     for (int k4 = 0; k4 < 4; ++k4) {
@@ -213,19 +217,19 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < 7; ++j)
-                    if (7 * g + j < 27) sQ[(7 * g + j) * NCELL + cell] = valid ? col[16 + j] : 0.f;
+                for (int j = 0; j < 4; ++j)
+                    if (4 * g + j < 27) sQ[(4 * g + j) * NCELL + cell] = valid ? col[8 + j] : 0.f;
                 const int oy = cy - 1, ox = cx - 1;
                 if (valid && oy >= 0 && oy < TR && ox >= 0 && ox < TC) {
                     float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float s = tanhf(col[j]);
-                        const float xs = col[8 + j] * s;
-                        const float4 w0 = sWND[2 * (8 * g + j)], w1 = sWND[2 * (8 * g + j) + 1];
-                        nd0 = fmaf(w0.x, s, fmaf(w0.w, xs, nd0));
-                        nd1 = fmaf(w0.y, s, fmaf(w1.x, xs, nd1));
-                        nd2 = fmaf(w0.z, s, fmaf(w1.y, xs, nd2));
+                    for (int j = 0; j < 4; ++j) {
+                        const float sv = tanhf(col[j]);
+                        const float xs = col[4 + j] * sv;
+                        const float4 w0 = sWND[2 * (4 * g + j)], w1 = sWND[2 * (4 * g + j) + 1];
+                        nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
+                        nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
+                        nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
                     }
                     float* o = sND + (g * NOUT + oy * TC + ox) * 3;
                     o[0] = nd0;
@@ -247,8 +251,9 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
                     float L = sBL[co];
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) L += sQ[(tap * 3 + co) * NCELL + (oy + tap / 3) * CC + ox + tap % 3];
-                    const float nd = ((sND[tid * 3 + co] + sND[(NOUT + tid) * 3 + co]) + sND[(2 * NOUT + tid) * 3 + co]) +
-                                     sND[(3 * NOUT + tid) * 3 + co];
+                    float nd = sND[tid * 3 + co];
+#pragma unroll
+                    for (int gg = 1; gg < kGroups; ++gg) nd += sND[(gg * NOUT + tid) * 3 + co];
                     acc[co] = sOut[co] * (L + nd);
                 }
                 auto U = [&](int ch, int cy, int cx) { return sRaw[ch * NCELL + cy * CC + cx]; };   // cell coordinates
@@ -295,19 +300,19 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
     }
 }
 
-// The composite weights [g][tap][ch][24] from the FP32 blob, one thread per
-// value: slots 0-7 t channel 8 g + e (input u_ch), 8-15 xi channel
-// 8 g + e - 8 (input v_ch), 16-22 q value 7 g + e - 16 (input u_ch; none past
-// 27), 23 zero.
+// The composite weights [g][tap][ch][12] from the FP32 blob, one thread per
+// value: slots 0-3 t channel 4 g + e (input u_ch), 4-7 xi channel
+// 4 g + e - 4 (input v_ch), 8-11 q value 4 g + e - 8 (input u_ch; none past
+// 27).
 __global__ void pack_comp_kernel(const float* __restrict__ w, float* __restrict__ out)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= kWF) return;
     const int e = r % kGW, ch = (r / kGW) % 3, c = (r / (3 * kGW)) % 25, g = r / (75 * kGW);
     int n = -1, i = ch;
-    if (e < 8) n = 8 * g + e;
-    else if (e < 16) { n = 64 + 8 * g + e - 8; i = 3 + ch; }
-    else if (e < 23 && 7 * g + e - 16 < 27) n = 32 + 7 * g + e - 16;
+    if (e < 4) n = 4 * g + e;
+    else if (e < 8) { n = 64 + 4 * g + e - 4; i = 3 + ch; }
+    else if (4 * g + e - 8 < 27) n = 32 + 4 * g + e - 8;
     float v = 0.f;
     if (n >= 0) {
         const int cy = c / 5, cx = c % 5;
