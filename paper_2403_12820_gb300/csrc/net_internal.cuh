@@ -117,7 +117,8 @@ inline NetLayout net_layout()
     size_t off = 0;
     L.blob = off; off = al(off + sizeof(float) * kBlob);
     L.part = off; off = al(off + sizeof(float) * (size_t)kWgradBlocks * kParams);
-    L.pack = off; off = al(off + 131072);         // packed tensor-core and FP32 composite operands
+    // packed tensor-core operands, then the FP32 composite weights (d_comp)
+    L.pack = off; off = al(off + al((size_t)net_tc_pack_bytes()) + sizeof(float) * (size_t)net_comp_pack_floats());
     L.status = off; off = al(off + 64);
     L.total = off;
     return L;
@@ -135,6 +136,7 @@ struct cloth_net {
     // the FP32 composite weights after the tensor-core operands, and the
     // FP32 edge and corner terms inside them
     float* d_comp() const { return reinterpret_cast<float*>(ws + L.pack + (cloth::net_tc_pack_bytes() + 255) / 256 * 256); }
+    // (net_layout reserves exactly these two parts, in this order)
     const float* d_edge() const { return reinterpret_cast<const float*>(ws + L.pack + cloth::net_tc_edge_offset()); }
     int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
     int sm_count = 0;
