@@ -299,8 +299,12 @@ enum {
 
 typedef struct cloth_net cloth_net;
 
-/* Device workspace of a network: weights in FP32 and packed tensor-core
- * forms, plus the per-block partial sums of net_backward. */
+/* Device workspace of a network: the FP32 weights; the composite-trunk
+ * operands of the network steps, repacked by net_create and
+ * net_set_weights (the trunk of Eq. 6 with P and the linear branch of Eq. 7
+ * folded into one 5x5 kernel, in BF16 for the tensor cores and FP32 for
+ * the CUDA cores, and FP32 edge terms); and the per-block partial sums of
+ * net_backward. */
 int net_workspace_size(size_t* bytes);
 
 /* Create a network on the current device from a HOST weight blob of
@@ -367,8 +371,13 @@ int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* by
 
 /* Advance every cloth `steps` network steps (Fig. 2): a = cell(u, v), then
  * v <- C(v + dt (a + f_p / m)), x <- x + dt v with the pressure f_p of Eq. 3
- * and the pins hard-encoded outside the network, then sphere contact.
- * d_work: cloth_net_workspace_size() bytes. */
+ * and the pins hard-encoded outside the network, then sphere contact.  One
+ * fused kernel per step for the whole batch: the tensor-core kernel for a
+ * BF16 network, the CUDA-core kernel for an FP32 one; both evaluate the
+ * trunk through the composite kernel (exact algebra, FP32 edge terms on the
+ * cloth's outermost ring), so results differ from net_forward's layered
+ * evaluation only by rounding.  d_work: cloth_net_workspace_size() bytes
+ * (the tile list). */
 int cloth_step_net(cloth_ctx* ctx, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream);
 
 /* Network rollout with the plain step as fallback and judge (Fig. 2: the
