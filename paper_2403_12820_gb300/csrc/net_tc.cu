@@ -27,10 +27,11 @@
 //      in_scale v, 0, 0 per node; zero outside the cloth) into one of two
 //      input buffers, and the raw FP32 u, v of the output nodes and their
 //      1-node halo into one of two FP32 tile buffers;
-//   2. per chunk of the (R+2)-row cell region, 13 MMAs of K = 16, each
-//      pairing two of the 25 taps (the second core-matrix column of K sits
-//      LBO = the taps' row distance further), into one of two tensor-memory
-//      accumulators (chunk c+1 runs during the epilogue of chunk c);
+//   2. per chunk of the (R+2)-row cell region (R = 14, WO = 26: exactly
+//      four chunks), 13 MMAs of K = 16, each pairing two of the 25 taps (the
+//      second core-matrix column of K sits LBO = the taps' row distance
+//      further), into one of two tensor-memory accumulators (chunk c+1 runs
+//      during the epilogue of chunk c);
 //   3. epilogue per cell-region node: the edge corrections (computed per
 //      tile from the staged input, before its first epilogue), s = tanh(t),
 //      N + D = WN s + WD (xi . s); q kept in shared memory (zero outside the
@@ -43,9 +44,9 @@
 // pass of tile t.  Between the chunks there is no CTA barrier: each worker
 // warp arrives on an accumulator's "free" mbarrier once it has read it, and
 // the issuing thread waits there before it reuses the accumulator; a tile
-// has two CTA barriers (before and after its final pass).  Every wait on the tensor cores is bounded; a timeout
-// sets a status bit and the kernel returns after releasing its tensor
-// memory.
+// has two CTA barriers (before and after its final pass).  Every wait on
+// the tensor cores is bounded; a timeout sets a status bit and the kernel
+// returns after releasing its tensor memory.
 #include <cuda_bf16.h>
 
 #include "net_internal.cuh"
