@@ -42,6 +42,7 @@ constexpr int kQuads = NCELL / kPos;       // 64
 constexpr int kWF = kGroups * 25 * 3 * kGW;
 static_assert(kGroups * kQuads == 2 * NTHR && kQuads % 32 == 0, "two items of four positions per thread, one group per warp");
 static_assert(NOUT <= NTHR, "one output node per thread in the final pass");
+static_assert(kQuads == 4 * CC && CR == 4 * kPos, "the rows cy0 + 4 p of the 64 quads cover the cell region once");
 
 // shared memory (bytes)
 constexpr int oW = 0;                                  // composite weights [g][tap][ch][12]
