@@ -60,3 +60,24 @@ def _ref_main(rank: int, world: int, port: int, out_dir: str):
 def test_reference_arm_other_ranks_do_no_work(tmp_path):
     _ref_main(1, 2, _free_port(), str(tmp_path))
     assert open(tmp_path / "ref1.txt").read() == "None"
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """Rank 0 of `--impl reference` times the FP64 oracle on the host cores
+    and returns the contract's JSON line: the plain arm's metric and unit,
+    the requested steps and warm-up, and cpu_baseline / e2e describing the
+    same run."""
+    import bench
+    args = bench.parse_args(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    out = bench.run_reference(args, 0, 1)
+    assert out["impl"] == "reference"
+    assert out["metric"].startswith("cloth node-steps/s") and out["unit"] == "node-steps/s"
+    assert out["value"] > 0 and out["higher_is_better"] is True and out["vs_baseline"] is None
+    assert out["steps"] == 1 and out["warmup"] == 3 and out["n_gpus"] == 1 and out["scaling"] == "weak"
+    assert out["ms_per_step"] > 0 and out["dtype"] == "f64" and out["data"] == "synthetic"
+    assert out["config"]["workload"].startswith("plain_batch")
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1 and cb["sample"]
+    e2e = out["e2e"]
+    assert e2e["value"] == out["value"] and e2e["unit"] == out["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
