@@ -3,6 +3,8 @@
 // as the judge of the network step.  On a check step both steps start from
 // the same state; a cloth whose largest node-position difference exceeds
 // the bound is switched to the plain step for the rest of the rollout.
+#include <cfloat>
+
 #include "cloth_internal.cuh"
 
 namespace cloth {
@@ -11,7 +13,8 @@ namespace {
 constexpr int TB = 256;
 
 // resid[b] = max over the nodes of cloth b (still in network mode) of
-// |u_net - u_plain|; positive floats order like their bit patterns.
+// |u_net - u_plain|, +inf where that difference is not finite; positive
+// floats (+inf included) order like their bit patterns.
 __global__ void residual_kernel(const ClothDesc* __restrict__ desc, const int32_t* __restrict__ mode,
                                 const float* __restrict__ net, const float* __restrict__ plain,
                                 float* __restrict__ resid)
@@ -29,7 +32,9 @@ __global__ void residual_kernel(const ClothDesc* __restrict__ desc, const int32_
             const float d = net[o + k * D.plane_stride] - plain[o + k * D.plane_stride];
             d2 = fmaf(d, d, d2);
         }
-        m = fmaxf(m, sqrtf(d2));
+        // a non-finite difference (a network result gone NaN or infinite)
+        // counts as an infinite residual: fmaxf would drop a NaN
+        m = fmaxf(m, d2 <= FLT_MAX ? sqrtf(d2) : __int_as_float(0x7f800000));
     }
     for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, s));
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(resid + b), __float_as_int(m));

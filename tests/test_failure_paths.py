@@ -10,7 +10,7 @@ import torch
 from paper_2403_12820_gb300 import _lib
 from paper_2403_12820_gb300 import workloads as wl
 from paper_2403_12820_gb300.cloth import ClothBatch, pack
-from paper_2403_12820_gb300.net import BF16, Net
+from paper_2403_12820_gb300.net import BF16, FP32, Net
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +71,37 @@ def test_corrupted_weights_switch_every_cloth_to_the_plain_step():
     ref.set_state(x0, v0)
     ref.rollout(20)
     assert torch.equal(cb.get_state()[0], ref.get_state()[0])
+    cb.close(); ref.close(); net.close()
+
+
+@pytest.mark.parametrize("precision", [BF16, FP32])
+def test_nan_weight_switches_every_cloth_to_the_plain_step(precision):
+    """One NaN weight turns every network result NaN.  net_create refuses a
+    non-finite blob, so the NaN comes the way a diverged training run would
+    leave it: device weights given to net_set_weights (the blob is made on the
+    host).  The residual check must see a non-finite residual, not drop it,
+    switch every cloth at the first check, and leave the plain rollout bit
+    for bit."""
+    specs, pins, x0, v0 = batch()
+    h = specs[0]["h"]
+    w = wl.kaiming_blob(903, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3).astype(np.float32)
+    net = Net(w, precision)
+    w[1728 + 5] = np.nan                      # one entry of W2
+    net.set_weights(torch.from_numpy(w).cuda())
+    cb = ClothBatch(specs, pins)
+    cb.set_state(x0, v0)
+    cb.rollout_net(net, 20, check_every=5, residual_bound=1e-3)
+    mode, resid = cb.modes()
+    assert mode.cpu().tolist() == [1, 1]
+    r = resid.cpu().numpy()
+    assert np.all(~np.isfinite(r) | (r > 1e-3)), r
+    ref = ClothBatch(specs, pins)
+    ref.set_state(x0, v0)
+    ref.rollout(20)
+    x, v = cb.get_state()
+    xr, vr = ref.get_state()
+    assert torch.equal(x, xr) and torch.equal(v, vr)
+    assert bool(torch.isfinite(x).all())
     cb.close(); ref.close(); net.close()
 
 
