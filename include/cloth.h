@@ -356,8 +356,11 @@ int net_backward(cloth_net* net, const float* d_z, float* d_saved, const float* 
  * loads the library until exit); nothing is allocated.  Returns
  * CLOTH_EINVAL when N * H * W exceeds CLOTH_NET_STATIC_MAX_NODES.  The first
  * call on a device looks up the array's device address and sets kernel
- * attributes; make that first call before any stream capture.  All calls on
- * a device share the array: calls whose work overlaps on the GPU race. */
+ * attributes; make that first call before any stream capture.  Both are
+ * kept until exit, so a cudaDeviceReset after the first call on a device is
+ * not supported.  All calls on a device share the array: calls whose work
+ * overlaps on the GPU race.  On CLOTH_ECUDA, cloth_last_cuda_error gives the
+ * cudaError_t. */
 #define CLOTH_NET_STATIC_MAX_NODES 16384
 int net_forward_static(const float* d_blob, const float* d_z, float* d_a, int32_t N, int32_t H, int32_t W,
                        void* stream);

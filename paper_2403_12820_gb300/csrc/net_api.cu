@@ -51,6 +51,7 @@ bool dims_ok(int32_t N, int32_t H, int32_t W)
 
 namespace cloth {
 int net_last_cuda_error() { return g_net_cuda; }
+void net_record_cuda_error(int e) { g_net_cuda = e; }
 }
 
 extern "C" {

@@ -56,6 +56,8 @@ cudaError_t launch_net_backward_simt(const float* w, const float* z, float* save
                                      float* partials, float* gw, int N, int H, int W, cudaStream_t s);
 cudaError_t net_simt_init();
 int net_last_cuda_error();
+// Record a CUDA failure of a network entry point for cloth_last_cuda_error.
+void net_record_cuda_error(int e);
 // One column of the trunk's composite kernels (Eq. 6 folded into Eq. 7):
 // G_n W2_a W1_b[:, i] for 3x3 taps a (W2) and b (W1) and input channel i,
 // where G_n is P's row n (n < 32), WL's tap tl and output co

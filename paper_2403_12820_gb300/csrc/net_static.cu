@@ -35,28 +35,30 @@ struct DeviceScratch {
 
 std::mutex g_mu;
 DeviceScratch g_dev[64];
-thread_local int g_static_cuda = 0;
+
+// CUDA failures go where cloth_last_cuda_error reads them.
+int static_cuda_fail(cudaError_t e)
+{
+    net_record_cuda_error((int)e);
+    return CLOTH_ECUDA;
+}
 
 // Device address of the scratch on the current device, looked up (and the
 // kernels' shared-memory limits raised) the first time a device is used.
+// Both are kept for the life of the process: a cudaDeviceReset after that
+// first call would leave them stale, so it is not supported.
 int scratch_address(float** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        g_static_cuda = (int)e;
-        return CLOTH_ECUDA;
-    }
+    if (e != cudaSuccess) return static_cuda_fail(e);
     if (dev < 0 || dev >= 64) return CLOTH_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_dev[dev].ready) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_net_static_scratch);
         if (e == cudaSuccess) e = net_simt_init();
-        if (e != cudaSuccess) {
-            g_static_cuda = (int)e;
-            return CLOTH_ECUDA;
-        }
+        if (e != cudaSuccess) return static_cuda_fail(e);
         g_dev[dev].ptr = static_cast<float*>(p);
         g_dev[dev].ready = true;
     }
@@ -88,9 +90,6 @@ extern "C" int net_forward_static(const float* d_blob, const float* d_z, float* 
     f.H = H;
     f.W = W;
     const cudaError_t e = launch_net_forward_simt(f, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) {
-        g_static_cuda = (int)e;
-        return CLOTH_ECUDA;
-    }
+    if (e != cudaSuccess) return static_cuda_fail(e);
     return CLOTH_OK;
 }

@@ -82,3 +82,26 @@ def test_missing_library_and_toolchain_fail_loudly(tmp_path, monkeypatch):
         _lib.load()
     with pytest.raises(RuntimeError, match="not found"):
         _lib.load(build_if_needed=False)
+
+
+def test_static_forward_cuda_failure_is_reported_by_cloth_last_cuda_error():
+    """With no CUDA device visible, net_forward_static fails in its device
+    look-up (before any launch: the pointers are never dereferenced) and
+    cloth_last_cuda_error reports the cudaError_t.  Run in a child process
+    with CUDA_VISIBLE_DEVICES empty, so it behaves the same on a GPU machine."""
+    import subprocess
+    import sys
+    code = (
+        "import ctypes, sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_2403_12820_gb300 import _lib\n"
+        "lib = _lib.load(build_if_needed=False)\n"
+        "p = ctypes.c_void_p\n"
+        "rc = lib.net_forward_static(p(256), p(512), p(768), 1, 4, 4, p(0))\n"
+        "print(rc, lib.cloth_last_cuda_error())\n"
+    )
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    rc, err = (int(t) for t in out.stdout.split())
+    assert rc == -3 and err != 0, (rc, err)

@@ -9,6 +9,8 @@ scratch the first one left behind.  Calls beyond the static capacity are
 refused on the host.  This file is collected last on purpose.
 """
 import ctypes
+import os
+import re
 
 import numpy as np
 import pytest
@@ -21,7 +23,13 @@ from paper_2403_12820_gb300.net import FP32, Net
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
-MAX_NODES = 16384
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MAX_NODES = int(re.search(r"#define\s+CLOTH_NET_STATIC_MAX_NODES\s+(\d+)",
+                          open(os.path.join(ROOT, "include", "cloth.h")).read()).group(1))
+# the capacity exactly filled, and one row over it
+FULL = (1, 6, MAX_NODES // 128, 128)
+OVER = (1, 6, MAX_NODES // 128 + 1, 128)
+assert MAX_NODES % 128 == 0
 
 
 def _call_static(d_blob, z):
@@ -42,7 +50,7 @@ def test_static_forward_matches_net_forward_twice():
     d_blob = torch.from_numpy(blob).cuda()
     net = Net(blob, FP32)
     rng = np.random.default_rng(78)
-    for shape in [(2, 6, 40, 50), (1, 6, 128, 128)]:          # the second fills the capacity exactly
+    for shape in [(2, 6, 40, 50), FULL]:
         z = torch.from_numpy(rng.normal(0.0, 0.02, size=shape).astype(np.float32)).cuda()
         ref, _ = net.forward(z)
         rc, a = _call_static(d_blob, z)
@@ -53,6 +61,6 @@ def test_static_forward_matches_net_forward_twice():
 
 def test_static_forward_refuses_oversized_calls():
     d_blob = torch.zeros(13036, device="cuda")
-    z = torch.zeros(1, 6, 129, 128, device="cuda")             # 16512 > 16384 nodes
+    z = torch.zeros(*OVER, device="cuda")
     rc, _ = _call_static(d_blob, z)
     assert rc == -1
