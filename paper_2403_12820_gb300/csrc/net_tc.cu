@@ -78,7 +78,14 @@ __host__ __device__ constexpr int ctap_off(int c) { return (c / 5) * PT + c % 5;
 // output columns below 64 take u's channels and the others v's.
 constexpr int kBc = kPairs * 2 * kNC * 16;
 constexpr int kKE = 4 * 5 * 3 * kNC, kKC = 4 * 3 * kNC;   // floats
-constexpr int kPack = kBc + (kKE + kKC) * 4;
+// FP32 rounding defects KD [direction 2: taps (s, 2) of the x edges, taps
+// (2, s) of the y edges][tap s 5][channel 3][96]: the composite tap's FP32
+// value less its BF16 value in B.  An edge node keeps only part of the
+// composite taps on its edge column or row, so their BF16 rounding error
+// would be large against what remains (up to 9x on a 1 x 1 cloth); the edge
+// terms add the defect back once per tap, which makes those taps FP32.
+constexpr int kKD = 2 * 5 * 3 * kNC;
+constexpr int kPack = kBc + (kKE + kKC + kKD) * 4;
 static_assert(kPack % 16 == 0, "pack");
 
 // FP32 u, v of the output nodes and their 1-node halo, for the update
@@ -358,12 +365,24 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             if (n < 64) { z[0] = bf_lo(r.x); z[1] = bf_hi(r.x); z[2] = bf_lo(r.y); }
             else { z[0] = bf_hi(r.y); z[1] = bf_lo(r.z); z[2] = bf_hi(r.z); }
         };
+        const float* gKD = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc) + kKE + kKC;
 #pragma unroll 1
         for (int ed = 0; ed < 4; ++ed) {
             if (!has[ed]) continue;
-            float k[15], kc[2][3];
+            // the rounding defect of a tap is added by the first edge (in the
+            // order x = 0, x = W-1, y = 0, y = H-1) whose column or row holds
+            // it: x = W-1 leaves its column to x = 0 on a one-column cloth,
+            // y = H-1 its row to y = 0 on a one-row cloth, and a y edge leaves
+            // the centre tap to an x edge its node is on (decided per node)
+            const bool none = (ed == 1 && g.W == 1) || (ed == 3 && g.H == 1);
+            float k[15], kdc[3], kc[2][3];
 #pragma unroll
-            for (int j = 0; j < 15; ++j) k[j] = sKE[(ed * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n];
+            for (int j = 0; j < 15; ++j) {
+                const float d = none ? 0.f : __ldg(gKD + ((ed >> 1) * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n);
+                k[j] = sKE[(ed * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n];
+                if (j / 3 == 2) kdc[j % 3] = d;
+                else k[j] += d;
+            }
 #pragma unroll
             for (int yb = 0; yb < 2; ++yb)
 #pragma unroll
@@ -375,12 +394,17 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 const int y = g.y0 - 1 + ry2, x = g.x0 - 1 + rx2;
                 if (y < 0 || y >= g.H || x < 0 || x >= g.W) continue;   // not a node of the cloth
                 const int j2 = ry2 * PT + rx2;
+                const bool ctr = !(ed >= 2 && (x == 0 || x == g.W - 1));
                 float acc = 0.f;
 #pragma unroll
                 for (int s5 = 0; s5 < 5; ++s5) {   // x edges: taps along y; y edges: along x
                     float z[3];
                     z3(j2 + (ed < 2 ? s5 * PT + 2 : 2 * PT + s5), z);
-                    acc = fmaf(k[3 * s5], z[0], fmaf(k[3 * s5 + 1], z[1], fmaf(k[3 * s5 + 2], z[2], acc)));
+                    float k0 = k[3 * s5], k1 = k[3 * s5 + 1], k2 = k[3 * s5 + 2];
+                    if (s5 == 2 && ctr) {
+                        k0 += kdc[0]; k1 += kdc[1]; k2 += kdc[2];
+                    }
+                    acc = fmaf(k0, z[0], fmaf(k1, z[1], fmaf(k2, z[2], acc)));
                 }
                 if (ed < 2 && (y == 0 || y == g.H - 1)) {   // corners (ay, ax): k4 = 2 (ay / 2) + ax / 2
                     float z[3];
@@ -616,30 +640,50 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// Composite tap (cy, cx) of output column n and input slot e in FP32: the
+// sum over a + b = c of the layer products, in one fixed order (the B
+// operand and the rounding defects both come from it).
+__device__ float composite_tap(const float* __restrict__ w, int n, int e, int cy, int cx)
+{
+    float v = 0.f;
+    for (int ay = 0; ay < 3; ++ay)
+        for (int ax = 0; ax < 3; ++ax) {
+            const int by = cy - ay, bx = cx - ax;
+            if (by >= 0 && by < 3 && bx >= 0 && bx < 3) v += trunk_composite(w, n, e, 3 * ay + ax, 3 * by + bx);
+        }
+    return v;
+}
+
 // The composite operands from the FP32 blob, one thread per value (the
 // algebra is trunk_composite).
 __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict__ out)
 {
     constexpr int nB = kPairs * 2 * kNC * 8;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nB + kKE + kKC) return;
+    if (r >= nB + kKE + kKC + kKD) return;
     auto tap = [](int y, int x) { return 3 * y + x; };
     if (r < nB) {   // B: tap pair p, the pair's first (kh 0) or second tap, column n, input slot e
         const int e = r % 8, n = (r / 8) % kNC, kh = (r / (8 * kNC)) % 2, p = r / (16 * kNC);
         const int c = 2 * p + kh, cy = c / 5, cx = c % 5;
         float v = 0.f;
         const bool u_col = n < 59 && e < 3, v_col = n >= 64 && e >= 3 && e < 6;
-        if (c < 25 && (u_col || v_col))
-            for (int ay = 0; ay < 3; ++ay)
-                for (int ax = 0; ax < 3; ++ax) {
-                    const int by = cy - ay, bx = cx - ax;
-                    if (by >= 0 && by < 3 && bx >= 0 && bx < 3) v += trunk_composite(w, n, e, tap(ay, ax), tap(by, bx));
-                }
+        if (c < 25 && (u_col || v_col)) v = composite_tap(w, n, e, cy, cx);
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         reinterpret_cast<__nv_bfloat16*>(out)[r] = h;
         return;
     }
     float* fo = reinterpret_cast<float*>(out + kBc);
+    if (r >= nB + kKE + kKC) {   // KD: direction dir, tap s, channel ch, column n
+        const int q3 = r - nB - kKE - kKC;
+        const int n = q3 % kNC, ch = (q3 / kNC) % 3, s5 = (q3 / (3 * kNC)) % 5, dir = q3 / (15 * kNC);
+        float d = 0.f;
+        if (n < 59 || n >= 64) {
+            const float v = composite_tap(w, n, n < 64 ? ch : 3 + ch, dir == 0 ? s5 : 2, dir == 0 ? 2 : s5);
+            d = v - __bfloat162float(__float2bfloat16_rn(v));
+        }
+        fo[kKE + kKC + q3] = d;
+        return;
+    }
     const int q = r - nB;
     if (q < kKE) {   // edge ed, tap s along the edge, channel ch, column n
         const int n = q % kNC, ch = (q / kNC) % 3, s = (q / (3 * kNC)) % 5, ed = q / (15 * kNC);
@@ -689,7 +733,7 @@ cudaError_t net_tc_init()
 
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 {
-    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC;
+    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC + kKD;
     pack_tc_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, static_cast<uint8_t*>(wpack));
     return cudaGetLastError();
 }
