@@ -8,13 +8,18 @@ trajectories.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import torch
 
-from . import stages
+from . import shard, stages
 from . import workloads as wl
 from .cloth import ClothBatch, pack
-from .net import FP32, N_BLOB, N_PARAMS, Net, adam_step
+from .net import BF16, FP32, N_BLOB, N_PARAMS, Net, adam_step
+
+# blob offsets of the linear branch's bias
+_OFF_BL = 11808
 
 
 class Dataset:
@@ -38,6 +43,52 @@ class Dataset:
             sim.get_state(self.x[t], self.v[t])
         sim.close()
         self.nodes = self.n * self.n
+        self.device = device
+
+    def stats(self) -> dict:
+        """Scales of the recorded data over the unpinned nodes of every step:
+        root mean square of u = x - X and of v per coordinate, and mean and
+        standard deviation per coordinate of the acceleration
+        (v[t+1] - v[t]) / dt (which includes the small pressure term)."""
+        d = self.device
+        specs = self.cfg["specs"]
+        n, h, dt = self.n, float(specs[0]["h"]), float(specs[0]["dt"])
+        X = torch.zeros(n, n, 3, device=d, dtype=torch.float64)
+        X[..., 0] = torch.arange(n, device=d, dtype=torch.float64)[None, :] * h
+        X[..., 1] = torch.arange(n, device=d, dtype=torch.float64)[:, None] * h
+        free = torch.ones(self.count, n * n, device=d, dtype=torch.float64)
+        for b, pl in enumerate(self.cfg["pins"]):
+            if len(pl):
+                free[b, torch.as_tensor(list(pl), device=d)] = 0.0
+        free = free.reshape(1, -1, 1)
+        cnt = float(free.sum()) * self.steps
+        su = torch.zeros(3, device=d, dtype=torch.float64)
+        sv, sa, sa2 = torch.zeros_like(su), torch.zeros_like(su), torch.zeros_like(su)
+        Xp = X.reshape(1, -1, 3).repeat(1, self.count, 1)
+        for t0 in range(0, self.steps, 25):          # in slices: the recording is large
+            t1 = min(self.steps, t0 + 25)
+            x = self.x[t0:t1].double()
+            v = self.v[t0:t1].double()
+            a = (self.v[t0 + 1:t1 + 1].double() - v) / dt
+            su += (((x - Xp) ** 2) * free).sum((0, 1))
+            sv += ((v ** 2) * free).sum((0, 1))
+            sa += (a * free).sum((0, 1))
+            sa2 += ((a ** 2) * free).sum((0, 1))
+        mean_a = sa / cnt
+        return {"rms_u": (su / cnt).sqrt().tolist(), "rms_v": (sv / cnt).sqrt().tolist(),
+                "mean_a": mean_a.tolist(), "std_a": (sa2 / cnt - mean_a ** 2).clamp_min(0).sqrt().tolist()}
+
+
+def data_scaled_blob(stats: dict, seed: int = 2004) -> np.ndarray:
+    """Initial C-cell weights scaled to the data (the input and output scales
+    of the blob are free to be set from data statistics): in_scale = 1 / rms
+    of u and v per coordinate, out_scale = the acceleration's standard
+    deviation, b_L = its mean / out_scale, the other weights Kaiming (seed)."""
+    ins = [1.0 / max(s, 1e-12) for s in stats["rms_u"]] + [1.0 / max(s, 1e-12) for s in stats["rms_v"]]
+    outs = [max(s, 1e-6) for s in stats["std_a"]]
+    blob = wl.kaiming_blob(seed, in_scale=ins, out_scale=outs)
+    blob[_OFF_BL:_OFF_BL + 3] = np.asarray(stats["mean_a"]) / np.asarray(outs)
+    return blob.astype(np.float32)
 
 
 class Trainer:
@@ -48,11 +99,17 @@ class Trainer:
     stages.CosineLR) replaces the constant lr; `trainable` (group names of
     stages.mask_groups) freezes every other group (branch-wise fine-tuning).
     `stride` k > 1 trains a larger-step cell: each network step spans k plain
-    steps, so the window's targets are k plain steps apart."""
+    steps, so the window's targets are k plain steps apart.  Without `blob`
+    the C-cell starts from data_scaled_blob of the dataset's statistics
+    (init="data") or from Kaiming weights with input scales 1 / h and 1 s/m
+    and output scale g (init="unit").  Under torch.distributed (`group`, or
+    the default group once one is set up) every rank samples its own windows
+    (seed + rank) and the gradients are averaged over the ranks before the
+    identical Adam step."""
 
     def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
                  alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn", lr_schedule=None,
-                 trainable=None, stride: int = 1):
+                 trainable=None, stride: int = 1, init: str = "data", group=None):
         if cell not in ("cnn", "pcell"):
             raise ValueError("cell must be 'cnn' or 'pcell'")
         if stride < 1 or unroll * stride > data.steps:
@@ -60,11 +117,20 @@ class Trainer:
         self.stride = int(stride)
         self.data, self.batch, self.unroll, self.lr, self.alpha = data, batch, unroll, lr, alpha
         self.cell = cell
-        self.rng = np.random.default_rng(seed)
+        import torch.distributed as dist
+        self.group = group
+        self.rank = dist.get_rank(group) if dist.is_available() and dist.is_initialized() else 0
+        self.rng = np.random.default_rng(seed + self.rank)
         h = data.cfg["specs"][0]["h"]
+        if init not in ("data", "unit"):
+            raise ValueError("init must be 'data' or 'unit'")
         if blob is None:
-            blob = (wl.kaiming_blob(2004, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
-                    if cell == "cnn" else wl.pcell_blob(2006, h=h))
+            if cell == "pcell":
+                blob = wl.pcell_blob(2006, h=h)
+            elif init == "data":
+                blob = data_scaled_blob(data.stats())
+            else:
+                blob = wl.kaiming_blob(2004, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
         self.w = torch.from_numpy(np.asarray(blob, dtype=np.float32)).to(device)
         self.n_params = N_PARAMS if cell == "cnn" else 39
         self.m = torch.zeros(self.n_params, device=device)
@@ -154,6 +220,154 @@ class Trainer:
             loss, g = cb.train_loss_pcell(self.w, self.unroll, tg, alpha=self.alpha)
         lr = self.lr_at(self.t)
         self.t += 1
+        shard.average_gradient(g, self.batch, self.group)
         adam_step(self.w, g, self.m, self.v, self.t, lr=lr, n=self.n_params, mask=self.mask)
         cb.close()
         return float(loss.item())
+
+
+# ------------------------------------------------------------- trained weights
+DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+TRAINED = os.path.join(DATA_DIR, "cnn_config4.npy")
+
+
+def load_trained(path: str = TRAINED):
+    """The committed C-cell weights of the training run (a float32 blob of
+    13,036 values), or None when the file is absent."""
+    if not os.path.exists(path):
+        return None
+    w = np.load(path).astype(np.float32)
+    if w.shape != (N_BLOB,) or not np.all(np.isfinite(w)):
+        raise ValueError(f"{path} is not a finite C-cell weight blob")
+    return w
+
+
+def gravity_only_blob(g=wl.G_DEFAULT) -> np.ndarray:
+    """The zero network: every weight 0, b_L = g, unit scales, so a = g
+    (free fall; the step still adds pressure, pins and contact)."""
+    w = np.zeros(N_BLOB, dtype=np.float32)
+    w[_OFF_BL:_OFF_BL + 3] = g
+    w[N_PARAMS:] = 1.0
+    return w
+
+
+def evaluate(blobs: dict, cfg: dict, warm: int = 100, steps: int = 100, device="cuda") -> dict:
+    """Accuracy of network rollouts against the plain step (Table 2's error):
+    the cloths of `cfg` are first stepped `warm` plain steps, then each
+    network of `blobs` ({name: (blob, precision)}) and the plain step run
+    `steps` steps from that state.  Per network: the mean over nodes of
+    |x_net - x_plain| / cloth width, and that error over the plain rollout's
+    mean node displacement.  Also the displacement itself (relative to
+    width)."""
+    specs, pins = cfg["specs"], cfg["pins"]
+    cb = ClothBatch(specs, pins, device=device)
+    cb.set_state(pack(cfg["x"]).to(device), pack(cfg["v"]).to(device))
+    cb.rollout(warm, graph_chunk=warm)
+    x0, v0 = cb.get_state()
+    cb.rollout(steps, graph_chunk=steps)
+    xp, _ = cb.get_state()
+    widths = torch.tensor([(s["cols"] - 1) * s["h"] for s in specs], device=device, dtype=torch.float64)
+
+    def per_cloth(a, b):
+        return torch.stack([(p - q).double().norm(dim=1).mean() for p, q in zip(cb.split(a), cb.split(b))])
+
+    disp = per_cloth(xp, x0)
+    out = {"warm_steps": warm, "steps": steps, "displacement_rel_width": float((disp / widths).mean())}
+    for name, (blob, prec) in blobs.items():
+        net = Net(blob, prec, device=device)
+        cn = ClothBatch(specs, pins, device=device)
+        cn.set_state(x0, v0)
+        cn.step_net(net, steps)
+        xn, _ = cn.get_state()
+        e = per_cloth(xn, xp)
+        out[name] = {"error_rel_width": float((e / widths).mean()), "error_rel_displacement": float((e / disp).mean()),
+                     "finite": bool(torch.isfinite(xn).all()), "status_word": cn.status()}
+        cn.close()
+        net.close()
+    cb.close()
+    return out
+
+
+def main(argv=None) -> int:
+    """Train the C-cell on the plain-simulator trajectories (512 cloths of
+    64 x 64 x 200 steps, batch 64 windows, 8-step unroll, Adam from lr 1e-3
+    with cosine annealing), checkpointing as it goes, then save the weights
+    and a JSON record (losses, timing, held-out accuracy) beside them."""
+    import argparse
+    import json
+    import time
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2403_12820_gb300.train")
+    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-min", type=float, default=1e-5)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--unroll", type=int, default=8)
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--seed", type=int, default=1004)
+    ap.add_argument("--out", default=TRAINED)
+    ap.add_argument("--checkpoint", default=None, help="checkpoint file (default: <out>.ckpt.npz)")
+    ap.add_argument("--checkpoint-every", type=int, default=500)
+    ap.add_argument("--resume", action="store_true")
+    ap.add_argument("--log-every", type=int, default=100)
+    ap.add_argument("--eval-count", type=int, default=8, help="held-out 128 x 128 cloths for the accuracy check")
+    a = ap.parse_args(argv)
+
+    import torch.distributed as dist
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and not dist.is_initialized():
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    rank = dist.get_rank() if dist.is_initialized() else 0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ckpt = a.checkpoint or a.out + ".ckpt.npz"
+    t0 = time.perf_counter()
+    data = Dataset(count=a.count, n=a.n, steps=a.steps, seed=a.seed, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    stats = data.stats()
+    tr = Trainer(data, batch=a.batch, unroll=a.unroll, lr=a.lr, device=dev,
+                 lr_schedule=stages.CosineLR(a.lr, a.lr_min, a.iters))
+    if a.resume and os.path.exists(ckpt):
+        tr.load(ckpt)
+    log = []
+    t1 = time.perf_counter()
+    while tr.t < a.iters:
+        loss = tr.step()
+        if not np.isfinite(loss):
+            raise RuntimeError(f"training diverged at iteration {tr.t}: loss {loss}")
+        if tr.t % a.log_every == 0 or tr.t == 1 or tr.t == a.iters:
+            log.append((tr.t, loss))
+            if rank == 0:
+                print(f"iter {tr.t} loss {loss:.5g} lr {tr.lr_at(tr.t - 1):.3g}", flush=True)
+        if rank == 0 and a.checkpoint_every > 0 and tr.t % a.checkpoint_every == 0:
+            tr.save(ckpt)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    if rank != 0:
+        return 0
+    w = tr.w.detach().cpu().numpy().astype(np.float32)
+    g = data.cfg["specs"][0]["g"]
+    ev = evaluate({"trained_fp32": (w, FP32), "trained_bf16": (w, BF16), "gravity_only": (gravity_only_blob(g), FP32)},
+                  wl.cnn_batch(count=a.eval_count), device=dev)
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    np.save(a.out, w)
+    import sys
+    rec = {"command": "python -m paper_2403_12820_gb300.train " + " ".join(sys.argv[1:] if argv is None else argv),
+           "workload": f"{a.count} trajectories of {a.n} x {a.n} x {a.steps} plain steps (seed {a.seed}); batch "
+                       f"{a.batch} windows, {a.unroll}-step unroll, Adam lr {a.lr} cosine to {a.lr_min}, "
+                       f"{a.iters} iterations, alpha 0.5",
+           "iterations": tr.t, "dataset_generation_s": gen_s, "train_s": train_s,
+           "iters_per_s": a.iters / max(train_s, 1e-9), "loss_log": log, "data_stats": stats,
+           "world_size": dist.get_world_size() if dist.is_initialized() else 1,
+           "held_out": dict(ev, workload=f"cnn_batch seed 1003, {a.eval_count} cloths of 128 x 128, "
+                                         "after 100 plain steps")}
+    with open(os.path.splitext(a.out)[0] + ".json", "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(rec["held_out"]), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

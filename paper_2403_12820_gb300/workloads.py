@@ -11,7 +11,7 @@ and its falling / pinned / pressure / ball scenes, Sec. 3.2.2):
   single_cloth   32x32 cloth, two top corners pinned, Gaussian noise 1e-4 m
   plain_batch    64 cloths, sides U{64..512}, k x U(0.8, 1.2), 1-4 pinned
                  boundary nodes, pressure ~ N(0, 0.5) N/m^2 per cloth
-  cnn_batch      32 cloths of 128x128 with smooth sag + noise states
+  cnn_batch      32 cloths of 128x128 drawn like plain_batch
   train_set      cloths of 64x64 (random pins, pressure, k scale)
   mixed_batch    16 cloths, sides U{256..1024}, sphere below each cloth
 """
@@ -129,14 +129,12 @@ def sag_state(spec: dict, rng: np.random.Generator, amp: float = 0.05, vamp: flo
 
 
 def cnn_batch(seed: int = 1003, count: int = 32, n: int = 128, steps: int = 1000) -> dict:
-    """Batch of 128x128 cloths in deformed, moving states, pressure ~ N(0, 0.5)."""
-    rng = np.random.default_rng(seed)
-    specs, pins, xs, vs = [], [], [], []
-    for _ in range(count):
-        spec = cloth_spec(n, n, p=rng.normal(0.0, 0.5))
-        x, v = sag_state(spec, rng)
-        specs.append(spec); pins.append([]); xs.append(x); vs.append(v)
-    return {"specs": specs, "pins": pins, "x": xs, "v": vs, "steps": steps}
+    """Batch of 128x128 cloths drawn like the plain batch (flat + 1e-4 m
+    noise, 1-4 pinned boundary nodes, pressure ~ N(0, 0.5), stiffness x
+    U(0.8, 1.2)), so that after a few plain steps their states look like the
+    training trajectories; the network workload starts from the state after
+    100 plain steps (the caller steps them)."""
+    return plain_batch(seed=seed, count=count, side_lo=n, side_hi=n, steps=steps)
 
 
 def mixed_batch(seed: int = 1005, count: int = 16, side_lo: int = 256, side_hi: int = 1024,
