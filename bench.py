@@ -49,14 +49,16 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cnn", action="store_true")
-    p.add_argument("--cnn-steps", type=int, default=200)
+    p.add_argument("--cnn-steps", type=int, default=1000)
     p.add_argument("--no-mixed", action="store_true")
-    p.add_argument("--mixed-steps", type=int, default=400)
+    p.add_argument("--mixed-steps", type=int, default=5000)
     p.add_argument("--no-train", action="store_true")
     p.add_argument("--no-pcell", action="store_true")
     p.add_argument("--no-larger-step", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
     p.add_argument("--de-generations", type=int, default=6)
+    p.add_argument("--only", choices=["cnn", "mixed", "pcell", "larger_step", "train", "single_cloth"], default=None,
+                   help="run one section alone and print its JSON (for profiling; not a bench line)")
     return p.parse_args(argv)
 
 
@@ -271,10 +273,16 @@ def run_plain(args, rank, world, local):
     import numpy as np
     import torch
 
+    from paper_2403_12820_gb300 import shard
     from paper_2403_12820_gb300 import workloads as wl
     from paper_2403_12820_gb300.cloth import ClothBatch, pack
 
-    cfg = wl.plain_batch()
+    # one batch of 64 cloths per rank (weak scaling), split over the ranks by
+    # whole cloths, largest first (no data-path communication)
+    cfg = wl.plain_batch(count=64 * world)
+    job_nodes = sum(s["rows"] * s["cols"] for s in cfg["specs"])
+    if world > 1:
+        cfg = shard.take(cfg, shard.partition([s["rows"] * s["cols"] for s in cfg["specs"]], world)[rank])
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
@@ -314,7 +322,7 @@ def run_plain(args, rank, world, local):
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world)
     status = cb.status()
-    value = world * nodes * args.steps / (ms_max / 1e3)
+    value = job_nodes * args.steps / (ms_max / 1e3)
 
     hbm, _, peak_kind = peaks()
     launch_s = ms / 1e3 / args.steps          # one plain-step kernel per step
@@ -327,8 +335,9 @@ def run_plain(args, rank, world, local):
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "plain_batch: 64 cloths, sides U{64..512} (seed 1002), 5.97M nodes, FP32, "
-                               f"CUDA graphs of {chunk} steps",
-                   "global_batch": 64 * world, "nodes_per_gpu": nodes, "launch": launch,
+                               f"CUDA graphs of {chunk} steps"
+                               + (f"; {64 * world} cloths split over {world} ranks largest first" if world > 1 else ""),
+                   "global_batch": 64 * world, "nodes_per_gpu": nodes, "job_nodes": job_nodes, "launch": launch,
                    "l2": "inputs larger than L2 (306 MB double-buffered state vs 129 MB L2)"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth)", "traffic": traffic,
@@ -363,7 +372,7 @@ def run_plain(args, rank, world, local):
             hout.copy_(xo, non_blocking=True)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, world)
-        out["e2e"] = {"value": world * nodes * per_call * calls / el, "unit": "node-steps/s",
+        out["e2e"] = {"value": job_nodes * per_call * calls / el, "unit": "node-steps/s",
                       "h2d_bytes_per_step": (hx.numel() + hv.numel()) * 4 / per_call,
                       "d2h_bytes_per_step": hout.numel() * 4 / per_call,
                       "steps_per_call": per_call, "calls": calls}
@@ -399,22 +408,37 @@ def cnn_blob(h: float):
     return wl.kaiming_blob(2003, in_scale=(1.0 / h,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3)
 
 
+def network_blob(h: float):
+    """The trained C-cell weights committed with the package (the training
+    run on the plain-simulator trajectories), else Kaiming weights; and
+    whether they are the trained ones."""
+    from paper_2403_12820_gb300.train import load_trained
+    w = load_trained()
+    return (w, True) if w is not None else (cnn_blob(h), False)
+
+
 def run_cnn(args, dev):
-    """Network step (Fig. 2) on 32 cloths of 128 x 128: node-steps/s of the
-    BF16 tensor-core step and of the FP32 CUDA-core step, the ratio to the
-    plain step on the same cloths, and the mean node-position error relative
-    to cloth width after 100 steps (Table 2's error)."""
+    """Network step (Fig. 2) on 32 cloths of 128 x 128 drawn like the plain
+    batch, from their state after 100 plain steps: node-steps/s of the BF16
+    tensor-core step and of the FP32 CUDA-core step (trained weights), the
+    ratio to the plain step on the same cloths, and the accuracy after 100
+    steps against the plain step (Table 2's error: mean node distance over
+    cloth width, and over the plain rollout's mean displacement) beside the
+    gravity-only network (a = g) and the untrained Kaiming network."""
     import torch
 
     from paper_2403_12820_gb300 import workloads as wl
     from paper_2403_12820_gb300.cloth import ClothBatch, pack
     from paper_2403_12820_gb300.net import BF16, FP32, Net
+    from paper_2403_12820_gb300.train import evaluate, gravity_only_blob
 
     cfg = wl.cnn_batch()
     h = cfg["specs"][0]["h"]
-    blob = cnn_blob(h)
-    x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
+    blob, trained = network_blob(h)
     cp = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cp.set_state(pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev))
+    cp.rollout(100, graph_chunk=100)
+    x0, v0 = cp.get_state()
     nodes = cp.total_nodes
     stream = torch.cuda.current_stream()
 
@@ -431,30 +455,49 @@ def run_cnn(args, dev):
     cp.rollout(10, graph_chunk=10)
     t_plain = timed(lambda k: cp.rollout(k, graph_chunk=100), 10 * args.cnn_steps)
     plain_rate = nodes * 10 * args.cnn_steps / t_plain
-    cp.set_state(x0, v0)
-    cp.step(100)
-    xp, _ = cp.get_state()
-    w = (cfg["specs"][0]["cols"] - 1) * h
-    disp = (xp - x0).norm(dim=1).mean().item()
     _, bf16_peak, peak_kind = peaks()
-    out = {"workload": "cnn_batch: 32 cloths of 128 x 128 (524,288 nodes), Kaiming weights (seed 2003)",
-           "plain_same_cloths": plain_rate}
-    for name, prec, steps in (("bf16", BF16, args.cnn_steps), ("f32", FP32, max(1, args.cnn_steps // 10))):
+    acc = evaluate({"bf16": (blob, BF16), "f32": (blob, FP32), "gravity_only": (gravity_only_blob(), FP32),
+                    "untrained_kaiming_bf16": (cnn_blob(h), BF16)}, cfg, warm=100, steps=100, device=dev,
+                   horizons=(300, 1000))
+    zero = acc["gravity_only"]["error_rel_width"]
+    out = {"workload": "cnn_batch: 32 cloths of 128 x 128 (524,288 nodes) drawn like the plain batch (seed 1003), "
+                       f"from their state after 100 plain steps; {'trained' if trained else 'Kaiming'} weights",
+           "trained": trained, "plain_same_cloths": plain_rate,
+           "accuracy_100_steps": {"displacement_rel_width": acc["displacement_rel_width"],
+                                  "gravity_only_error_rel_width": zero,
+                                  "gravity_only_error_rel_displacement": acc["gravity_only"]["error_rel_displacement"],
+                                  "untrained_kaiming_bf16_error_rel_width":
+                                      acc["untrained_kaiming_bf16"]["error_rel_width"]}}
+    def timed_segments(cn, fn, steps):
+        """`steps` network steps as segments of 100 from the start state (a
+        network rollout leaves the physical states after some hundreds of
+        steps); CUDA events around each segment only."""
+        total, left = 0.0, steps
+        while left > 0:
+            k = min(100, left)
+            cn.set_state(x0, v0)
+            total += timed(fn, k)
+            left -= k
+        return total
+
+    for name, prec in (("bf16", BF16), ("f32", FP32)):
         net = Net(blob, prec, device=dev)
         cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
         cn.set_state(x0, v0)
         cn.step_net(net, 3)
-        t = timed(lambda k: cn.step_net(net, k), steps)
+        steps = args.cnn_steps
+        t = timed_segments(cn, lambda k: cn.step_net(net, k), steps)
         rate = nodes * steps / t
-        cn.set_state(x0, v0)
-        cn.step_net(net, 100)
-        xn, _ = cn.get_state()
-        err = (xn - xp).norm(dim=1).mean().item()
         tflops = CNN_FLOP_PER_NODE * rate / 1e12
+        e = acc[name]
         out[name] = {"value": rate, "unit": "node-steps/s", "steps": steps, "ms_per_step": t / steps * 1e3,
-                     "ratio_to_plain": rate / plain_rate, "error_100_steps_rel_width": err / w,
-                     "error_100_steps_rel_displacement": err / max(disp, 1e-30), "achieved_tflops": tflops,
-                     "gpu_launches_per_step": 1 if prec == BF16 else 4, "status_word": cn.status()}
+                     "ratio_to_plain": rate / plain_rate, "error_100_steps_rel_width": e["error_rel_width"],
+                     "error_100_steps_rel_displacement": e["error_rel_displacement"],
+                     "error_rel_width_at_steps": e.get("horizon_errors"),
+                     "beats_gravity_only": e["error_rel_width"] < zero,
+                     "within_1pct_of_width": e["error_rel_width"] <= 0.01,
+                     "achieved_tflops": tflops, "gpu_launches_per_step": 1, "timed_as": "segments of 100 steps",
+                     "status_word": cn.status()}
         if prec == BF16:
             out[name]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                                      "frac": tflops / bf16_peak, "peak_kind": f"{peak_kind} (cuBLAS bf16 burst)",
@@ -463,12 +506,16 @@ def run_cnn(args, dev):
         net.close()
     # larger-step network: stride 4 (dt_net = 4 dt), 25 network steps cover the
     # simulated time of the 100 plain steps the error is taken against
+    cp.set_state(x0, v0)
+    cp.rollout(100, graph_chunk=100)
+    xp, _ = cp.get_state()
+    w = (cfg["specs"][0]["cols"] - 1) * h
     net = Net(blob, BF16, device=dev)
     cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cn.set_net_stride(4)
     cn.set_state(x0, v0)
     cn.step_net(net, 3)
-    t = timed(lambda k: cn.step_net(net, k), args.cnn_steps)
+    t = timed_segments(cn, lambda k: cn.step_net(net, k), args.cnn_steps)
     rate = nodes * args.cnn_steps / t
     cn.set_state(x0, v0)
     cn.step_net(net, 25)
@@ -476,7 +523,8 @@ def run_cnn(args, dev):
     err = (xn - xp).norm(dim=1).mean().item()
     out["bf16_stride4"] = {"value": rate, "unit": "node-steps/s (network steps of 4 dt)",
                            "plain_equivalent_node_steps_per_s": 4 * rate, "ratio_to_plain_equivalent": 4 * rate / plain_rate,
-                           "error_100_plain_steps_rel_width": err / w, "status_word": cn.status()}
+                           "error_100_plain_steps_rel_width": err / w, "status_word": cn.status(),
+                           "note": "weights trained for steps of dt, run at 4 dt"}
     cn.close()
     net.close()
     cp.close()
@@ -485,11 +533,13 @@ def run_cnn(args, dev):
 
 def run_mixed(args, dev):
     """Large mixed batch with the plain-step fallback: 16 cloths with sides
-    U{256..1024} over a sphere, BF16 network rollout captured in CUDA graphs,
-    every 10th step judged by one plain step from the same state; a cloth
-    whose largest node difference exceeds 1e-3 m switches to the plain step.
-    Reports node-steps/s of the checked rollout, of the unchecked network
-    rollout and of the plain rollout on the same cloths."""
+    U{256..1024} falling onto a sphere, the BF16 network rollout (trained
+    weights) captured in CUDA graphs, every 10th step judged by one plain
+    step from the same state; a cloth whose largest node difference exceeds
+    1e-3 m switches to the plain step.  Reports node-steps/s of the checked
+    rollout over the configured 5000 steps and how many cloths switched, and
+    (over 1000 steps) the unchecked network rollout and the plain rollout on
+    the same cloths."""
     import torch
 
     from paper_2403_12820_gb300 import workloads as wl
@@ -501,11 +551,13 @@ def run_mixed(args, dev):
     x0, v0 = pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev)
     cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     nodes = cb.total_nodes
-    net = Net(cnn_blob(h), BF16, device=dev)
+    blob, trained = network_blob(h)
+    net = Net(blob, BF16, device=dev)
     stream = torch.cuda.current_stream()
     steps = max(100, args.mixed_steps // 100 * 100)
+    side = min(steps, 1000)
 
-    def timed(fn):
+    def timed(fn, n):
         cb.set_state(x0, v0)
         cb.reset_modes()
         fn(100)                       # warm-up, graph capture
@@ -514,28 +566,41 @@ def run_mixed(args, dev):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        fn(steps)
+        fn(n)
         e1.record(stream)
         torch.cuda.synchronize()
-        return nodes * steps / (e0.elapsed_time(e1) / 1e3)
+        return nodes * n / (e0.elapsed_time(e1) / 1e3)
 
-    checked = timed(lambda k: cb.rollout_net(net, k, check_every=10, residual_bound=1e-3, graph_chunk=100))
+    checked = timed(lambda k: cb.rollout_net(net, k, check_every=10, residual_bound=1e-3, graph_chunk=100), steps)
     mode, resid = cb.modes()
     status = cb.status()
-    unchecked = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100))
-    plain = timed(lambda k: cb.rollout(k, graph_chunk=100))
+    xc, _ = cb.get_state()
+    finite = bool(torch.isfinite(xc).all())
+    # the same checked rollout again, untimed, in pieces of 500 steps: how
+    # many cloths had switched to the plain step by then
+    cb.set_state(x0, v0)
+    cb.reset_modes()
+    switched_by = {}
+    for k in range(500, steps + 1, 500):
+        cb.rollout_net(net, 500, check_every=10, residual_bound=1e-3, graph_chunk=100)
+        switched_by[str(k)] = int(cb.modes()[0].sum().item())
+    unchecked = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100), side)
+    plain = timed(lambda k: cb.rollout(k, graph_chunk=100), side)
     # the same rollouts with Coulomb contact (mu 0.3) in place of the
     # stopping contact, selected at run time (same graphs; this batch has no pins)
     for b in range(cb.B):
         cb.set_boundary(b, (0.0, 0.0, 0.0), 0.3)
-    friction_net = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100))
-    friction_plain = timed(lambda k: cb.rollout(k, graph_chunk=100))
+    friction_net = timed(lambda k: cb.rollout_net(net, k, graph_chunk=100), side)
+    friction_plain = timed(lambda k: cb.rollout(k, graph_chunk=100), side)
     out = {"workload": f"mixed_batch: 16 cloths, sides U{{256..1024}} (seed 1005), {nodes / 1e6:.2f}M nodes, "
-                       "sphere R = 0.3 w, BF16 network (Kaiming weights, seed 2003), FP32 state",
+                       f"sphere R = 0.3 w, BF16 network ({'trained' if trained else 'Kaiming'} weights), FP32 state",
+           "trained": trained,
            "value": checked, "unit": "node-steps/s", "steps": steps, "check_every": 10, "residual_bound_m": 1e-3,
-           "graph_chunk": 100, "switched_to_plain": int(mode.sum().item()),
-           "largest_residual_m": float(resid.max().item()), "network_unchecked": unchecked,
-           "plain_same_cloths": plain, "ratio_to_plain": checked / plain, "status_word": status,
+           "graph_chunk": 100, "switched_to_plain": int(mode.sum().item()), "cloths": cb.B,
+           "switched_by_step": switched_by,
+           "largest_residual_m": float(resid.max().item()), "state_finite": finite,
+           "network_unchecked": unchecked, "plain_same_cloths": plain, "ratio_to_plain": checked / plain,
+           "side_rollout_steps": side, "status_word": status,
            "coulomb_contact": {"network_unchecked": friction_net, "plain": friction_plain, "friction": 0.3},
            "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
     net.close()
@@ -629,7 +694,7 @@ def run_larger_step(args, dev, plain_rate: float):
     moving_rate = nodes * 1000 / t_mv
     for b in range(cb.B):
         cb.set_boundary(b, (0.0, 0.0, 0.0), -1.0)
-    net = Net(cnn_blob(cfg["specs"][0]["h"]), BF16, device=dev)
+    net = Net(network_blob(cfg["specs"][0]["h"])[0], BF16, device=dev)
     cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cn.set_net_stride(k)
     cn.set_state(x0, v0)
@@ -757,6 +822,16 @@ def main(argv=None):
         out = run_reference(args, rank, int(os.environ.get("WORLD_SIZE", "1")))
         if out is not None:
             print(json.dumps(out), flush=True)
+        return 0
+    if args.only is not None:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        fn = {"cnn": lambda: run_cnn(args, dev), "mixed": lambda: run_mixed(args, dev),
+              "pcell": lambda: run_pcell(args, dev, float("nan")),
+              "larger_step": lambda: run_larger_step(args, dev, float("nan")),
+              "train": lambda: run_train(args, dev), "single_cloth": lambda: run_single_cloth(dev)}[args.only]
+        print(json.dumps({"section": args.only, "result": fn()}), flush=True)
         return 0
     rank, world, local = dist_setup(args.gpus)
     out = run_plain(args, rank, world, local)

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -112,6 +113,11 @@ struct cloth_ctx {
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (chunk, start buffer) -> graph
+    // checked network rollouts: (network, its workspace, precision, rollout
+    // workspace and size, chunk, check period, residual bound bits, start
+    // buffer) -> graph
+    using NetGraphKey = std::tuple<const void*, const void*, int, const void*, size_t, int, int, uint32_t, int>;
+    std::map<NetGraphKey, cudaGraphExec_t> net_graphs;
     std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
     std::vector<int32_t> impl_blk;     // implicit step: first block of each cloth, then the total
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
@@ -129,6 +135,16 @@ struct cloth_ctx {
 };
 
 namespace {
+
+// Forget every cached rollout graph (the launch shape or the stride changed,
+// or the context goes away).
+void drop_graphs(cloth_ctx* c)
+{
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    for (auto& kv : c->net_graphs) cudaGraphExecDestroy(kv.second);
+    c->net_graphs.clear();
+}
 
 // Build and upload the work list of the plain step; every warp of the
 // launch runs a contiguous range of it.
@@ -655,26 +671,33 @@ int cloth_rollout_net(cloth_ctx* c, const cloth_net* net, const cloth_net_rollou
     }
     int done = 0;
     if (chunk > 0 && o->steps >= chunk) {
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
-        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        const int cur0 = c->cur;
-        int r = CLOTH_OK;
-        for (int i = 0; i < chunk && r == CLOTH_OK; ++i) r = one_step(i, c->cap);
-        const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
-        c->cur = cur0;
-        if (r) { if (g) cudaGraphDestroy(g); return r; }
-        if (e != cudaSuccess) return cuda_fail(e);
-        const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
-        cudaGraphDestroy(g);
-        if (e2 != cudaSuccess) return cuda_fail(e2);
-        cudaError_t e3 = cudaSuccess;
-        while (o->steps - done >= chunk && e3 == cudaSuccess) {
-            e3 = cudaGraphLaunch(ge, s);
-            done += chunk;
+        // the graph is kept for later calls with the same network,
+        // workspace, chunk, check period, bound and start buffer (the tile
+        // list written above is the same for them)
+        uint32_t bound_bits = 0;
+        std::memcpy(&bound_bits, &o->residual_bound, sizeof(bound_bits));
+        const cloth_ctx::NetGraphKey key{net, net->ws, net->precision, d_work, bytes, chunk, ce, bound_bits, c->cur};
+        auto it = c->net_graphs.find(key);
+        if (it == c->net_graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            const int cur0 = c->cur;
+            int r = CLOTH_OK;
+            for (int i = 0; i < chunk && r == CLOTH_OK; ++i) r = one_step(i, c->cap);
+            const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+            c->cur = cur0;
+            if (r) { if (g) cudaGraphDestroy(g); return r; }
+            if (e != cudaSuccess) return cuda_fail(e);
+            const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) return cuda_fail(e2);
+            it = c->net_graphs.emplace(key, ge).first;
         }
-        cudaGraphExecDestroy(ge);
-        if (e3 != cudaSuccess) return cuda_fail(e3);
+        while (o->steps - done >= chunk) {
+            CK(cudaGraphLaunch(it->second, s));
+            done += chunk;   // chunk is even: the current buffer is unchanged
+        }
     }
     for (; done < o->steps; ++done) {
         const int r = one_step(done, s);
@@ -924,8 +947,7 @@ int cloth_set_launch(cloth_ctx* c, int32_t seg_rows, int32_t warps_per_sm, void*
     if (!c || seg_rows < -1 || (seg_rows > 0 && seg_rows < kMinSegRows) || warps_per_sm < -1 || warps_per_sm > 64)
         return CLOTH_EINVAL;
     if (warps_per_sm != 0) c->warps_per_sm = warps_per_sm > 0 ? warps_per_sm : 0;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    drop_graphs(c);
     const int seg = seg_rows > 0 ? seg_rows : (seg_rows < 0 ? 0 : c->seg_rows);
     const int rc = set_work(c, seg, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
@@ -942,8 +964,7 @@ int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const in
         if (!(R == -1 || R >= kMinSegRows) || !(w == -1 || (w >= 1 && w <= 64))) return CLOTH_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    drop_graphs(c);
     // apply candidate i as cloth_set_launch would (-1: balanced / default)
     auto apply = [&](int i) {
         c->warps_per_sm = warps_per_sm[i] > 0 ? warps_per_sm[i] : 0;
@@ -1072,6 +1093,7 @@ int cloth_set_net_stride(cloth_ctx* c, int32_t k, void* stream)
     if (!c || k < 1 || k > kMaxNetStride) return CLOTH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     for (auto& d : c->desc) d.dt_net = (float)k * d.dt;
+    if (k != c->net_stride) drop_graphs(c);   // a network step's plain steps are captured
     c->net_stride = k;
     CK(cudaMemcpyAsync(c->d_desc(), c->desc.data(), sizeof(ClothDesc) * c->B, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
@@ -1125,7 +1147,7 @@ int cloth_info(const cloth_ctx* c, int32_t* B, int64_t* total_nodes)
 void cloth_destroy(cloth_ctx* c)
 {
     if (!c) return;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
 }

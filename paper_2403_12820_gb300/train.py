@@ -251,37 +251,55 @@ def gravity_only_blob(g=wl.G_DEFAULT) -> np.ndarray:
     return w
 
 
-def evaluate(blobs: dict, cfg: dict, warm: int = 100, steps: int = 100, device="cuda") -> dict:
+def evaluate(blobs: dict, cfg: dict, warm: int = 100, steps: int = 100, device="cuda", horizons=()) -> dict:
     """Accuracy of network rollouts against the plain step (Table 2's error):
     the cloths of `cfg` are first stepped `warm` plain steps, then each
     network of `blobs` ({name: (blob, precision)}) and the plain step run
     `steps` steps from that state.  Per network: the mean over nodes of
     |x_net - x_plain| / cloth width, and that error over the plain rollout's
     mean node displacement.  Also the displacement itself (relative to
-    width)."""
+    width).  `horizons` (step counts beyond `steps`) add the error relative
+    to width at those horizons ("horizon_errors"; None once a network state
+    is not finite)."""
     specs, pins = cfg["specs"], cfg["pins"]
     cb = ClothBatch(specs, pins, device=device)
     cb.set_state(pack(cfg["x"]).to(device), pack(cfg["v"]).to(device))
     cb.rollout(warm, graph_chunk=warm)
     x0, v0 = cb.get_state()
-    cb.rollout(steps, graph_chunk=steps)
-    xp, _ = cb.get_state()
+    marks = sorted({int(steps)} | {int(h) for h in horizons})
+    plain = {}
+    done = 0
+    for h in marks:
+        cb.rollout(h - done, graph_chunk=100)
+        done = h
+        plain[h] = cb.get_state()[0]
     widths = torch.tensor([(s["cols"] - 1) * s["h"] for s in specs], device=device, dtype=torch.float64)
 
     def per_cloth(a, b):
         return torch.stack([(p - q).double().norm(dim=1).mean() for p, q in zip(cb.split(a), cb.split(b))])
 
-    disp = per_cloth(xp, x0)
+    disp = per_cloth(plain[steps], x0)
     out = {"warm_steps": warm, "steps": steps, "displacement_rel_width": float((disp / widths).mean())}
     for name, (blob, prec) in blobs.items():
         net = Net(blob, prec, device=device)
         cn = ClothBatch(specs, pins, device=device)
         cn.set_state(x0, v0)
-        cn.step_net(net, steps)
-        xn, _ = cn.get_state()
-        e = per_cloth(xn, xp)
-        out[name] = {"error_rel_width": float((e / widths).mean()), "error_rel_displacement": float((e / disp).mean()),
-                     "finite": bool(torch.isfinite(xn).all()), "status_word": cn.status()}
+        rec = {}
+        done = 0
+        for h in marks:
+            cn.step_net(net, h - done)
+            done = h
+            xn, _ = cn.get_state()
+            e = per_cloth(xn, plain[h])
+            if h == steps:
+                rec.update({"error_rel_width": float((e / widths).mean()),
+                            "error_rel_displacement": float((e / disp).mean()),
+                            "finite": bool(torch.isfinite(xn).all())})
+            if h in horizons:
+                ok = bool(torch.isfinite(xn).all())
+                rec.setdefault("horizon_errors", {})[str(h)] = float((e / widths).mean()) if ok else None
+        rec["status_word"] = cn.status()
+        out[name] = rec
         cn.close()
         net.close()
     cb.close()
@@ -350,7 +368,7 @@ def main(argv=None) -> int:
     w = tr.w.detach().cpu().numpy().astype(np.float32)
     g = data.cfg["specs"][0]["g"]
     ev = evaluate({"trained_fp32": (w, FP32), "trained_bf16": (w, BF16), "gravity_only": (gravity_only_blob(g), FP32)},
-                  wl.cnn_batch(count=a.eval_count), device=dev)
+                  wl.cnn_batch(count=a.eval_count), device=dev, horizons=(200, 300, 500, 1000))
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.save(a.out, w)
     import sys
