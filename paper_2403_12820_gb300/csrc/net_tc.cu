@@ -33,12 +33,16 @@
 //      further), into one of two tensor-memory accumulators (chunk c+1 runs
 //      during the epilogue of chunk c);
 //   3. epilogue per cell-region node: the edge corrections (computed per
-//      tile from the staged input, before its first epilogue), s = tanh(t),
-//      N + D = WN s + WD (xi . s); q kept in shared memory (zero outside the
-//      cloth: WL's zero padding);
-//   4. per output node: L = bL + sum_tap q_tap at the tap's neighbour,
-//      a = out_scale (L + N + D); then (step mode) v <- C(v + dt (a + f_p /
-//      m)), u <- u + dt v, sphere contact, store.
+//      tile from the staged input, before its first epilogue), s = tanh(t)
+//      and xi . s as the BF16 A operand of a second MMA, N + D = [s, xi . s]
+//      [WN | WD]^T (M = 128, N = 16, K = 64) into a third tensor-memory
+//      region; q kept in shared memory (zero outside the cloth: WL's zero
+//      padding);
+//   4. per cell-region node that is an output node (one thread each: the
+//      16 worker warps are the region's 16 rows): L = bL + sum_tap q_tap at
+//      the tap's neighbour, N + D from tensor memory, a = out_scale (L + N +
+//      D); then (step mode) v <- C(v + dt (a + f_p / m)), u <- u + dt v,
+//      sphere contact, store.
 // Tiles are pipelined: the input of tile t+1 is staged while the MMAs of
 // tile t run, and the first two chunks of tile t+1 run during the final
 // pass of tile t.  Between the chunks there is no CTA barrier: each worker
@@ -85,7 +89,12 @@ constexpr int kKE = 4 * 5 * 3 * kNC, kKC = 4 * 3 * kNC;   // floats
 // would be large against what remains (up to 9x on a 1 x 1 cloth); the edge
 // terms add the defect back once per tap, which makes those taps FP32.
 constexpr int kKD = 2 * 5 * 3 * kNC;
-constexpr int kPack = kBc + (kKE + kKC + kKD) * 4;
+// BF16 B operand of the N + D MMA: [k / 8][n 16][k % 8], k < 32 the s
+// channels (WN), k >= 32 the xi . s channels (WD); columns n >= 3 are zero.
+constexpr int kNDN = 16, kNDK = 64;
+constexpr int kOffBnd = kBc + (kKE + kKC + kKD) * 4;
+constexpr int kBnd = kNDK * kNDN * 2;
+constexpr int kPack = kOffBnd + kBnd;
 static_assert(kPack % 16 == 0, "pack");
 
 // FP32 u, v of the output nodes and their 1-node halo, for the update
@@ -97,28 +106,36 @@ constexpr int NQ = (R + 2) * (WO + 2);
 // shared memory map (bytes)
 constexpr int oBc = 0;
 constexpr int oIn = oBc + kBc;                      // input [2 tiles][N0BUF][8] bf16
-constexpr int oKE = oIn + 2 * N0BUF * 16;           // KE, KC (floats)
+constexpr int oBnd = oIn + 2 * N0BUF * 16;          // B of the N + D MMA
+constexpr int oAnd = oBnd + kBnd;                   // A of the N + D MMA [2 accumulators][8][128][8] bf16
+constexpr int kAnd = (kNDK / 8) * 128 * 16;         // bytes of one
 constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);  // edge nodes of a cell region: x = 0, x = W-1, y = 0, y = H-1
-constexpr int oCorr = oKE + (kKE + kKC) * 4;        // the edge nodes' corrections [kSlots][96] float
+constexpr int oCorr = oAnd + 2 * kAnd;              // the edge nodes' corrections [kSlots][96] float
 constexpr int oQ = oCorr + kSlots * kNC * 4;        // q [27][NQ] float
 constexpr int kUFloats = 6 * UH * UW;
 constexpr int oU = oQ + NQ * 27 * 4;                // u, v [2 tiles][6][UH][UW] float
-constexpr int oND = oU + 2 * kUFloats * 4;          // N + D [4 channel groups][R * WO][3] float
-constexpr int oPar = oND + 4 * R * WO * 3 * 4;         // WND[32][8] (WN0..2 WD0..2 0 0), bL[3] outs[3] ins[6]
-constexpr int oDesc = oPar + (256 + 16) * 4;        // the two tiles' cloth descriptors
+constexpr int oPar = oU + 2 * kUFloats * 4;         // bL[3] outs[3] ins[6]
+constexpr int oDesc = oPar + 16 * 4;                // the two tiles' cloth descriptors
 constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
 constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers of the two accumulators; TMEM address
-constexpr int kNumBars = 4;   // accumulator b full (MMAs done) at b, free (16 warps read it) at 2 + b
+// accumulator b full (MMAs done) at b, free (16 warps read it and wrote
+// their part of the N + D operand) at 2 + b, the tile's N + D done at 4, the
+// tear-down drain at 5
+constexpr int kNumBars = 6;
 constexpr int oTmemSlot = oBar + 8 * kNumBars;
 constexpr int kSmem = oTmemSlot + 16;
 static_assert(kSmem <= 232448, "shared memory");
-static_assert(oIn % 16 == 0 && oKE % 16 == 0 && oCorr % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 && oND % 16 == 0 &&
-                  oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
+static_assert(oIn % 16 == 0 && oBnd % 16 == 0 && oAnd % 16 == 0 && oCorr % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 &&
+                  oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0 && kOffBnd % 16 == 0,
               "alignment");
 
-// TMEM columns: accumulator b at [96 b, +96)
+// TMEM columns: accumulator b at [96 b, +96), N + D of chunk c at
+// [192 + 16 c, +16)
 constexpr uint32_t kTmemCols = 256;
-static_assert(2 * kNC <= (int)kTmemCols, "tensor memory columns");
+constexpr uint32_t kTmemND = 2 * kNC;
+static_assert(kTmemND + C2 * kNDN <= kTmemCols, "tensor memory columns");
+static_assert(C2 * 4 == NWORK / 32 && N2 <= C2 * 128 && PT == 32,
+              "the final pass gives each worker warp one region row: 4 chunks x 4 lane quarters");
 
 struct TcArgs {
     const uint4* wpack;   // packed operands (kPack bytes)
@@ -170,15 +187,15 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     const int quarter = warp & 3;                 // TMEM lanes [32 quarter, +32) of this warp
     const int cg = (warp >> 2) & 3;               // channel group: columns [8 cg, +8) of t, q and xi
     const uint32_t sbase = tc::smem_u32(sm);
-    const float* sKE = reinterpret_cast<const float*>(sm + oKE);
-    const float* sKC = sKE + kKE;
+    // the FP32 edge and corner terms stay in global memory (read once per
+    // edge tile, through the L1 cache)
+    const float* gKE = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc);
+    const float* gKC = gKE + kKE;
     float* sCorr = reinterpret_cast<float*>(sm + oCorr);
     float* sQ = reinterpret_cast<float*>(sm + oQ);
     float* sU = reinterpret_cast<float*>(sm + oU);
-    float* sND = reinterpret_cast<float*>(sm + oND);
-    const float4* sWND = reinterpret_cast<const float4*>(sm + oPar);   // [c][2]
     float* sPar = reinterpret_cast<float*>(sm + oPar);
-    float* sBL = sPar + 256;
+    float* sBL = sPar;
     float* sOut = sBL + 3;
     float* sIns = sOut + 3;
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
@@ -186,15 +203,12 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
     auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
     auto bar_free = [&](int b) { return sbase + oBar + 8u * (uint32_t)(2 + b); };
+    const uint32_t bar_nd = sbase + oBar + 8u * 4u, bar_drain = sbase + oBar + 8u * 5u;
     auto sIn = [&](int buf) { return reinterpret_cast<uint4*>(sm + oIn) + buf * N0BUF; };
 
     // ---- one-time set-up: operands, barriers, tensor memory
     for (int e = tid; e < kBc / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBc)[e] = A.wpack[e];
-    for (int e = tid; e < (kKE + kKC) / 4; e += NTH) reinterpret_cast<uint4*>(sm + oKE)[e] = A.wpack[kBc / 16 + e];
-    for (int e = tid; e < 32 * 8; e += NTH) {
-        const int c = e >> 3, j = e & 7;
-        sPar[e] = j < 3 ? A.w[kOffWN + j * kC + c] : (j < 6 ? A.w[kOffWD + (j - 3) * kC + c] : 0.f);
-    }
+    for (int e = tid; e < kBnd / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBnd)[e] = A.wpack[kOffBnd / 16 + e];
     if (tid < 3) {
         sBL[tid] = A.w[kOffBL + tid];
         sOut[tid] = A.w[kOffOuts + tid];
@@ -208,6 +222,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             tc::mbar_init(bar(b), 1);
             tc::mbar_init(bar_free(b), NWORK / 32);
         }
+        tc::mbar_init(bar_nd, 1);
+        tc::mbar_init(bar_drain, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     const uint32_t tmem = *sTmem;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     uint32_t ph[2] = {0, 0};
+    uint32_t ph_nd = 0;   // the workers' phase of bar_nd (one completion per tile)
     bool timed_out = false;
     const int n_tiles = STEP ? A.n_tiles : A.N * A.tiles_y * A.tiles_x;
 
@@ -229,18 +246,28 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // LBO = 16 bytes, a row's last tap with the next row's first at LBO =
     // (PT - 4) rows.
     const uint64_t dBc = tc::sdesc(sbase + oBc, kNC * 16, 128);
-    // the issuer's view of the accumulators: every use but the first waits
-    // for the 16 worker warps' reads of the previous one
-    bool used[2] = {false, false};
+    // N + D operands: A [k / 8][row 128][8] (LBO 128 rows, SBO 8 rows), B
+    // [k / 8][n 16][8] (LBO 16 rows, SBO 8 rows); one MMA per 16 of K
+    const uint64_t dBnd = tc::sdesc(sbase + oBnd, kNDN * 16, 128);
+    // the issuer's view of the accumulators: it waits on an accumulator's
+    // "free" barrier (the 16 worker warps read it and wrote their part of the
+    // N + D operand) before it issues that chunk's N + D MMA and reuses the
+    // accumulator
     uint32_t pfree[2] = {0, 0};
-    auto issue_chunk = [&](int c2, int ib) {   // chunk c2 of input buffer ib into accumulator c2 & 1
-        const int b = c2 & 1;
-        if (used[b]) {
-            if (!tc::mbar_wait(bar_free(b), pfree[b], kWaitLimit)) return false;
-            pfree[b] ^= 1u;
-        }
-        used[b] = true;
+    auto wait_free = [&](int b) {
+        if (!tc::mbar_wait(bar_free(b), pfree[b], kWaitLimit)) return false;
+        pfree[b] ^= 1u;
         tc::fence_after();
+        return true;
+    };
+    auto issue_nd = [&](int c2) {   // N + D of chunk c2 from A operand c2 & 1
+        const uint32_t d = tmem + kTmemND + (uint32_t)(kNDN * c2);
+        const uint64_t dA = tc::sdesc(sbase + oAnd + (uint32_t)((c2 & 1) * kAnd), 128 * 16, 128);
+#pragma unroll
+        for (int k = 0; k < kNDK / 16; ++k)
+            tc::mma_bf16(d, dA + (uint64_t)(k * 2 * 128), dBnd + (uint64_t)(k * 2 * kNDN), tc::idesc_bf16(128, kNDN), k > 0);
+    };
+    auto issue_chunk = [&](int c2, int ib) {   // chunk c2 of input buffer ib into accumulator c2 & 1
         const uint32_t d = tmem + (uint32_t)kNC * (uint32_t)(c2 & 1);
         const uint32_t in = sbase + oIn + (uint32_t)(ib * N0BUF * 16);
         const uint64_t dA = tc::sdesc(in, 16, 128), dAw = tc::sdesc(in, (PT - 4) * 16, 128);
@@ -252,7 +279,6 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             tc::mma_bf16(d, ad, dBc + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), p > 0);
         }
         tc::mma_commit(bar(c2 & 1));
-        return true;
     };
 
     // ---- per-tile pieces
@@ -379,14 +405,14 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
             for (int j = 0; j < 15; ++j) {
                 const float d = none ? 0.f : __ldg(gKD + ((ed >> 1) * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n);
-                k[j] = sKE[(ed * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n];
+                k[j] = __ldg(gKE + (ed * 5 + j / 3) * 3 * kNC + (j % 3) * kNC + n);
                 if (j / 3 == 2) kdc[j % 3] = d;
                 else k[j] += d;
             }
 #pragma unroll
             for (int yb = 0; yb < 2; ++yb)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) kc[yb][ch] = ed < 2 ? sKC[(2 * yb + ed) * 3 * kNC + ch * kNC + n] : 0.f;
+                for (int ch = 0; ch < 3; ++ch) kc[yb][ch] = ed < 2 ? __ldg(gKC + (2 * yb + ed) * 3 * kNC + ch * kNC + n) : 0.f;
             const int len = ed < 2 ? R + 2 : WO + 2;
 #pragma unroll 1
             for (int i = gi; i < len; i += kGroups) {
@@ -419,10 +445,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
     };
 
-    // 3. epilogue of chunk c2 (accumulator b): the edge corrections,
-    // s = tanh(t), and N + D over the channel group [8 cg, +8) into its own
-    // plane of sND; q, the WL partial sums, into sQ (zero outside the cloth:
-    // WL's zero padding)
+    // 3. epilogue of chunk c2 (accumulator b): the edge corrections;
+    // s = tanh(t) and xi . s of the channel group [8 cg, +8) into the BF16
+    // A operand of the N + D MMA (rows: the chunk's 128 positions); q, the
+    // WL partial sums, into sQ (zero outside the cloth: WL's zero padding)
     auto epilogue = [&](const Geo& g, int c2, int b) {
         tc::fence_after();
         const int j2 = c2 * 128 + quarter * 32 + lane;
@@ -459,32 +485,52 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             for (int k = 0; k < 8; ++k)
                 if (k < 3 || cg < 3) qr[k * NQ] = valid ? q[k] : 0.f;
         }
-        if (out_node) {
-            float nd0 = 0.f, nd1 = 0.f, nd2 = 0.f;
+        {
+            // every row of the operand is written (rows that are no output
+            // node give N + D nobody reads; their inputs are finite)
+            float sv[8], xs[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const float sv = tc::tanh_approx(t[c]);
-                const float xs = xi[c] * sv;
-                const float4 w0 = sWND[2 * (8 * cg + c)], w1 = sWND[2 * (8 * cg + c) + 1];
-                nd0 = fmaf(w0.x, sv, fmaf(w0.w, xs, nd0));
-                nd1 = fmaf(w0.y, sv, fmaf(w1.x, xs, nd1));
-                nd2 = fmaf(w0.z, sv, fmaf(w1.y, xs, nd2));
+                sv[c] = tc::tanh_approx(t[c]);
+                xs[c] = xi[c] * sv[c];
             }
-            float* o = sND + (cg * R * WO + oy * WO + ox) * 3;
-            o[0] = nd0;
-            o[1] = nd1;
-            o[2] = nd2;
+            uint4* a = reinterpret_cast<uint4*>(sm + oAnd + b * kAnd) + quarter * 32 + lane;
+            a[cg * 128] = pack8(sv);
+            a[(4 + cg) * 128] = pack8(xs);
         }
+        tc::fence_async_smem();   // the operand, for the tensor cores
         tc::fence_before();
+        (void)out_node;
     };
 
-    // 4. per output node: L, a (the channel groups' N + D added in a fixed
-    // order), and (step mode) the update (workers)
+    // 4. per output node: L, N + D from tensor memory, a, and (step mode)
+    // the update (workers).  Worker warp w takes cell-region row 4 (w / 4) +
+    // w % 4 = the TMEM lane quarter w % 4 of chunk w / 4, so each thread
+    // reads its own position's N + D.  Returns false if the N + D MMAs did
+    // not finish in time.
     auto final_pass = [&](const Geo& g, int buf) {
         const float* sUb = sU + buf * kUFloats;
-        for (int o = tid; o < R * WO; o += NWORK) {
-            const int oy = o / WO, ox = o % WO, y = g.y0 + oy, x = g.x0 + ox;
-            if (y >= g.H || x >= g.W) continue;
+        const int cc = warp >> 2;
+        const int j2 = cc * 128 + quarter * 32 + lane;   // ry2 = j2 / PT, rx2 = lane (PT = 32)
+        const int oy = j2 / PT - 1, ox = j2 % PT - 1;
+        const bool ok = tc::mbar_wait(bar_nd, ph_nd, kWaitLimit);
+        ph_nd ^= 1u;
+        tc::fence_after();
+        float nd[4];
+        {
+            uint32_t r[4];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                         : "r"(lane_base + kTmemND + (uint32_t)(kNDN * cc))
+                         : "memory");
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) nd[i] = __uint_as_float(r[i]);
+        }
+        tc::fence_before();
+        if (!ok) return false;
+        const int o = oy * WO + ox, y = g.y0 + oy, x = g.x0 + ox;
+        if (oy >= 0 && oy < R && ox >= 0 && ox < WO && y < g.H && x < g.W) {
             float acc[3];
 #pragma unroll
             for (int co = 0; co < 3; ++co) {
@@ -492,9 +538,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap)
                     L += sQ[(tap * 3 + co) * NQ + (oy + tap / 3) * (WO + 2) + ox + tap % 3];
-                const float nd = ((sND[o * 3 + co] + sND[(R * WO + o) * 3 + co]) + sND[(2 * R * WO + o) * 3 + co]) +
-                                 sND[(3 * R * WO + o) * 3 + co];
-                acc[co] = sOut[co] * (L + nd);
+                acc[co] = sOut[co] * (L + nd[co]);
             }
             if constexpr (!STEP) {
 #pragma unroll
@@ -542,6 +586,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 }
             }
         }
+        return true;
     };
 
     // ---- the pipeline.  Prologue: stage the first tile and issue its first
@@ -590,8 +635,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         Geo gnn{};
         if (tnn < n_tiles) gnn = geo(tnn);
         // No CTA barrier between the chunks: each worker warp reports its
-        // reads of an accumulator on that accumulator's "free" barrier, and
-        // the issuer waits there before it reuses the accumulator.
+        // reads of an accumulator (and its part of the N + D operand) on that
+        // accumulator's "free" barrier; the issuer waits there, issues the
+        // chunk's N + D MMA and then reuses the accumulator; after the last
+        // chunk's N + D it commits to bar_nd, which the final pass waits for.
         bool ok = true;
         for (int c2 = 0; c2 < C2; ++c2) {
             const int b = c2 & 1;
@@ -606,18 +653,25 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 if (STEP && c2 == 0 && has_next && tid < kDescV) reinterpret_cast<uint4*>(sD + (buf ^ 1))[tid] = dv;
             }
             ph[b] ^= 1u;
-            if (issuer && ok && c2 + 2 < C2) ok = issue_chunk(c2 + 2, buf);
+            if (issuer && ok) {
+                ok = wait_free(b);
+                if (ok) {
+                    issue_nd(c2);
+                    if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
+                    if (c2 == C2 - 1) tc::mma_commit(bar_nd);
+                }
+            }
         }
 
         // the next tile's first two chunks run during this tile's final pass
         if (worker) tc::fence_async_smem();   // the staged input, for the tensor cores
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
-        if (issuer && has_next) {
-            ok = issue_chunk(0, buf ^ 1);
-            if (ok && C2 > 1) ok = issue_chunk(1, buf ^ 1);
+        if (issuer && has_next) {   // the accumulators were freed by the last two chunks
+            issue_chunk(0, buf ^ 1);
+            if (C2 > 1) issue_chunk(1, buf ^ 1);
         }
         if (worker) {
-            final_pass(g, buf);
+            if (!final_pass(g, buf)) ok = false;
             if (has_next) edge_prep(gn, sIn(buf ^ 1));   // this tile's epilogues are done
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
@@ -628,16 +682,18 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         buf ^= 1;
     }
 
-    // ---- tear-down: after a timeout, wait (bounded) for the MMAs in flight
-    // (a chunk may have been issued and not yet waited for: try both phases)
-    if (timed_out) {
-        if (tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
-        for (int k = 0; k < 2; ++k)
-            for (int b = 0; b < 2; ++b) tc::mbar_wait(bar(b), (uint32_t)k, 1u << 18);
-    }
+    // ---- tear-down: the issuer commits once more, so bar_drain completes
+    // when every MMA it issued is done (after a timeout some may still be
+    // in flight); tensor memory is freed after that (bounded) wait
+    if (timed_out && tid == 0 && A.status) atomicOr(A.status, kStatusTimeout);
+    if (issuer) tc::mma_commit(bar_drain);
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) {
+        if (!tc::mbar_wait(bar_drain, 0, kWaitLimit) && lane == 0 && A.status) atomicOr(A.status, kStatusTimeout);
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
 }
 
 // Composite tap (cy, cx) of output column n and input slot e in FP32: the
@@ -660,8 +716,16 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
 {
     constexpr int nB = kPairs * 2 * kNC * 8;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nB + kKE + kKC + kKD) return;
+    if (r >= nB + kKE + kKC + kKD + kNDK * kNDN) return;
     auto tap = [](int y, int x) { return 3 * y + x; };
+    if (r >= nB + kKE + kKC + kKD) {   // B of N + D: [k / 8][n][k % 8]
+        const int e2 = r - (nB + kKE + kKC + kKD);
+        const int e = e2 % 8, n = (e2 / 8) % kNDN, k = (e2 / (8 * kNDN)) * 8 + e;
+        float v = 0.f;
+        if (n < 3) v = k < kC ? w[kOffWN + n * kC + k] : w[kOffWD + n * kC + (k - kC)];
+        reinterpret_cast<__nv_bfloat16*>(out + kOffBnd)[e2] = __float2bfloat16_rn(v);
+        return;
+    }
     if (r < nB) {   // B: tap pair p, the pair's first (kh 0) or second tap, column n, input slot e
         const int e = r % 8, n = (r / 8) % kNC, kh = (r / (8 * kNC)) % 2, p = r / (16 * kNC);
         const int c = 2 * p + kh, cy = c / 5, cx = c % 5;
@@ -733,7 +797,7 @@ cudaError_t net_tc_init()
 
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 {
-    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC + kKD;
+    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC + kKD + kNDK * kNDN;
     pack_tc_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, static_cast<uint8_t*>(wpack));
     return cudaGetLastError();
 }
