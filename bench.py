@@ -57,7 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--no-larger-step", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
     p.add_argument("--de-generations", type=int, default=6)
-    p.add_argument("--only", choices=["cnn", "mixed", "pcell", "larger_step", "train", "single_cloth"], default=None,
+    p.add_argument("--only", choices=["cnn", "cnn_step", "mixed", "pcell", "larger_step", "train", "single_cloth"],
+                   default=None,
                    help="run one section alone and print its JSON (for profiling; not a bench line)")
     return p.parse_args(argv)
 
@@ -531,6 +532,39 @@ def run_cnn(args, dev):
     return out
 
 
+def run_cnn_step(args, dev):
+    """The BF16 and FP32 network steps alone on the network workload (no
+    accuracy runs): `--cnn-steps` steps of each from the state after 100
+    plain steps, for profiling."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import BF16, FP32, Net
+
+    cfg = wl.cnn_batch()
+    blob, trained = network_blob(cfg["specs"][0]["h"])
+    cb = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cb.set_state(pack(cfg["x"]).to(dev), pack(cfg["v"]).to(dev))
+    cb.rollout(100, graph_chunk=100)
+    x0, v0 = cb.get_state()
+    out = {"trained": trained}
+    for name, prec in (("bf16", BF16), ("f32", FP32)):
+        net = Net(blob, prec, device=dev)
+        cb.set_state(x0, v0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        cb.step_net(net, args.cnn_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / max(1, args.cnn_steps), "steps": args.cnn_steps,
+                     "status_word": cb.status()}
+        net.close()
+    cb.close()
+    return out
+
+
 def run_mixed(args, dev):
     """Large mixed batch with the plain-step fallback: 16 cloths with sides
     U{256..1024} falling onto a sphere, the BF16 network rollout (trained
@@ -645,7 +679,13 @@ def run_single_cloth(dev):
     return out
 
 
-def run_larger_step(args, dev, plain_rate: float):
+def _ratio(a, b):
+    """a / b, or None when the plain rate it is taken against was not
+    measured (a section run alone)."""
+    return None if b is None else a / b
+
+
+def run_larger_step(args, dev, plain_rate: float | None):
     """Larger time steps on the 64-cloth plain batch (Sec. 5: larger-step and
     implicit integration): the implicit plain step (linearised backward
     Euler, 20 CG iterations) and the BF16 network step, both at 10 dt, in
@@ -706,12 +746,12 @@ def run_larger_step(args, dev, plain_rate: float):
            "stride": k,
            "implicit": {"value": impl_rate, "unit": "node-steps/s (implicit steps of 10 dt)", "cg_iters": iters,
                         "ms_per_step": t_impl / 10 * 1e3, "plain_equivalent_node_steps_per_s": k * impl_rate,
-                        "ratio_to_explicit": k * impl_rate / plain_rate,
+                        "ratio_to_explicit": _ratio(k * impl_rate, plain_rate),
                         "mean_error_rel_width_after_100_dt": float(err.mean().item()),
                         "max_cloth_error_rel_width": float(err.max().item()), "status_word": cb.status()},
            "bf16_network": {"value": net_rate, "unit": "node-steps/s (network steps of 10 dt)",
                             "ms_per_step": t_net / 50 * 1e3, "plain_equivalent_node_steps_per_s": k * net_rate,
-                            "ratio_to_explicit": k * net_rate / plain_rate, "status_word": cn.status()},
+                            "ratio_to_explicit": _ratio(k * net_rate, plain_rate), "status_word": cn.status()},
            "explicit_plain": plain_rate,
            "explicit_plain_moving_pins": {"value": moving_rate, "unit": "node-steps/s",
                                           "pin_velocity_m_s": [0.05, 0.0, 0.0]}}
@@ -721,7 +761,7 @@ def run_larger_step(args, dev, plain_rate: float):
     return out
 
 
-def run_pcell(args, dev, plain_rate: float):
+def run_pcell(args, dev, plain_rate: float | None):
     """Network step with the literal cell (Eq. 6-7, Fig. 1: frozen difference
     channels, ISRU, three branches) on the plain batch's 64 cloths,
     spring-like weights (seed 2005): node-steps/s against the HBM roofline
@@ -751,7 +791,7 @@ def run_pcell(args, dev, plain_rate: float):
     achieved = BYTES_PER_NODE_STEP * rate / 1e9
     out = {"workload": "plain_batch cloths (5.97M nodes), literal cell with spring-like weights (seed 2005)",
            "value": rate, "unit": "node-steps/s", "steps": steps, "ms_per_step": t / steps * 1e3,
-           "ratio_to_plain": rate / plain_rate, "gpu_launches_per_step": 1, "status_word": cb.status(),
+           "ratio_to_plain": _ratio(rate, plain_rate), "gpu_launches_per_step": 1, "status_word": cb.status(),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_kind": f"{peak_kind} (copy bandwidth)",
                         "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * nodes}}
@@ -827,9 +867,10 @@ def main(argv=None):
         import torch
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        fn = {"cnn": lambda: run_cnn(args, dev), "mixed": lambda: run_mixed(args, dev),
-              "pcell": lambda: run_pcell(args, dev, float("nan")),
-              "larger_step": lambda: run_larger_step(args, dev, float("nan")),
+        fn = {"cnn": lambda: run_cnn(args, dev), "cnn_step": lambda: run_cnn_step(args, dev),
+              "mixed": lambda: run_mixed(args, dev),
+              "pcell": lambda: run_pcell(args, dev, None),
+              "larger_step": lambda: run_larger_step(args, dev, None),
               "train": lambda: run_train(args, dev), "single_cloth": lambda: run_single_cloth(dev)}[args.only]
         print(json.dumps({"section": args.only, "result": fn()}), flush=True)
         return 0

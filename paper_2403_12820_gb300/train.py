@@ -91,6 +91,89 @@ def data_scaled_blob(stats: dict, seed: int = 2004) -> np.ndarray:
     return blob.astype(np.float32)
 
 
+class StatePool:
+    """Cloths stepped by the network being trained, whose states become
+    training windows: the physics term of Eq. 8 compares the network's
+    acceleration with the plain step's at any state, so states the network
+    itself reaches (and drifts into) are labelled by the plain simulator as
+    the recorded ones are (one plain step for the physics target, `unroll`
+    plain steps for the data targets).  Each slot is one recorded cloth
+    (its parameters and pins), restarted from a random recorded state of it
+    when it has run `max_age` network steps or left the data's envelope
+    (an in-plane displacement beyond `lim_u`, a speed beyond `lim_v`, or a
+    non-finite value).  Not part of a checkpoint: a resumed trainer starts
+    a new pool."""
+
+    def __init__(self, data: Dataset, count: int, steps: int, max_age: int, lim_u: float, lim_v: float,
+                 rng: np.random.Generator, device):
+        self.data, self.steps, self.max_age, self.lim_u, self.lim_v = data, int(steps), int(max_age), lim_u, lim_v
+        self.rng, self.device = rng, device
+        self.count = min(int(count), data.count)
+        self.ids = rng.choice(data.count, size=self.count, replace=False)
+        self.specs = [data.cfg["specs"][i] for i in self.ids]
+        self.pins = [data.cfg["pins"][i] for i in self.ids]
+        nn = data.nodes
+        self.idx = torch.from_numpy((self.ids[:, None] * nn + np.arange(nn)[None, :]).reshape(-1)).to(device)
+        n, h = data.n, float(self.specs[0]["h"])
+        X = torch.zeros(n, n, 3, device=device)
+        X[..., 0] = torch.arange(n, device=device, dtype=torch.float32)[None, :] * h
+        X[..., 1] = torch.arange(n, device=device, dtype=torch.float32)[:, None] * h
+        self.X = X.reshape(1, nn, 3)
+        self.cb = ClothBatch(self.specs, self.pins, device=device)
+        self.x = data.x[0, self.idx].clone()
+        self.v = data.v[0, self.idx].clone()
+        self.age = np.zeros(self.count, dtype=np.int64)
+        self.restarts = 0
+        self.reset(np.arange(self.count))
+
+    def reset(self, slots) -> None:
+        slots = np.asarray(slots, dtype=np.int64)
+        if slots.size == 0:
+            return
+        nn = self.data.nodes
+        t = self.rng.integers(0, self.data.steps + 1, size=slots.size)
+        rows = torch.from_numpy((slots[:, None] * nn + np.arange(nn)[None, :]).reshape(-1)).to(self.device)
+        src = torch.from_numpy((self.ids[slots][:, None] * nn + np.arange(nn)[None, :]).reshape(-1)).to(self.device)
+        tt = torch.from_numpy(np.repeat(t, nn)).to(self.device)
+        self.x[rows] = self.data.x[tt, src]
+        self.v[rows] = self.data.v[tt, src]
+        self.age[slots] = 0
+        self.restarts += int(slots.size)
+        self.cb.set_state(self.x, self.v)
+
+    def advance(self, net: Net) -> None:
+        """`steps` network steps of every slot, then the restarts."""
+        self.cb.step_net(net, self.steps)
+        self.age += self.steps
+        self.cb.get_state(self.x, self.v)
+        nn = self.data.nodes
+        u = (self.x.view(self.count, nn, 3) - self.X)[..., :2].abs().amax(dim=(1, 2))
+        sp = self.v.view(self.count, nn, 3).abs().amax(dim=(1, 2))
+        fin = torch.isfinite(self.x.view(self.count, -1)).all(dim=1) & torch.isfinite(self.v.view(self.count, -1)).all(dim=1)
+        bad = (~fin) | (u > self.lim_u) | (sp > self.lim_v)
+        bad = bad.cpu().numpy() | (self.age > self.max_age)
+        self.reset(np.nonzero(bad)[0])
+
+    def windows(self, k: int, unroll: int, stride: int):
+        """k windows starting at distinct slots' current states, with the
+        plain step's positions every `stride` steps as targets."""
+        slots = self.rng.choice(self.count, size=k, replace=False)
+        nn = self.data.nodes
+        rows = torch.from_numpy((slots[:, None] * nn + np.arange(nn)[None, :]).reshape(-1)).to(self.device)
+        specs = [self.specs[j] for j in slots]
+        pins = [self.pins[j] for j in slots]
+        x0, v0 = self.x[rows].contiguous(), self.v[rows].contiguous()
+        sim = ClothBatch(specs, pins, device=self.device)
+        sim.set_state(x0, v0)
+        tg = torch.empty(unroll, k * nn, 3, device=self.device)
+        sim.rollout(unroll * stride, record=tg, record_every=stride)
+        sim.close()
+        return specs, pins, x0, v0, tg
+
+    def close(self) -> None:
+        self.cb.close()
+
+
 class Trainer:
     """Batches of `batch` windows, each an `unroll`-step stretch of one
     trajectory; Adam (Table 1) with lr 1e-3.  `cell` is "cnn" (the C-cell,
@@ -105,11 +188,16 @@ class Trainer:
     and output scale g (init="unit").  Under torch.distributed (`group`, or
     the default group once one is set up) every rank samples its own windows
     (seed + rank) and the gradients are averaged over the ranks before the
-    identical Adam step."""
+    identical Adam step.  With `pool` > 0 (C-cell only), from iteration
+    `pool_warm` on a fraction `pool_frac` of every batch comes from a
+    StatePool of that many cloths stepped `pool_steps` network steps per
+    iteration (restarted after `pool_age` steps or outside 15 x the data's
+    in-plane displacement and 20 x its speed)."""
 
     def __init__(self, data: Dataset, blob=None, batch: int = 64, unroll: int = 8, lr: float = 1e-3,
                  alpha: float = 0.5, seed: int = 7, device="cuda", cell: str = "cnn", lr_schedule=None,
-                 trainable=None, stride: int = 1, init: str = "data", group=None):
+                 trainable=None, stride: int = 1, init: str = "data", group=None, pool: int = 0,
+                 pool_frac: float = 0.5, pool_steps: int = 4, pool_age: int = 800, pool_warm: int = 300):
         if cell not in ("cnn", "pcell"):
             raise ValueError("cell must be 'cnn' or 'pcell'")
         if stride < 1 or unroll * stride > data.steps:
@@ -141,6 +229,17 @@ class Trainer:
         self.lr_schedule = lr_schedule
         self.mask = None
         self.set_trainable(trainable)
+        self.pool = None
+        self.pool_cfg = None
+        if pool > 0:
+            if cell != "cnn":
+                raise ValueError("the state pool serves the C-cell")
+            if not 0.0 < pool_frac < 1.0:
+                raise ValueError("pool_frac must lie in (0, 1)")
+            st = data.stats()
+            self.pool_cfg = {"count": int(pool), "frac": float(pool_frac), "steps": int(pool_steps),
+                             "age": int(pool_age), "warm": int(pool_warm),
+                             "lim_u": 15.0 * max(st["rms_u"][0], st["rms_u"][1]), "lim_v": 20.0 * max(st["rms_v"])}
 
     def set_trainable(self, trainable=None) -> None:
         """Train only the named groups (None: every parameter)."""
@@ -207,14 +306,35 @@ class Trainer:
         tg = torch.stack([d.x[st + s * self.stride, idx] for s in range(1, self.unroll + 1)]).contiguous()
         return specs, pins, x0, v0, tg
 
+    def sample_with_pool(self):
+        """sample(), with the pool's share of the batch from the state pool
+        once it is active."""
+        pc = self.pool_cfg
+        if pc is None or self.t < pc["warm"]:
+            return self.sample()
+        if self.pool is None:
+            self.pool = StatePool(self.data, pc["count"], pc["steps"], pc["age"], pc["lim_u"], pc["lim_v"],
+                                  self.rng, self.device)
+        self.pool.advance(self.net)
+        k = max(1, min(self.pool.count, int(round(pc["frac"] * self.batch))))
+        full = self.batch
+        self.batch = full - k
+        try:
+            specs, pins, x0, v0, tg = self.sample()
+        finally:
+            self.batch = full
+        ps, pp, px, pv, pt = self.pool.windows(k, self.unroll, self.stride)
+        return specs + ps, pins + pp, torch.cat([x0, px]), torch.cat([v0, pv]), torch.cat([tg, pt], dim=1)
+
     def step(self) -> float:
-        specs, pins, x0, v0, tg = self.sample()
+        if self.cell == "cnn":
+            self.net.set_weights(self.w)
+        specs, pins, x0, v0, tg = self.sample_with_pool()
         cb = ClothBatch(specs, pins, device=self.device)
         cb.set_state(x0, v0)
         if self.stride != 1:
             cb.set_net_stride(self.stride)
         if self.cell == "cnn":
-            self.net.set_weights(self.w)
             loss, g = cb.train_loss(self.net, self.unroll, tg, alpha=self.alpha)
         else:
             loss, g = cb.train_loss_pcell(self.w, self.unroll, tg, alpha=self.alpha)
@@ -309,8 +429,10 @@ def evaluate(blobs: dict, cfg: dict, warm: int = 100, steps: int = 100, device="
 def main(argv=None) -> int:
     """Train the C-cell on the plain-simulator trajectories (512 cloths of
     64 x 64 x 200 steps, batch 64 windows, 8-step unroll, Adam from lr 1e-3
-    with cosine annealing), checkpointing as it goes, then save the weights
-    and a JSON record (losses, timing, held-out accuracy) beside them."""
+    with cosine annealing; from iteration 300 on half of each batch from a
+    pool of 64 cloths stepped by the network, labelled by the plain step),
+    checkpointing as it goes, then save the weights and a JSON record
+    (losses, timing, held-out accuracy) beside them."""
     import argparse
     import json
     import time
@@ -331,6 +453,11 @@ def main(argv=None) -> int:
     ap.add_argument("--resume", action="store_true")
     ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--eval-count", type=int, default=8, help="held-out 128 x 128 cloths for the accuracy check")
+    ap.add_argument("--pool", type=int, default=64, help="cloths of the network-stepped state pool (0: none)")
+    ap.add_argument("--pool-frac", type=float, default=0.5)
+    ap.add_argument("--pool-steps", type=int, default=4)
+    ap.add_argument("--pool-age", type=int, default=800)
+    ap.add_argument("--pool-warm", type=int, default=300)
     a = ap.parse_args(argv)
 
     import torch.distributed as dist
@@ -346,7 +473,8 @@ def main(argv=None) -> int:
     gen_s = time.perf_counter() - t0
     stats = data.stats()
     tr = Trainer(data, batch=a.batch, unroll=a.unroll, lr=a.lr, device=dev,
-                 lr_schedule=stages.CosineLR(a.lr, a.lr_min, a.iters))
+                 lr_schedule=stages.CosineLR(a.lr, a.lr_min, a.iters), pool=a.pool, pool_frac=a.pool_frac,
+                 pool_steps=a.pool_steps, pool_age=a.pool_age, pool_warm=a.pool_warm)
     if a.resume and os.path.exists(ckpt):
         tr.load(ckpt)
     log = []
@@ -379,6 +507,8 @@ def main(argv=None) -> int:
            "iterations": tr.t, "dataset_generation_s": gen_s, "train_s": train_s,
            "iters_per_s": a.iters / max(train_s, 1e-9), "loss_log": log, "data_stats": stats,
            "world_size": dist.get_world_size() if dist.is_initialized() else 1,
+           "state_pool": dict(tr.pool_cfg, restarts=tr.pool.restarts if tr.pool is not None else 0)
+           if tr.pool_cfg is not None else None,
            "held_out": dict(ev, workload=f"cnn_batch seed 1003, {a.eval_count} cloths of 128 x 128, "
                                          "after 100 plain steps")}
     with open(os.path.splitext(a.out)[0] + ".json", "w") as fh:

@@ -105,3 +105,27 @@ def test_training_reduces_the_loss():
         adam_step(tr.w, g, tr.m, tr.v, it + 1, lr=1e-2, n=N_PARAMS)
         losses.append(loss.item())
     assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5]), (losses[:5], losses[-5:])
+
+
+def test_state_pool_windows_are_labelled_by_the_plain_step():
+    """The trainer's network-stepped state pool: after its warm-up the pool
+    supplies part of each batch; a pool window's targets are the plain
+    step's positions from the window's start (checked against the oracle),
+    the losses stay finite, and slots restart once they reach their age."""
+    from paper_2403_12820_gb300.train import Dataset, Trainer
+    data = Dataset(count=6, n=12, steps=12, seed=1004)
+    tr = Trainer(data, batch=4, unroll=3, seed=9, pool=4, pool_frac=0.5, pool_steps=4, pool_age=8, pool_warm=2)
+    losses = [tr.step() for _ in range(8)]
+    assert all(np.isfinite(losses))
+    assert tr.pool is not None and tr.pool.restarts > tr.pool.count
+    specs, pins, x0, v0, tg = tr.pool.windows(2, 3, 1)
+    nn = 12 * 12
+    for b in range(2):
+        xb = x0[b * nn:(b + 1) * nn].cpu().numpy().astype(np.float64).reshape(12, 12, 3)
+        vb = v0[b * nn:(b + 1) * nn].cpu().numpy().astype(np.float64).reshape(12, 12, 3)
+        xr, vr = xb, vb
+        for s in range(3):
+            xr, vr = oracle.step(specs[b], xr, vr, pins=pins[b], steps=1)
+            got = tg[s, b * nn:(b + 1) * nn].cpu().numpy().astype(np.float64).reshape(12, 12, 3)
+            assert np.abs(got - xr).max() <= 1e-6, (b, s)
+    tr.pool.close()
