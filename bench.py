@@ -485,6 +485,11 @@ def run_cnn(args, dev):
         net = Net(blob, prec, device=dev)
         cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
         cn.set_state(x0, v0)
+        tile = None
+        if prec == FP32:   # the FP32 step's tile shape from the launch tuner (the state does not move)
+            from paper_2403_12820_gb300 import tune
+            rec = tune.autotune_net(cn, net, warmup=3, steps=20)
+            tile = {"tile_cols": rec["tile_cols"], "candidates_us": {str(c): round(t, 2) for c, t in rec["candidates"]}}
         cn.step_net(net, 3)
         steps = args.cnn_steps
         t = timed_segments(cn, lambda k: cn.step_net(net, k), steps)
@@ -499,6 +504,8 @@ def run_cnn(args, dev):
                      "within_1pct_of_width": e["error_rel_width"] <= 0.01,
                      "achieved_tflops": tflops, "gpu_launches_per_step": 1, "timed_as": "segments of 100 steps",
                      "status_word": cn.status()}
+        if tile is not None:
+            out[name]["tile"] = tile
         if prec == BF16:
             out[name]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                                      "frac": tflops / bf16_peak, "peak_kind": f"{peak_kind} (cuBLAS bf16 burst)",

@@ -109,6 +109,7 @@ struct cloth_ctx {
     int grid = 0, block = 128;
     int warps_per_sm = 0;              // 0: the plain-step kernel's occupancy
     int net_stride = 1;                // plain steps one network step spans
+    int comp_variant = 0;              // tile shape of the FP32 network step (net_comp_variant_cols)
     int train_seg = 0;                 // Eq. 8 unroll: keep every train_seg-th state (0: all)
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
@@ -121,7 +122,7 @@ struct cloth_ctx {
     std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
     std::vector<int32_t> impl_blk;     // implicit step: first block of each cloth, then the total
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
-    int lists_kind = -1;                   // which list it holds (network precision)
+    int lists_kind = -1;                   // which list it holds (network precision, FP32 tile shape)
 
     ClothDesc* d_desc() const { return reinterpret_cast<ClothDesc*>(ws + L.desc); }
     WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
@@ -271,11 +272,21 @@ std::vector<int4> net_tiles(const cloth_ctx* c, int R, int WO)
 }
 // of the fused tensor-core (BF16) and CUDA-core (FP32) network steps
 std::vector<int4> tc_tiles(const cloth_ctx* c) { return net_tiles(c, net_tc_tile_rows(), net_tc_tile_cols()); }
-std::vector<int4> comp_tiles(const cloth_ctx* c) { return net_tiles(c, net_comp_tile_rows(), net_comp_tile_cols()); }
+std::vector<int4> comp_tiles(const cloth_ctx* c, int variant)
+{
+    return net_tiles(c, net_comp_tile_rows(), net_comp_variant_cols(variant));
+}
+std::vector<int4> comp_tiles(const cloth_ctx* c) { return comp_tiles(c, c->comp_variant); }
+// kind of a network's tile list (what the workspace holds)
+int list_kind(const cloth_ctx* c, const cloth_net* net)
+{
+    return net->precision == CLOTH_NET_BF16 ? CLOTH_NET_BF16 : 10 + c->comp_variant;
+}
 
 // One fused network step over the tile list: the tensor-core kernel for a
-// BF16 network (one CTA per SM), the FP32 composite kernel otherwise (two
-// blocks per SM).  `mode` restricts it to the cloths in network mode.
+// BF16 network (one CTA per SM), the FP32 composite kernel otherwise (in the
+// context's tile shape, as many blocks as are resident).  `mode` restricts
+// it to the cloths in network mode.
 int launch_net_step(const cloth_ctx* c, const cloth_net* net, const int4* d_tiles, int n_tiles, const float* src,
                     float* dst, const int32_t* mode, cudaStream_t s)
 {
@@ -283,8 +294,9 @@ int launch_net_step(const cloth_ctx* c, const cloth_net* net, const int4* d_tile
         CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, n_tiles, src, dst, c->d_pins(),
                               c->d_status(), std::min(n_tiles, c->sm_count), s, mode));
     else
-        CK(launch_net_comp_step(net->d_w(), net->d_comp(), net->d_edge(), c->d_desc(), d_tiles, n_tiles, src, dst,
-                                c->d_pins(), c->d_status(), std::min(n_tiles, 2 * c->sm_count), s, mode));
+        CK(launch_net_comp_step(c->comp_variant, net->d_w(), net->d_comp(), net->d_edge(), c->d_desc(), d_tiles,
+                                n_tiles, src, dst, c->d_pins(), c->d_status(),
+                                std::min(n_tiles, net_comp_blocks_per_sm(c->comp_variant) * c->sm_count), s, mode));
     return CLOTH_OK;
 }
 
@@ -293,11 +305,11 @@ int net_tile_list(cloth_ctx* c, const cloth_net* net, void* d_work, size_t bytes
 {
     const std::vector<int4> tiles = net->precision == CLOTH_NET_BF16 ? tc_tiles(c) : comp_tiles(c);
     if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
-    if (c->lists_written != d_work || c->lists_kind != net->precision) {
+    if (c->lists_written != d_work || c->lists_kind != list_kind(c, net)) {
         CK(cudaMemcpyAsync(d_work, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
         c->lists_written = d_work;
-        c->lists_kind = net->precision;
+        c->lists_kind = list_kind(c, net);
     }
     *n_tiles = (int)tiles.size();
     return CLOTH_OK;
@@ -725,7 +737,10 @@ int cloth_reset_modes(cloth_ctx* c, void* stream)
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
-    *bytes = align_up(sizeof(int4) * (precision == CLOTH_NET_BF16 ? tc_tiles(c) : comp_tiles(c)).size(), kAlign);
+    size_t n = precision == CLOTH_NET_BF16 ? tc_tiles(c).size() : 0;
+    if (precision != CLOTH_NET_BF16)   // room for the list of any FP32 tile shape
+        for (int v = 0; v < net_comp_variants(); ++v) n = std::max(n, comp_tiles(c, v).size());
+    *bytes = align_up(sizeof(int4) * n, kAlign);
     return CLOTH_OK;
 }
 
@@ -1002,6 +1017,83 @@ int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const in
     rc = apply(b);
     if (rc) return rc;
     CK(cudaStreamSynchronize(s));
+    return CLOTH_OK;
+}
+
+int cloth_net_tile_choices(int32_t* cols, int32_t capacity, int32_t* count)
+{
+    if (!count || capacity < 0 || (capacity > 0 && !cols)) return CLOTH_EINVAL;
+    *count = net_comp_variants();
+    for (int v = 0; v < net_comp_variants() && v < capacity; ++v) cols[v] = net_comp_variant_cols(v);
+    return CLOTH_OK;
+}
+
+int cloth_set_net_tile(cloth_ctx* c, int32_t tile_cols)
+{
+    if (!c) return CLOTH_EINVAL;
+    for (int v = 0; v < net_comp_variants(); ++v)
+        if (net_comp_variant_cols(v) == tile_cols) {
+            if (v != c->comp_variant) {
+                drop_graphs(c);   // the captured network steps use the old shape
+                c->comp_variant = v;
+            }
+            return CLOTH_OK;
+        }
+    return CLOTH_EINVAL;
+}
+
+int cloth_get_net_tile(const cloth_ctx* c, int32_t* tile_cols)
+{
+    if (!c || !tile_cols) return CLOTH_EINVAL;
+    *tile_cols = net_comp_variant_cols(c->comp_variant);
+    return CLOTH_OK;
+}
+
+int cloth_tune_net(cloth_ctx* c, const cloth_net* net, int32_t warmup, int32_t steps, float* us_out,
+                   int32_t* best_cols, void* d_work, size_t bytes, void* stream)
+{
+    if (!c || !net || !us_out || !best_cols || !d_work || warmup < 0 || steps < 1) return CLOTH_EINVAL;
+    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;   // the tensor-core step has one shape
+    if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
+    size_t need = 0;
+    int rc = cloth_net_workspace_size(c, net->precision, &need);
+    if (rc) return rc;
+    if (bytes < need) return CLOTH_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    drop_graphs(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    // every timed step reads the current state and writes the other buffer,
+    // so the state the caller sees does not move
+    const float* src = c->d_state(c->cur);
+    float* dst = c->d_state(c->cur ^ 1);
+    const int nv = net_comp_variants();
+    for (int v = 0; v < nv && rc == CLOTH_OK && ce == cudaSuccess; ++v) {
+        c->comp_variant = v;
+        int n_tiles = 0;
+        rc = net_tile_list(c, net, d_work, bytes, &n_tiles, s);
+        const int4* tl = static_cast<const int4*>(d_work);
+        for (int k = 0; k < warmup && rc == CLOTH_OK; ++k) rc = launch_net_step(c, net, tl, n_tiles, src, dst, nullptr, s);
+        if (rc) break;
+        if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) break;
+        for (int k = 0; k < steps && rc == CLOTH_OK; ++k) rc = launch_net_step(c, net, tl, n_tiles, src, dst, nullptr, s);
+        if (rc) break;
+        if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) break;
+        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        us_out[v] = ms * 1000.f / (float)steps;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ce != cudaSuccess) { c->comp_variant = 0; return cuda_fail(ce); }
+    if (rc) { c->comp_variant = 0; return rc; }
+    int b = 0;
+    for (int v = 1; v < nv; ++v)
+        if (us_out[v] < us_out[b]) b = v;
+    c->comp_variant = b;
+    *best_cols = net_comp_variant_cols(b);
     return CLOTH_OK;
 }
 

@@ -10,10 +10,12 @@
 // padding is restored by the same edge and corner terms as the tensor-core
 // step (FP32 tables packed with it), so every node gets the layered result.
 //
-// One block of 256 threads per tile of 14 x 14 output nodes, two blocks per
-// SM, looping over the tiles.  Per tile:
-//   0. stage the 20 x 20 input region (scaled z, and the raw u, v of the
-//      16 x 16 cell region for the update), zero outside the cloth;
+// One block of 16 (TC + 2) threads per tile of 14 x TC output nodes,
+// looping over the tiles; TC is 14 by default (256 threads, two blocks per
+// SM), and 6 and 30 are the other tile shapes the launch tuner can pick.
+// Per tile:
+//   0. stage the 20 x (TC + 6) input region (scaled z, and the raw u, v of
+//      the 16 x (TC + 2) cell region for the update), zero outside the cloth;
 //   1. the composite convolution over the 16 x 16 cell region: a thread
 //      takes four cell positions 4 rows apart and one of eight column groups
 //      (t and xi channels [4 g, +4), q values [4 g, +4) below 27),
@@ -31,31 +33,39 @@
 namespace cloth {
 namespace {
 
-constexpr int TR = 14, TC = 14;            // output tile
-constexpr int CR = TR + 2, CC = TC + 2;    // cell region, origin (y0 - 1, x0 - 1)
-constexpr int IR = TR + 6, IC = TC + 6;    // input region, origin (y0 - 3, x0 - 3)
-constexpr int NCELL = CR * CC, NIN = IR * IC, NOUT = TR * TC;
-constexpr int NTHR = 256;
 constexpr int kGroups = 8, kGW = 12;       // column groups; weights per (group, tap, channel)
 constexpr int kPos = 4;                    // cell positions per item, 4 rows apart
-constexpr int kQuads = NCELL / kPos;       // 64
 constexpr int kWF = kGroups * 25 * 3 * kGW;
-static_assert(kGroups * kQuads == 2 * NTHR && kQuads % 32 == 0, "two items of four positions per thread, one group per warp");
-static_assert(NOUT <= NTHR, "one output node per thread in the final pass");
-static_assert(kQuads == 4 * CC && CR == 4 * kPos, "the rows cy0 + 4 p of the 64 quads cover the cell region once");
 
-// shared memory (bytes)
-constexpr int oW = 0;                                  // composite weights [g][tap][ch][12]
-constexpr int oZ = oW + kWF * 4;                       // scaled z: [NIN] float4 u0 u1 u2 v0, then [NIN] float2 v1 v2
-constexpr int oRaw = oZ + NIN * 24;                    // raw u, v [6][NCELL]
-constexpr int oQ = oRaw + 6 * NCELL * 4;               // q [27][NCELL]
-constexpr int oND = oQ + 27 * NCELL * 4;               // N + D shares [g][NOUT][3]
-constexpr int oPar = oND + kGroups * NOUT * 3 * 4;     // WND[32][8], bL[3], outs[3], ins[6]
-constexpr int oDesc = oPar + (256 + 16) * 4;
-constexpr int oPin = oDesc + (int)sizeof(ClothDesc);
-constexpr int kSmem = oPin + (NOUT + 15) / 16 * 16;
-static_assert(oZ % 16 == 0 && oRaw % 16 == 0 && oPar % 16 == 0 && oDesc % 16 == 0, "alignment");
-static_assert(2 * (kSmem + 1024) <= 233472, "two blocks per SM");
+// Tile shape 14 x TCOL and what follows from it.
+template <int TCOL>
+struct Shape {
+    static constexpr int TR = 14, TC = TCOL;               // output tile
+    static constexpr int CR = TR + 2, CC = TC + 2;         // cell region, origin (y0 - 1, x0 - 1)
+    static constexpr int IR = TR + 6, IC = TC + 6;         // input region, origin (y0 - 3, x0 - 3)
+    static constexpr int NCELL = CR * CC, NIN = IR * IC, NOUT = TR * TC;
+    static constexpr int NTHR = 16 * CC;                   // two items of four positions per thread
+    static constexpr int kQuads = NCELL / kPos;            // 4 CC
+    static constexpr int kMinBlocks = TC <= 6 ? 3 : (TC <= 14 ? 2 : 1);
+    // shared memory (bytes)
+    static constexpr int oW = 0;                                  // composite weights [g][tap][ch][12]
+    static constexpr int oZ = oW + kWF * 4;                       // scaled z: [NIN] float4 u0 u1 u2 v0, then [NIN] float2 v1 v2
+    static constexpr int oRaw = oZ + NIN * 24;                    // raw u, v [6][NCELL]
+    static constexpr int oQ = oRaw + 6 * NCELL * 4;               // q [27][NCELL]
+    static constexpr int oND = oQ + 27 * NCELL * 4;               // N + D shares [g][NOUT][3]
+    static constexpr int oPar = oND + kGroups * NOUT * 3 * 4;     // WND[32][8], bL[3], outs[3], ins[6]
+    static constexpr int oDesc = oPar + (256 + 16) * 4;
+    static constexpr int oPin = oDesc + (int)sizeof(ClothDesc);
+    static constexpr int kSmem = oPin + (NOUT + 15) / 16 * 16;
+    static_assert(kGroups * kQuads == 2 * NTHR && kQuads % 32 == 0, "two items of four positions per thread, one group per warp");
+    static_assert(NOUT <= NTHR, "one output node per thread in the final pass");
+    static_assert(kQuads == 4 * CC && CR == 4 * kPos, "the rows cy0 + 4 p of the quads cover the cell region once");
+    static_assert(oZ % 16 == 0 && oRaw % 16 == 0 && oPar % 16 == 0 && oDesc % 16 == 0, "alignment");
+    static_assert(kMinBlocks * (kSmem + 1024) <= 233472, "resident blocks per SM");
+};
+// the tile widths the launch tuner chooses among (index = variant)
+constexpr int kVariants = 3;
+constexpr int kVariantCols[kVariants] = {14, 6, 30};
 
 struct CompArgs {
     const float* w;        // FP32 blob
@@ -74,8 +84,14 @@ struct CompArgs {
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 F2(float a) { return make_float2(a, a); }
 
-__global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
+template <int TCOL>
+__global__ void __launch_bounds__(Shape<TCOL>::NTHR, Shape<TCOL>::kMinBlocks) net_comp_kernel(CompArgs A)
 {
+    using S = Shape<TCOL>;
+    constexpr int TR = S::TR, TC = S::TC, CR = S::CR, CC = S::CC, IC = S::IC;
+    constexpr int NCELL = S::NCELL, NIN = S::NIN, NOUT = S::NOUT, NTHR = S::NTHR, kQuads = S::kQuads;
+    constexpr int oW = S::oW, oZ = S::oZ, oRaw = S::oRaw, oQ = S::oQ, oND = S::oND, oPar = S::oPar;
+    constexpr int oDesc = S::oDesc, oPin = S::oPin;
     extern __shared__ __align__(16) uint8_t sm[];
     const int tid = threadIdx.x;
     const float4* sW = reinterpret_cast<const float4*>(sm + oW);
@@ -140,7 +156,7 @@ __global__ void __launch_bounds__(NTHR, 2) net_comp_kernel(CompArgs A)
         __syncthreads();
 
         // 1. the composite convolution, two items per thread: column group g
-        // (the same for a whole warp) and cell positions p0 + 64 k, k < 4
+        // (the same for a whole warp) and cell positions p0 + 4 k CC, k < 4
 #pragma unroll 1
         for (int r = 0; r < 2; ++r) {
             const int item = r * NTHR + tid, g = item / kQuads, p0 = item % kQuads;
@@ -328,13 +344,28 @@ __global__ void pack_comp_kernel(const float* __restrict__ w, float* __restrict_
 
 }  // namespace
 
-int net_comp_tile_rows() { return TR; }
-int net_comp_tile_cols() { return TC; }
+int net_comp_tile_rows() { return 14; }
+int net_comp_variants() { return kVariants; }
+int net_comp_variant_cols(int v) { return v >= 0 && v < kVariants ? kVariantCols[v] : 0; }
+int net_comp_blocks_per_sm(int v)
+{
+    switch (v) {
+    case 1: return Shape<6>::kMinBlocks;
+    case 2: return Shape<30>::kMinBlocks;
+    default: return Shape<14>::kMinBlocks;
+    }
+}
 int net_comp_pack_floats() { return kWF; }
 
 cudaError_t net_comp_init()
 {
-    return cudaFuncSetAttribute(net_comp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(net_comp_kernel<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Shape<14>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(net_comp_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<6>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(net_comp_kernel<30>, cudaFuncAttributeMaxDynamicSharedMemorySize, Shape<30>::kSmem);
+    return e;
 }
 
 cudaError_t launch_pack_comp(const float* w, float* out, cudaStream_t s)
@@ -343,7 +374,7 @@ cudaError_t launch_pack_comp(const float* w, float* out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_comp_step(const float* w, const float* wf, const float* ke, const ClothDesc* desc,
+cudaError_t launch_net_comp_step(int variant, const float* w, const float* wf, const float* ke, const ClothDesc* desc,
                                  const int4* tiles, int n_tiles, const float* src, float* dst,
                                  const uint32_t* pinmask, int32_t* status, int grid, cudaStream_t s,
                                  const int32_t* mode)
@@ -360,7 +391,11 @@ cudaError_t launch_net_comp_step(const float* w, const float* wf, const float* k
     a.pinmask = pinmask;
     a.mode = mode;
     a.status = status;
-    net_comp_kernel<<<grid, NTHR, kSmem, s>>>(a);
+    switch (variant) {
+    case 1: net_comp_kernel<6><<<grid, Shape<6>::NTHR, Shape<6>::kSmem, s>>>(a); break;
+    case 2: net_comp_kernel<30><<<grid, Shape<30>::NTHR, Shape<30>::kSmem, s>>>(a); break;
+    default: net_comp_kernel<14><<<grid, Shape<14>::NTHR, Shape<14>::kSmem, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

@@ -94,15 +94,19 @@ cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDes
 cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
                                   int32_t* status, int grid, cudaStream_t s);
 // FP32 fused network step with the composite trunk (net_comp.cu): tiles of
-// net_comp_tile_rows() x net_comp_tile_cols() output nodes; its composite
-// weights (net_comp_pack_floats() floats) follow the tensor-core operands in
-// the pack, and it reads their FP32 edge and corner terms.
+// net_comp_tile_rows() x net_comp_variant_cols(v) output nodes for one of
+// net_comp_variants() tile shapes v (0: the default; the launch tuner picks
+// among them), net_comp_blocks_per_sm(v) resident blocks per SM; its
+// composite weights (net_comp_pack_floats() floats) follow the tensor-core
+// operands in the pack, and it reads their FP32 edge and corner terms.
 int net_comp_tile_rows();
-int net_comp_tile_cols();
+int net_comp_variants();
+int net_comp_variant_cols(int v);
+int net_comp_blocks_per_sm(int v);
 int net_comp_pack_floats();
 cudaError_t net_comp_init();
 cudaError_t launch_pack_comp(const float* w, float* out, cudaStream_t s);
-cudaError_t launch_net_comp_step(const float* w, const float* wf, const float* ke, const ClothDesc* desc,
+cudaError_t launch_net_comp_step(int variant, const float* w, const float* wf, const float* ke, const ClothDesc* desc,
                                  const int4* tiles, int n_tiles, const float* src, float* dst,
                                  const uint32_t* pinmask, int32_t* status, int grid, cudaStream_t s,
                                  const int32_t* mode = nullptr);

@@ -133,3 +133,63 @@ def test_tune_rejects_bad_candidates_before_running():
         cb.tune_launch([(16, -1)], steps=0)
     assert cb.get_launch() == before
     cb.close()
+
+
+def test_net_tile_choices_are_the_library_shapes():
+    """The FP32 network step's tile widths (host query, no GPU): the default
+    first, each distinct."""
+    ch = tune.net_tile_choices()
+    assert ch[0] == 14 and len(set(ch)) == len(ch) >= 2
+
+
+@pytest.mark.gpu
+def test_fp32_step_is_bitwise_the_same_in_every_tile_shape_and_the_tuner_picks_the_fastest(tmp_path):
+    """Each node's arithmetic in the FP32 network step does not depend on the
+    tiling, so every tile shape gives the same state bit for bit (an uneven
+    batch: single nodes, thin strips, sizes off every tile width, pins,
+    pressure, a sphere); cloth_tune_net leaves the state, applies the
+    fastest shape, and the cache brings it back without timing."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import BF16, FP32, Net
+    rng = np.random.default_rng(401)
+    specs, pins, xs, vs = [], [], [], []
+    for (r, c) in [(1, 1), (1, 7), (5, 3), (14, 14), (15, 31), (29, 61), (40, 13), (70, 33)]:
+        sph = {"center": (0.1, 0.1, -0.05), "radius": 0.06} if r == 29 else None
+        sp = wl.cloth_spec(r, c, p=rng.normal(0, 0.5), sphere=sph)
+        x, v = wl.sag_state(sp, rng, amp=0.02, vamp=0.1)
+        specs.append(sp); xs.append(x); vs.append(v); pins.append([0] if r * c > 1 else [])
+    w = wl.kaiming_blob(402, in_scale=(50.0,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3, bias_sigma=0.1)
+    net = Net(w, FP32)
+    x0, v0 = pack(xs).cuda(), pack(vs).cuda()
+    outs = []
+    for cols in tune.net_tile_choices():
+        cb = ClothBatch(specs, pins)
+        cb.set_net_tile(cols)
+        assert cb.get_net_tile() == cols
+        cb.set_state(x0, v0)
+        cb.step_net(net, 7)
+        outs.append(cb.get_state())
+        assert cb.status() == 0
+        cb.close()
+    for x, v in outs[1:]:
+        assert torch.equal(x, outs[0][0]) and torch.equal(v, outs[0][1])
+    cb = ClothBatch(specs, pins)
+    cb.set_state(x0, v0)
+    with pytest.raises(Exception):
+        cb.set_net_tile(13)
+    path = str(tmp_path / "net_tiles.json")
+    rec = tune.autotune_net(cb, net, cache_path=path, warmup=1, steps=3)
+    assert not rec["cached"] and rec["tile_cols"] in tune.net_tile_choices()
+    assert rec["tile_cols"] == min(rec["candidates"], key=lambda ct: ct[1])[0]
+    assert cb.get_net_tile() == rec["tile_cols"]
+    x, v = cb.get_state()
+    assert torch.equal(x, x0) and torch.equal(v, v0)          # tuning does not move the state
+    cb.set_net_tile(tune.net_tile_choices()[0])
+    again = tune.autotune_net(cb, net, cache_path=path)
+    assert again["cached"] and cb.get_net_tile() == rec["tile_cols"]
+    with pytest.raises(Exception):
+        cb.tune_net(Net(w, BF16))                               # one shape on the tensor cores
+    cb.close()
