@@ -39,8 +39,8 @@ int64_t units_for(const cloth_grid* g, int B, int seg_rows, int strip = kStrip)
 }
 
 struct Layout {
-    size_t desc, units, warp_first, pins, state[2], status, ctl, total;
-    int64_t state_floats, pin_words, max_units;
+    size_t desc, units, warp_first, pins, pin_list, state[2], status, ctl, total;
+    int64_t state_floats, pin_words, max_units, pin_list_cap;
 };
 
 Layout make_layout(int B, const cloth_grid* g)
@@ -62,6 +62,10 @@ Layout make_layout(int B, const cloth_grid* g)
     L.units = off;    off = align_up(off + sizeof(WorkUnit) * L.max_units, kAlign);
     L.warp_first = off; off = align_up(off + sizeof(int32_t) * (kMaxWarps + 1), kAlign);
     L.pins = off;     off = align_up(off + sizeof(uint32_t) * words, kAlign);
+    // the pinned nodes as (cloth, node) pairs: room for one per pin word
+    // (one node in 32; more pins than that are set from the mask instead)
+    L.pin_list_cap = std::max<int64_t>(words, 64);
+    L.pin_list = off; off = align_up(off + sizeof(int2) * L.pin_list_cap, kAlign);
     L.state[0] = off; off = align_up(off + sizeof(float) * floats, kAlign);
     L.state[1] = off; off = align_up(off + sizeof(float) * floats, kAlign);
     L.status = off;   off = align_up(off + 64, kAlign);
@@ -120,6 +124,7 @@ struct cloth_ctx {
     using NetGraphKey = std::tuple<const void*, const void*, int, const void*, size_t, int, int, uint32_t, int>;
     std::map<NetGraphKey, cudaGraphExec_t> net_graphs;
     std::vector<int64_t> free_nodes;   // nodes per cloth that are not pinned
+    int32_t n_pins = 0;                // entries of the pin list; -1: pins set from the mask
     std::vector<int32_t> impl_blk;     // implicit step: first block of each cloth, then the total
     const void* lists_written = nullptr;   // step workspace holding current cloth lists
     int lists_kind = -1;                   // which list it holds (network precision, FP32 tile shape)
@@ -128,6 +133,7 @@ struct cloth_ctx {
     WorkUnit* d_units() const { return reinterpret_cast<WorkUnit*>(ws + L.units); }
     int32_t* d_warp_first() const { return reinterpret_cast<int32_t*>(ws + L.warp_first); }
     uint32_t* d_pins() const { return reinterpret_cast<uint32_t*>(ws + L.pins); }
+    int2* d_pin_list() const { return reinterpret_cast<int2*>(ws + L.pin_list); }
     float* d_state(int k) const { return reinterpret_cast<float*>(ws + L.state[k]); }
     int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + L.status); }
     int32_t* d_mode() const { return reinterpret_cast<int32_t*>(ws + L.ctl); }
@@ -238,6 +244,9 @@ int launch_plain(cloth_ctx* c, const float* src, float* dst, const int32_t* mode
     a.pinmask = c->d_pins();
     a.status = c->d_status();
     a.mode = mode;
+    a.pin_list = c->d_pin_list();
+    a.n_pins = c->n_pins;
+    a.n_cloths = c->B;
     if (c->damp) CK(launch_plain_step_damp(a, false, c->grid, c->block, s));
     else CK(launch_plain_step(a, false, c->grid, c->block, s));
     return CLOTH_OK;
@@ -255,6 +264,9 @@ int launch_step(cloth_ctx* c, bool forces_only, float* force_out, cudaStream_t s
     a.pinmask = c->d_pins();
     a.force_out = force_out;
     a.status = c->d_status();
+    a.pin_list = c->d_pin_list();
+    a.n_pins = c->n_pins;
+    a.n_cloths = c->B;
     if (c->damp) CK(launch_plain_step_damp(a, forces_only, c->grid, c->block, s));
     else CK(launch_plain_step(a, forces_only, c->grid, c->block, s));
     if (!forces_only) c->cur ^= 1;
@@ -783,6 +795,7 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
     if (e != cudaSuccess) { delete c; return cuda_fail(e); }
 
     std::vector<uint32_t> pinmask(L.pin_words, 0u);
+    std::vector<int2> pin_list;
     int64_t floats = 0, words = 0, nodes = 0;
     for (int b = 0; b < B; ++b) {
         const cloth_grid& g = grids[b];
@@ -837,7 +850,10 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
                 if (n < 0 || (int64_t)n >= (int64_t)g.rows * g.cols) { delete c; return CLOTH_EINVAL; }
                 const int r = n / g.cols, col = n % g.cols;
                 uint32_t& wd = pinmask[words + (int64_t)r * d.pin_wpr + col / 32];
-                if (!(wd & (1u << (col % 32)))) ++pinned;
+                if (!(wd & (1u << (col % 32)))) {
+                    ++pinned;
+                    pin_list.push_back(make_int2(b, n));
+                }
                 wd |= 1u << (col % 32);
             }
         }
@@ -854,6 +870,9 @@ int cloth_create(cloth_ctx** out, int32_t B, const cloth_grid* grids, const clot
     e = cudaMemcpyAsync(c->d_desc(), c->desc.data(), sizeof(ClothDesc) * B, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && L.pin_words)
         e = cudaMemcpyAsync(c->d_pins(), pinmask.data(), sizeof(uint32_t) * L.pin_words, cudaMemcpyHostToDevice, s);
+    c->n_pins = (int64_t)pin_list.size() <= L.pin_list_cap ? (int32_t)pin_list.size() : -1;
+    if (e == cudaSuccess && c->n_pins > 0)
+        e = cudaMemcpyAsync(c->d_pin_list(), pin_list.data(), sizeof(int2) * pin_list.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[0], 0, L.state[1] - L.state[0], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.state[1], 0, L.status - L.state[1], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.status, 0, L.total - L.status, s);

@@ -123,6 +123,11 @@ struct StepArgs {
     float* force_out;     // forces-only mode: packed ABI layout
     int32_t* status;
     const int32_t* mode;  // if set, only cloths in plain mode are stepped
+    // pinned nodes, set after the step by the undamped kernel's launcher:
+    // (cloth, node) pairs, n_pins of them (0: none; -1: too many for the
+    // list, set from the pin mask of the n_cloths cloths instead)
+    const int2* pin_list;
+    int32_t n_pins, n_cloths;
 };
 
 // Launchers (plain_step.cu, state.cu).

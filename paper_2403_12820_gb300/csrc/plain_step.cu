@@ -14,8 +14,10 @@
 // accumulator, in registers (same lane, rows r .. r+2) or through one warp
 // shuffle (neighbour lane).  After row r its accumulator holds all 12
 // springs, and the node is finished: gravity and drag (Eq. 4), the
-// semi-implicit Euler update with pins (Eq. 5), sphere contact, float4
-// stores.  Pressure (Eq. 3) of row r+1 is added while rows r .. r+2 are in
+// semi-implicit Euler update (Eq. 5), sphere contact, float4 stores.  The
+// pinned nodes (the constraint C of Eq. 5) are set afterwards by a small
+// kernel over the pin list (pin_fix_kernel): a per-row test of the pin mask
+// inside this kernel cost about 7 % of the step, for a few nodes per cloth.  Pressure (Eq. 3) of row r+1 is added while rows r .. r+2 are in
 // the window.
 //
 // Precision: positions are stored as u = x - X (displacement from the rest
@@ -127,9 +129,7 @@ __device__ __forceinline__ float shdn(float v) { return __shfl_down_sync(kFull, 
 // in global memory after every row's stores.
 struct UnitConst {
     float dt, dtm, keep, dtg[3];   // dt, dt/m, 1 - dt d/m, dt g
-    float pin_v[3];                // velocity of the pinned nodes
-    int32_t pin_wpr, sph_on;
-    const uint32_t* pins;          // the cloth's pin bitmask
+    int32_t sph_on;
 };
 
 // Stiffness pairs of the 12 springs a lane evaluates per row, indexed
@@ -184,12 +184,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
             uc->dtg[0] = D.dt * D.gx;
             uc->dtg[1] = D.dt * D.gy;
             uc->dtg[2] = D.dt * D.gz;
-            uc->pin_v[0] = D.pin_vx;
-            uc->pin_v[1] = D.pin_vy;
-            uc->pin_v[2] = D.pin_vz;
-            uc->pin_wpr = D.pin_wpr;
             uc->sph_on = D.sph_on;
-            uc->pins = a.pinmask + D.pin_off;
         }
         __syncwarp();
         {
@@ -436,18 +431,6 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
                         vn.A[c] = fma2(dtm, F0.A[c], fma2(keep, V0.A[c], dtg[c]));
                         vn.B[c] = fma2(dtm, F0.B[c], fma2(keep, V0.B[c], dtg[c]));
                     }
-                    const uint32_t pw = __ldg(uc->pins + (int64_t)r * uc->pin_wpr + (c4 >> 5));
-                    const unsigned pb = (pw >> (c4 & 31)) & 0xfu;
-                    if (pb) {   // pinned nodes: C sets the velocity of the object they move with
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float pv = uc->pin_v[c];
-                            if (pb & 1u) vn.A[c].x = pv;
-                            if (pb & 4u) vn.A[c].y = pv;
-                            if (pb & 2u) vn.B[c].x = pv;
-                            if (pb & 8u) vn.B[c].y = pv;
-                        }
-                    }
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         un.A[c] = fma2(dt, vn.A[c], P0.A[c]);
@@ -508,6 +491,72 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
 
 }  // namespace
 
+// C of Eq. 5 for the pinned nodes of the step src -> dst just taken: the
+// velocity of the object they move with, the position update with it, and
+// sphere contact, exactly as the update of a free node but for the velocity
+// (the same single-rounding FMA), overwriting what the step wrote for them.
+// One thread per entry (cloth, node) of the pin list; cloths not in plain
+// mode (mode set) are left alone.
+__global__ void pin_fix_kernel(const ClothDesc* __restrict__ desc, const int2* __restrict__ pins, int n,
+                               const float* __restrict__ src, float* __restrict__ dst, const int32_t* __restrict__ mode,
+                               int32_t* __restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 p = pins[i];
+    if (mode && mode[p.x] != kModePlain) return;
+    const ClothDesc& D = desc[p.x];
+    const int r = p.y / D.cols, c = p.y % D.cols;
+    const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
+    float un[3], vn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        vn[k] = pin_v(D, k);
+        un[k] = fmaf(D.dt, vn[k], src[o + k * D.plane_stride]);
+    }
+    if (D.sph_on) sphere_contact(D, c, r, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
+    if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(status, kStatusNonfinite);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dst[o + k * D.plane_stride] = un[k];
+        dst[o + (3 + k) * D.plane_stride] = vn[k];
+    }
+}
+
+// The same from the pin mask (one thread per mask word), for a context whose
+// pins do not fit its pin list.
+__global__ void pin_fix_mask_kernel(const ClothDesc* __restrict__ desc, int B, const uint32_t* __restrict__ mask,
+                                    const float* __restrict__ src, float* __restrict__ dst,
+                                    const int32_t* __restrict__ mode, int32_t* __restrict__ status)
+{
+    const int b = blockIdx.y;
+    if (b >= B || (mode && mode[b] != kModePlain)) return;
+    const ClothDesc& D = desc[b];
+    const int64_t words = (int64_t)D.rows * D.pin_wpr;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t bits = mask[D.pin_off + w];
+        const int r = (int)(w / D.pin_wpr), c0 = (int)(w % D.pin_wpr) * 32;
+        while (bits) {
+            const int c = c0 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int64_t o = D.plane_off + (int64_t)r * D.pitch + col_pos(c);
+            float un[3], vn[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                vn[k] = pin_v(D, k);
+                un[k] = fmaf(D.dt, vn[k], src[o + k * D.plane_stride]);
+            }
+            if (D.sph_on) sphere_contact(D, c, r, D.h, un[0], un[1], un[2], vn[0], vn[1], vn[2]);
+            if (!isfinite(un[0] + un[1] + un[2] + vn[0] + vn[1] + vn[2])) atomicOr(status, kStatusNonfinite);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dst[o + k * D.plane_stride] = un[k];
+                dst[o + (3 + k) * D.plane_stride] = vn[k];
+            }
+        }
+    }
+}
+
 int plain_step_blocks_per_sm_nodamp(int block)
 {
     int n = 0;
@@ -517,9 +566,23 @@ int plain_step_blocks_per_sm_nodamp(int block)
 
 cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s)
 {
-    if (forces_only) plain_step_kernel<true><<<grid, block, 0, s>>>(a);
-    else plain_step_kernel<false><<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    if (forces_only) {
+        plain_step_kernel<true><<<grid, block, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    plain_step_kernel<false><<<grid, block, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.n_pins > 0) {
+        pin_fix_kernel<<<(a.n_pins + 127) / 128, 128, 0, s>>>(a.desc, a.pin_list, a.n_pins, a.src, a.dst, a.mode,
+                                                             a.status);
+        e = cudaGetLastError();
+    } else if (a.n_pins < 0) {   // the pins did not fit the list: from the mask
+        pin_fix_mask_kernel<<<dim3(64, (unsigned)a.n_cloths), 128, 0, s>>>(a.desc, a.n_cloths, a.pinmask, a.src,
+                                                                          a.dst, a.mode, a.status);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace cloth

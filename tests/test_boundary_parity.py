@@ -172,3 +172,28 @@ def test_training_loss_with_moving_pins():
     gg = grad.cpu().numpy()
     assert np.abs(gg[:39] - rg[:39]).max() <= 1e-4 * np.abs(rg[:39]).max()
     cb.close()
+
+
+def test_plain_step_with_more_pins_than_the_pin_list_holds():
+    """The undamped plain step sets its pinned nodes after the step, from the
+    context's pin list, or from the pin mask when a context has more pins
+    than the list holds (one per 32 nodes): a batch with every boundary node
+    of a 40 x 40 cloth pinned (156 pins, moving), beside cloths with a few
+    pins, against the oracle after 20 steps; and the same cloths in a batch
+    whose pins fit the list."""
+    specs, pins, xs, vs = batch(311, [(40, 40), (9, 33), (21, 6)])
+    pins[0] = [int(k) for k in wl.boundary_nodes(40, 40)]
+    for sel in ([0, 1, 2], [1, 2]):
+        sp, pn = [specs[i] for i in sel], [pins[i] for i in sel]
+        cb = ClothBatch(sp, pn)
+        cb.set_state(pack([xs[i] for i in sel]).cuda(), pack([vs[i] for i in sel]).cuda())
+        cb.step(20)
+        x, v = cb.get_state()
+        got = [t.cpu().numpy().astype(np.float64) for t in cb.split(x)]
+        gotv = [t.cpu().numpy().astype(np.float64) for t in cb.split(v)]
+        for j, i in enumerate(sel):
+            xr, vr = oracle.step(specs[i], xs[i], vs[i], pins=pins[i], steps=20)
+            assert np.abs(got[j] - xr).max() <= X_TOL, (sel, i)
+            assert np.abs(gotv[j] - vr).max() <= 1e-2, (sel, i)
+        assert cb.status() == 0
+        cb.close()
