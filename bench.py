@@ -343,7 +343,8 @@ def run_plain(args, rank, world, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth)", "traffic": traffic,
                      "algorithmic_bytes_per_launch": BYTES_PER_NODE_STEP * nodes},
-        "gpu_launches": args.steps,
+        # the plain-step kernel, and the kernel that sets the pinned nodes
+        "gpu_launches": args.steps * (2 if any(len(p) for p in cfg["pins"]) else 1),
         "clocks": clocks,
         "status_word": status,
     }
