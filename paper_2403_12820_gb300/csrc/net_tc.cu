@@ -17,8 +17,8 @@
 // lies on, with a single-tap add-back where two edges meet), in FP32 from
 // the same BF16 inputs, so every node gets the layered result.
 //
-// One CTA (16 worker warps + 1 warp that issues the MMAs) per SM loops over
-// tiles of R x WO output nodes.  Every region of a tile is stored at the
+// One CTA (16 worker warps, 1 warp that issues the MMAs and 3 helper warps)
+// per SM loops over tiles of R x WO output nodes.  Every region of a tile is stored at the
 // pitch PT = WO + 6, so node (ry, rx) of a region has the linear index
 // ry * PT + rx, an M = 128 MMA covers 128 consecutive linear indices ("a
 // chunk"), and a 5x5 tap (cy, cx) is the same buffer shifted by
@@ -43,12 +43,13 @@
 //      the tap's neighbour, N + D from tensor memory, a = out_scale (L + N +
 //      D); then (step mode) v <- C(v + dt (a + f_p / m)), u <- u + dt v,
 //      sphere contact, store.
-// Tiles are pipelined: the input of tile t+1 is staged while the MMAs of
-// tile t run, and the first two chunks of tile t+1 run during the final
-// pass of tile t.  Between the chunks there is no CTA barrier: each worker
-// warp arrives on an accumulator's "free" mbarrier once it has read it, and
-// the issuing thread waits there before it reuses the accumulator; a tile
-// has two CTA barriers (before and after its final pass).  Every wait on
+// Tiles are pipelined: the helper warps stage the input of tile t+1 (step
+// 1) while the chunks of tile t run, and the first two chunks of tile t+1
+// run during the final pass of tile t.  Between the chunks there is no CTA
+// barrier: each worker warp arrives on an accumulator's "free" mbarrier once
+// it has read it, and the issuing thread waits there before it reuses the
+// accumulator; a tile has two CTA barriers (before and after its final
+// pass).  Every wait on
 // the tensor cores is bounded; a timeout sets a status bit and the kernel
 // returns after releasing its tensor memory.
 #include <cuda_bf16.h>
@@ -65,7 +66,8 @@ constexpr int N2 = (R + 2) * PT;                // cell region (origin y0 - 1, x
 constexpr int C2 = (N2 + 127) / 128;            // chunks of the cell region
 constexpr int N0BUF = (C2 * 128 + 4 * PT + 4 + 1 + 15) / 16 * 16;   // input rows the MMAs read
 constexpr int NWORK = 512;                       // 16 worker warps; warps w, w + 4, w + 8, w + 12 share TMEM lanes
-constexpr int NTH = NWORK + 32;                  // + 1 warp that issues the MMAs
+constexpr int NHELP = 96;                        // 3 helper warps: stage the next tile's input
+constexpr int NTH = NWORK + 32 + NHELP;          // + 1 warp that issues the MMAs + the helpers
 constexpr int kNC = 96;                          // MMA N: t [0, 32), q [32, 59), 0 [59, 64), xi [64, 96)
 constexpr int kPairs = 13;                       // 25 taps in K = 16 pairs (the last pair's second tap is 0)
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -110,8 +112,9 @@ constexpr int oBnd = oIn + 2 * N0BUF * 16;          // B of the N + D MMA
 constexpr int oAnd = oBnd + kBnd;                   // A of the N + D MMA [2 accumulators][8][128][8] bf16
 constexpr int kAnd = (kNDK / 8) * 128 * 16;         // bytes of one
 constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);  // edge nodes of a cell region: x = 0, x = W-1, y = 0, y = H-1
+constexpr int kCorr = kSlots * kNC;                 // floats of one tile's edge table
 constexpr int oCorr = oAnd + 2 * kAnd;              // the edge nodes' corrections [kSlots][96] float
-constexpr int oQ = oCorr + kSlots * kNC * 4;        // q [27][NQ] float
+constexpr int oQ = oCorr + kCorr * 4;               // q [27][NQ] float
 constexpr int kUFloats = 6 * UH * UW;
 constexpr int oU = oQ + NQ * 27 * 4;                // u, v [2 tiles][6][UH][UW] float
 constexpr int oPar = oU + 2 * kUFloats * 4;         // bL[3] outs[3] ins[6]
@@ -183,7 +186,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool worker = tid < NWORK, issuer = tid == NWORK;
+    const bool worker = tid < NWORK, issuer = tid == NWORK, helper = tid >= NWORK + 32;
+    const int htid = tid - (NWORK + 32);          // helper thread index
     const int quarter = warp & 3;                 // TMEM lanes [32 quarter, +32) of this warp
     const int cg = (warp >> 2) & 3;               // channel group: columns [8 cg, +8) of t, q and xi
     const uint32_t sbase = tc::smem_u32(sm);
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // edge tile, through the L1 cache)
     const float* gKE = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc);
     const float* gKC = gKE + kKE;
-    float* sCorr = reinterpret_cast<float*>(sm + oCorr);
+    auto sCorr = [&](int) { return reinterpret_cast<float*>(sm + oCorr); };   // one edge table for both tile buffers
     float* sQ = reinterpret_cast<float*>(sm + oQ);
     float* sU = reinterpret_cast<float*>(sm + oU);
     float* sPar = reinterpret_cast<float*>(sm + oPar);
@@ -320,8 +324,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // grid; the raw u, v of the output nodes and their halo also go to FP32
     // tile buffer `buf`, and (step mode) the output nodes' pinned flags to
     // sPin[buf].  Split into a load of input node j0 into registers and its
-    // store to shared memory, so the loads can be in flight while the thread
-    // waits for an MMA.
+    // store to shared memory, so that a helper has all its nodes' loads in
+    // flight at once.
     struct Raw {
         float v[6];
         uint32_t pin;     // the node's pin-mask word; its bit is picked at the store
@@ -367,8 +371,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             stage_store(g, buf, j0, rw);
         }
     };
-    constexpr int kStageParts = (N0 + NWORK - 1) / NWORK;   // input nodes per worker
-    static_assert(kStageParts <= C2, "one staging part per chunk");
+    constexpr int kHelpParts = (N0 + NHELP - 1) / NHELP;   // input nodes per helper
 
     // The edge terms of a tile, from its staged input (workers, once per
     // tile, spread over all of them): for each cell-region node on an edge
@@ -377,10 +380,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // also on a y edge the add-back of the term both corrections removed.
     // Slots: x = 0 by cell row, x = W-1 by cell row, y = 0 by cell column,
     // y = H-1 by cell column.
-    auto edge_prep = [&](const Geo& g, const uint4* in) {
-        constexpr int kGroups = NWORK / kNC;   // node groups: thread -> (column n, group gi)
-        if (tid >= kGroups * kNC) return;
-        const int n = tid % kNC, gi = tid / kNC;
+    auto edge_prep = [&](const Geo& g, const uint4* in, float* corr, int t, int nthr) {
+        const int kGroups = nthr / kNC;   // node groups: thread t -> (column n, group gi)
+        if (t >= kGroups * kNC) return;
+        const int n = t % kNC, gi = t / kNC;
         if (n >= 59 && n < 64) return;   // padding columns: never read
         const int rxE = g.W - g.x0, ryN = g.H - g.y0;   // cell column of x = W-1, cell row of y = H-1
         const bool has[4] = {g.x0 == 0, rxE >= 0 && rxE < WO + 2, g.y0 == 0, ryN >= 0 && ryN < R + 2};
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                         if (yb ? y == g.H - 1 : y == 0)
                             acc = fmaf(kc[yb][0], z[0], fmaf(kc[yb][1], z[1], fmaf(kc[yb][2], z[2], acc)));
                 }
-                sCorr[(base[ed] + i) * kNC + n] = acc;
+                corr[(base[ed] + i) * kNC + n] = acc;
             }
         }
     };
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // s = tanh(t) and xi . s of the channel group [8 cg, +8) into the BF16
     // A operand of the N + D MMA (rows: the chunk's 128 positions); q, the
     // WL partial sums, into sQ (zero outside the cloth: WL's zero padding)
-    auto epilogue = [&](const Geo& g, int c2, int b) {
+    auto epilogue = [&](const Geo& g, int c2, int b, const float* corr) {
         tc::fence_after();
         const int j2 = c2 * 128 + quarter * 32 + lane;
         const int ry2 = j2 / PT, rx2 = j2 % PT;
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         tc::tmem_wait_ld();
         if (valid && (x == 0 || y == 0 || x == g.W - 1 || y == g.H - 1)) {
             auto add = [&](int slot) {
-                const float4* c = reinterpret_cast<const float4*>(sCorr + slot * kNC + 8 * cg);
+                const float4* c = reinterpret_cast<const float4*>(corr + slot * kNC + 8 * cg);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const float4 a = c[j], e = c[8 + j], d = c[16 + j];
@@ -589,17 +592,15 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         return true;
     };
 
-    // ---- the pipeline.  Prologue: stage the first tile and issue its first
-    // two chunks.  The geometry of the tile after the current one is known
-    // one iteration ahead, so its loads have landed when its input is fetched.
+    // ---- the pipeline.  Prologue: stage the first tile, issue its first two
+    // chunks and compute its edge terms.
+    static_assert(C2 >= 2, "two chunks in flight");
     int tile = skip((int)blockIdx.x);
     int buf = 0;
-    Geo g{}, gn{};
     int tn = n_tiles;
     if (tile < n_tiles) {
-        g = geo(tile);
+        const Geo g = geo(tile);
         tn = skip(tile + (int)gridDim.x);
-        if (tn < n_tiles) gn = geo(tn);
         if (worker) {
             stage(g, 0);
             tc::fence_async_smem();
@@ -607,78 +608,86 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         __syncthreads();
         if (issuer) {
             issue_chunk(0, 0);
-            if (C2 > 1) issue_chunk(1, 0);
+            issue_chunk(1, 0);
         }
-        if (worker) edge_prep(g, sIn(0));
+        if (worker) edge_prep(g, sIn(0), sCorr(0), tid, NWORK);
         __syncthreads();
     }
     while (tile < n_tiles && !timed_out) {
         const bool has_next = tn < n_tiles;
-
-        // 2-3. the chunks of this tile, double-buffered in TMEM (chunk c+1
-        // runs while the workers read chunk c).  Each worker loads its input
-        // nodes of the next tile up front and stores one after each of the
-        // first chunks' epilogues, so the loads have the MMAs' time to land.
-        Raw rw[kStageParts];
-        if (worker && has_next) {
-#pragma unroll
-            for (int k = 0; k < kStageParts; ++k)
-                if (tid + k * NWORK < N0) stage_load(gn, tid + k * NWORK, rw[k]);
-        }
-        // the next tile's descriptor (8 x 16 bytes), stored after chunk 0
-        constexpr int kDescV = (int)(sizeof(ClothDesc) / sizeof(uint4));
-        static_assert(sizeof(ClothDesc) % sizeof(uint4) == 0 && kDescV <= NWORK, "descriptor copy");
-        uint4 dv = make_uint4(0, 0, 0, 0);
-        if (STEP && has_next && tid < kDescV) dv = reinterpret_cast<const uint4*>(A.desc + gn.cloth)[tid];
-        // the tile after next: its geometry loads land during the chunks
         const int tnn = has_next ? skip(tn + (int)gridDim.x) : n_tiles;
-        Geo gnn{};
-        if (tnn < n_tiles) gnn = geo(tnn);
-        // No CTA barrier between the chunks: each worker warp reports its
-        // reads of an accumulator (and its part of the N + D operand) on that
-        // accumulator's "free" barrier; the issuer waits there, issues the
-        // chunk's N + D MMA and then reuses the accumulator; after the last
-        // chunk's N + D it commits to bar_nd, which the final pass waits for.
+        // the geometry each role needs: the workers this tile's and (for its
+        // edge terms) the next one's, the helpers the next one's
+        Geo g{}, gn{};
+        if (helper) {
+            if (has_next) gn = geo(tn);
+        } else if (worker) {
+            g = geo(tile);
+            if (has_next) gn = geo(tn);
+        }
         bool ok = true;
-        for (int c2 = 0; c2 < C2; ++c2) {
-            const int b = c2 & 1;
-            if (worker) {
-                if (ok) ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
-                if (ok) epilogue(g, c2, b);
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(bar_free(b));   // also after a timeout: the issuer's wait ends
+        if (helper) {
+            // 1. the next tile's input, descriptor and pinned flags while this
+            // tile's chunks run, all of a helper's input nodes in flight at once
+            if (has_next) {
+                constexpr int kDescV = (int)(sizeof(ClothDesc) / sizeof(uint4));
+                static_assert(sizeof(ClothDesc) % sizeof(uint4) == 0 && kDescV <= NHELP, "descriptor copy");
+                if (STEP && htid < kDescV)
+                    reinterpret_cast<uint4*>(sD + (buf ^ 1))[htid] = reinterpret_cast<const uint4*>(A.desc + gn.cloth)[htid];
+                constexpr int kBatch = kHelpParts;   // input nodes in flight per helper
+#pragma unroll 1
+                for (int k0 = 0; k0 < kHelpParts; k0 += kBatch) {
+                    Raw rw[kBatch];
 #pragma unroll
-                for (int k = 0; k < kStageParts; ++k)   // register-indexed: k is a constant here
-                    if (k == c2 && has_next && tid + k * NWORK < N0) stage_store(gn, buf ^ 1, tid + k * NWORK, rw[k]);
-                if (STEP && c2 == 0 && has_next && tid < kDescV) reinterpret_cast<uint4*>(sD + (buf ^ 1))[tid] = dv;
+                    for (int k = 0; k < kBatch; ++k)
+                        if (htid + (k0 + k) * NHELP < N0) stage_load(gn, htid + (k0 + k) * NHELP, rw[k]);
+#pragma unroll
+                    for (int k = 0; k < kBatch; ++k)
+                        if (htid + (k0 + k) * NHELP < N0) stage_store(gn, buf ^ 1, htid + (k0 + k) * NHELP, rw[k]);
+                }
+                tc::fence_async_smem();   // the staged input, for the tensor cores
             }
-            ph[b] ^= 1u;
-            if (issuer && ok) {
-                ok = wait_free(b);
-                if (ok) {
-                    issue_nd(c2);
-                    if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
-                    if (c2 == C2 - 1) tc::mma_commit(bar_nd);
+        } else {
+            // 2-3. the chunks of this tile, double-buffered in TMEM (chunk c+1
+            // runs while the workers read chunk c).  No CTA barrier between
+            // them: each worker warp reports its reads of an accumulator (and
+            // its part of the N + D operand) on that accumulator's "free"
+            // barrier; the issuer waits there, issues the chunk's N + D MMA and
+            // then reuses the accumulator; after the last chunk's N + D it
+            // commits to bar_nd, which the final pass waits for.
+            for (int c2 = 0; c2 < C2; ++c2) {
+                const int b = c2 & 1;
+                if (worker) {
+                    if (ok) ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
+                    if (ok) epilogue(g, c2, b, sCorr(buf));
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bar_free(b));   // also after a timeout: the issuer's wait ends
+                }
+                ph[b] ^= 1u;
+                if (issuer && ok) {
+                    ok = wait_free(b);
+                    if (ok) {
+                        issue_nd(c2);
+                        if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
+                        if (c2 == C2 - 1) tc::mma_commit(bar_nd);
+                    }
                 }
             }
         }
 
         // the next tile's first two chunks run during this tile's final pass
-        if (worker) tc::fence_async_smem();   // the staged input, for the tensor cores
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         if (issuer && has_next) {   // the accumulators were freed by the last two chunks
             issue_chunk(0, buf ^ 1);
-            if (C2 > 1) issue_chunk(1, buf ^ 1);
+            issue_chunk(1, buf ^ 1);
         }
         if (worker) {
             if (!final_pass(g, buf)) ok = false;
-            if (has_next) edge_prep(gn, sIn(buf ^ 1));   // this tile's epilogues are done
+            if (has_next) edge_prep(gn, sIn(buf ^ 1), sCorr(buf ^ 1), tid, NWORK);   // this tile's epilogues are done
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tile = tn;
         tn = tnn;
-        g = gn;
-        gn = gnn;
         buf ^= 1;
     }
 
