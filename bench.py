@@ -72,6 +72,25 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes of one SM (4 schedulers x 32)
+
+
+def fp32_alu_peak(dev):
+    """CUDA-core FP32 peak in TFLOP/s from the unit counts and the maximum SM
+    clock: SMs x 128 FMA lanes x 2 flop x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        idx = torch.cuda.current_device() if dev is None else torch.device(dev).index or 0
+        r = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i", str(idx)],
+                           capture_output=True, text=True, timeout=20)
+        mhz = float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz
+
+
 def kernel_hash(files) -> str:
     h = hashlib.sha256()
     for f in files:
@@ -486,11 +505,11 @@ def run_cnn(args, dev):
         net = Net(blob, prec, device=dev)
         cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
         cn.set_state(x0, v0)
-        tile = None
-        if prec == FP32:   # the FP32 step's tile shape from the launch tuner (the state does not move)
-            from paper_2403_12820_gb300 import tune
-            rec = tune.autotune_net(cn, net, warmup=3, steps=20)
-            tile = {"tile_cols": rec["tile_cols"], "candidates_us": {str(c): round(t, 2) for c, t in rec["candidates"]}}
+        # the step's tile shape from the launch tuner (the state does not move)
+        from paper_2403_12820_gb300 import tune
+        rec = tune.autotune_net(cn, net, warmup=3, steps=20)
+        shape = lambda ch: f"{ch['rows']}x{ch['cols']} {ch['kind']}"
+        tile = {"shape": shape(rec["shape"]), "candidates_us": {shape(ch): round(t, 2) for ch, t in rec["candidates"]}}
         cn.step_net(net, 3)
         steps = args.cnn_steps
         t = timed_segments(cn, lambda k: cn.step_net(net, k), steps)
@@ -505,11 +524,16 @@ def run_cnn(args, dev):
                      "within_1pct_of_width": e["error_rel_width"] <= 0.01,
                      "achieved_tflops": tflops, "gpu_launches_per_step": 1, "timed_as": "segments of 100 steps",
                      "status_word": cn.status()}
-        if tile is not None:
-            out[name]["tile"] = tile
-        if prec == BF16:
+        out[name]["tile"] = tile
+        if prec == BF16 or rec["shape"]["kind"] == "tensor":
             out[name]["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                                      "frac": tflops / bf16_peak, "peak_kind": f"{peak_kind} (cuBLAS bf16 burst)",
+                                     "algorithmic_flop_per_node": CNN_FLOP_PER_NODE}
+        else:   # the FP32 step runs on the CUDA cores
+            alu, sms, mhz = fp32_alu_peak(dev)
+            out[name]["roofline"] = {"bound": "alu", "achieved": tflops, "peak": alu, "unit": "TFLOP/s",
+                                     "frac": tflops / alu,
+                                     "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz",
                                      "algorithmic_flop_per_node": CNN_FLOP_PER_NODE}
         cn.close()
         net.close()

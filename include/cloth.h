@@ -249,19 +249,26 @@ int cloth_tune_launch(cloth_ctx* ctx, int32_t n, const int32_t* seg_rows, const 
  * the default), number of work units. */
 int cloth_get_launch(const cloth_ctx* ctx, int32_t* seg_rows, int32_t* warps_per_sm, int32_t* n_units);
 
-/* Tile shapes of the FP32 network step (the fused CUDA-core kernel of
- * cloth_step_net / cloth_rollout_net for a CLOTH_NET_FP32 network, Fig. 2):
- * output tiles of 14 rows x tile_cols columns.  cloth_net_tile_choices
- * writes the available tile_cols (at most `capacity` of them, host array)
- * and their number (*count); the first is the default.  Host only. */
-int cloth_net_tile_choices(int32_t* cols, int32_t capacity, int32_t* count);
+/* Tile shapes of the fused network step of cloth_step_net /
+ * cloth_rollout_net (Fig. 2) for networks of `precision`.  Choice v has
+ * output tiles of rows[v] x cols[v] nodes on kinds[v]: 0 = the CUDA cores
+ * (FP32), 1 = the tensor cores (tcgen05; for CLOTH_NET_FP32 each FP32 product
+ * as three BF16 products, hi hi + hi lo + lo hi, of the operands split into a
+ * high and a low BF16 part, with tanh and N + D in FP32).  FP32: two
+ * tensor-core shapes (10 and 6 rows), then three CUDA-core shapes; BF16:
+ * three tensor-core shapes (14, 10 and 6 rows).  Writes at most `capacity` entries to the host arrays and the
+ * number of choices to *count; choice 0 is the default.  CLOTH_EINVAL for
+ * another precision.  Host only. */
+int cloth_net_tile_choices(int32_t precision, int32_t* rows, int32_t* cols, int32_t* kinds, int32_t capacity,
+                           int32_t* count);
 
-/* Select the FP32 network step's tile width (one of the choices; else
- * CLOTH_EINVAL).  Results are the same in every shape, bit for bit (each
- * node's arithmetic does not depend on the tiling); only the speed differs.
- * Cached network-rollout graphs are dropped when it changes. */
-int cloth_set_net_tile(cloth_ctx* ctx, int32_t tile_cols);
-int cloth_get_net_tile(const cloth_ctx* ctx, int32_t* tile_cols);
+/* Select the tile shape of the precision's network step (a choice index;
+ * else CLOTH_EINVAL).  Shapes of one kind give the same results, bit for bit
+ * (each node's arithmetic does not depend on the tiling); the FP32 shapes of
+ * the two kinds agree within the FP32 tolerance.  Cached network-rollout
+ * graphs are dropped when it changes. */
+int cloth_set_net_tile(cloth_ctx* ctx, int32_t precision, int32_t choice);
+int cloth_get_net_tile(const cloth_ctx* ctx, int32_t precision, int32_t* choice);
 
 
 /* Topology as the step kernels see it: for every node of cloth b, bit s of
@@ -398,17 +405,17 @@ int cloth_net_workspace_size(const cloth_ctx* ctx, int32_t precision, size_t* by
  * (the tile list). */
 int cloth_step_net(cloth_ctx* ctx, const cloth_net* net, int32_t steps, void* d_work, size_t bytes, void* stream);
 
-/* Launch-shape tuner of the FP32 network step: runs `warmup` untimed and
- * `steps` timed network steps of `net` in every tile shape (CUDA events on
- * `stream`; each step reads the current state and writes the other buffer,
- * so the state does not move), writes microseconds per step to us_out[v]
- * (host, one per choice, in the order of cloth_net_tile_choices), selects
- * the fastest and writes its tile width to *best_cols (host).  d_work is a
- * device workspace of cloth_net_workspace_size(ctx, CLOTH_NET_FP32) bytes.
- * CLOTH_EUNSUPPORTED for a BF16 network (the tensor-core step has one
- * shape).  Cached graphs are dropped.  Synchronises `stream`. */
-int cloth_tune_net(cloth_ctx* ctx, const cloth_net* net, int32_t warmup, int32_t steps, float* us_out,
-                   int32_t* best_cols, void* d_work, size_t bytes, void* stream);
+/* Launch-shape tuner of the network step: runs `warmup` untimed and `steps`
+ * timed network steps of `net` in every tile shape of its precision (CUDA
+ * events on `stream`; each step reads the current state and writes the
+ * other buffer, so the state does not move), writes microseconds per step
+ * to us_out[v] (host, one per choice, in the order of
+ * cloth_net_tile_choices), selects the fastest and writes its index to
+ * *best (host).  d_work is a device workspace of
+ * cloth_net_workspace_size(ctx, precision) bytes.  Cached graphs are
+ * dropped.  Synchronises `stream`. */
+int cloth_tune_net(cloth_ctx* ctx, const cloth_net* net, int32_t warmup, int32_t steps, float* us_out, int32_t* best,
+                   void* d_work, size_t bytes, void* stream);
 
 /* Network rollout with the plain step as fallback and judge (Fig. 2: the
  * framework couples the network with the physics-based simulator).

@@ -61,9 +61,9 @@ SIGNATURES = {
     "cloth_topology": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     "cloth_set_launch": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
     "cloth_get_launch": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int32)]),
-    "cloth_net_tile_choices": (c_int32, [P(c_int32), c_int32, P(c_int32)]),
-    "cloth_set_net_tile": (c_int32, [c_void_p, c_int32]),
-    "cloth_get_net_tile": (c_int32, [c_void_p, P(c_int32)]),
+    "cloth_net_tile_choices": (c_int32, [c_int32, P(c_int32), P(c_int32), P(c_int32), c_int32, P(c_int32)]),
+    "cloth_set_net_tile": (c_int32, [c_void_p, c_int32, c_int32]),
+    "cloth_get_net_tile": (c_int32, [c_void_p, c_int32, P(c_int32)]),
     "cloth_tune_net": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, P(c_float), P(c_int32), c_void_p,
                                  ctypes.c_size_t, c_void_p]),
     "cloth_set_boundary": (c_int32, [c_void_p, c_int32, P(c_float), c_float, c_void_p]),

@@ -165,26 +165,27 @@ class ClothBatch:
         _lib.call("cloth_set_boundary", self.handle, int(b), (ctypes.c_float * 3)(*[float(a) for a in pin_v]),
                   ctypes.c_float(friction), self._s())
 
-    def set_net_tile(self, tile_cols: int) -> None:
-        """Tile width of the FP32 network step (one of tune.net_tile_choices())."""
-        _lib.call("cloth_set_net_tile", self.handle, int(tile_cols))
+    def set_net_tile(self, precision: int, choice: int) -> None:
+        """Tile shape of the network step for networks of `precision` (an
+        index into tune.net_tile_choices(precision))."""
+        _lib.call("cloth_set_net_tile", self.handle, int(precision), int(choice))
 
-    def get_net_tile(self) -> int:
+    def get_net_tile(self, precision: int) -> int:
         c = ctypes.c_int32()
-        _lib.call("cloth_get_net_tile", self.handle, ctypes.byref(c))
+        _lib.call("cloth_get_net_tile", self.handle, int(precision), ctypes.byref(c))
         return c.value
 
     def tune_net(self, net, warmup: int = 3, steps: int = 10) -> tuple[int, list[float]]:
-        """Time the FP32 network step in every tile shape (cloth_tune_net; the
-        state does not move) and apply the fastest.  Returns (its tile width,
-        us per step of each choice)."""
+        """Time the network step of `net` in every tile shape of its precision
+        (cloth_tune_net; the state does not move) and apply the fastest.
+        Returns (its choice index, us per step of each choice)."""
         ws = self.net_workspace(net.precision)
         us = (ctypes.c_float * 16)()
         best = ctypes.c_int32()
         _lib.call("cloth_tune_net", self.handle, net.handle, int(warmup), int(steps), us, ctypes.byref(best),
                   _ptr(ws), ws.numel(), self._s())
         from .tune import net_tile_choices
-        n = len(net_tile_choices())
+        n = len(net_tile_choices(net.precision))
         return best.value, [float(us[i]) for i in range(n)]
 
     def get_launch(self) -> tuple[int, int, int]:

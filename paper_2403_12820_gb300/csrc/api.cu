@@ -113,7 +113,8 @@ struct cloth_ctx {
     int grid = 0, block = 128;
     int warps_per_sm = 0;              // 0: the plain-step kernel's occupancy
     int net_stride = 1;                // plain steps one network step spans
-    int comp_variant = 0;              // tile shape of the FP32 network step (net_comp_variant_cols)
+    int fp32_tile = 0;                 // tile shape of the FP32 network step (a choice of tile_shape)
+    int bf16_tile = 0;                 // tile shape of the BF16 network step (a choice of tile_shape)
     int train_seg = 0;                 // Eq. 8 unroll: keep every train_seg-th state (0: all)
     int sm_count = 0;
     cudaStream_t cap = nullptr;        // private stream for graph capture
@@ -283,39 +284,69 @@ std::vector<int4> net_tiles(const cloth_ctx* c, int R, int WO)
     return t;
 }
 // of the fused tensor-core (BF16) and CUDA-core (FP32) network steps
-std::vector<int4> tc_tiles(const cloth_ctx* c) { return net_tiles(c, net_tc_tile_rows(), net_tc_tile_cols()); }
-std::vector<int4> comp_tiles(const cloth_ctx* c, int variant)
+// Tile shapes of a precision's fused step: FP32 choice v < net_tc_split_variants()
+// is the tensor-core kernel with three BF16 products per term in shape v (the
+// default, the faster kind), the next ones the CUDA-core kernel in shape
+// v - net_tc_split_variants(); BF16 choice v the tensor-core kernel in shape v.
+int tile_choices(int precision)
 {
-    return net_tiles(c, net_comp_tile_rows(), net_comp_variant_cols(variant));
+    return precision == CLOTH_NET_BF16 ? net_tc_variants() : net_tc_split_variants() + net_comp_variants();
 }
-std::vector<int4> comp_tiles(const cloth_ctx* c) { return comp_tiles(c, c->comp_variant); }
+bool fp32_split(int v) { return v < net_tc_split_variants(); }
+int fp32_comp(int v) { return v - net_tc_split_variants(); }
+void tile_shape(int precision, int v, int* rows, int* cols, int* kind)
+{
+    if (precision == CLOTH_NET_BF16) {
+        *rows = net_tc_variant_rows(v); *cols = net_tc_tile_cols(); *kind = 1;
+    } else if (fp32_split(v)) {
+        *rows = net_tc_split_rows(v); *cols = net_tc_tile_cols(); *kind = 1;
+    } else {
+        *rows = net_comp_tile_rows(); *cols = net_comp_variant_cols(fp32_comp(v)); *kind = 0;
+    }
+}
+std::vector<int4> shape_tiles(const cloth_ctx* c, int precision, int v)
+{
+    int rows, cols, kind;
+    tile_shape(precision, v, &rows, &cols, &kind);
+    return net_tiles(c, rows, cols);
+}
+int& tile_variant(cloth_ctx* c, int precision) { return precision == CLOTH_NET_BF16 ? c->bf16_tile : c->fp32_tile; }
+int tile_variant(const cloth_ctx* c, int precision) { return precision == CLOTH_NET_BF16 ? c->bf16_tile : c->fp32_tile; }
+std::vector<int4> net_step_tiles(const cloth_ctx* c, int precision)
+{
+    return shape_tiles(c, precision, tile_variant(c, precision));
+}
 // kind of a network's tile list (what the workspace holds)
 int list_kind(const cloth_ctx* c, const cloth_net* net)
 {
-    return net->precision == CLOTH_NET_BF16 ? CLOTH_NET_BF16 : 10 + c->comp_variant;
+    return (net->precision == CLOTH_NET_BF16 ? 100 : 10) + tile_variant(c, net->precision);
 }
 
-// One fused network step over the tile list: the tensor-core kernel for a
-// BF16 network (one CTA per SM), the FP32 composite kernel otherwise (in the
-// context's tile shape, as many blocks as are resident).  `mode` restricts
-// it to the cloths in network mode.
+// One fused network step over the tile list, in the context's tile shape for
+// the network's precision: the tensor-core kernel (one CTA per SM) for a
+// BF16 network or the FP32 three-term shape, else the FP32 composite kernel
+// on the CUDA cores (as many blocks as are resident).  `mode` restricts it
+// to the cloths in network mode.
 int launch_net_step(const cloth_ctx* c, const cloth_net* net, const int4* d_tiles, int n_tiles, const float* src,
                     float* dst, const int32_t* mode, cudaStream_t s)
 {
-    if (net->precision == CLOTH_NET_BF16)
-        CK(launch_net_tc_step(net->d_pack(), net->d_w(), c->d_desc(), d_tiles, n_tiles, src, dst, c->d_pins(),
-                              c->d_status(), std::min(n_tiles, c->sm_count), s, mode));
+    const bool bf16 = net->precision == CLOTH_NET_BF16;
+    if (bf16 || fp32_split(c->fp32_tile))
+        CK(launch_net_tc_step(bf16 ? c->bf16_tile : c->fp32_tile, !bf16, net->d_pack(), net->d_w(), c->d_desc(),
+                              d_tiles, n_tiles, src, dst, c->d_pins(), c->d_status(), std::min(n_tiles, c->sm_count),
+                              s, mode));
     else
-        CK(launch_net_comp_step(c->comp_variant, net->d_w(), net->d_comp(), net->d_edge(), c->d_desc(), d_tiles,
-                                n_tiles, src, dst, c->d_pins(), c->d_status(),
-                                std::min(n_tiles, net_comp_blocks_per_sm(c->comp_variant) * c->sm_count), s, mode));
+        CK(launch_net_comp_step(fp32_comp(c->fp32_tile), net->d_w(), net->d_comp(), net->d_edge(), c->d_desc(),
+                                d_tiles, n_tiles, src, dst, c->d_pins(), c->d_status(),
+                                std::min(n_tiles, net_comp_blocks_per_sm(fp32_comp(c->fp32_tile)) * c->sm_count), s,
+                                mode));
     return CLOTH_OK;
 }
 
 // The network's tile list in the workspace (uploaded once per workspace and precision).
 int net_tile_list(cloth_ctx* c, const cloth_net* net, void* d_work, size_t bytes, int* n_tiles, cudaStream_t s)
 {
-    const std::vector<int4> tiles = net->precision == CLOTH_NET_BF16 ? tc_tiles(c) : comp_tiles(c);
+    const std::vector<int4> tiles = net_step_tiles(c, net->precision);
     if (bytes < sizeof(int4) * tiles.size()) return CLOTH_ENOMEM;
     if (c->lists_written != d_work || c->lists_kind != list_kind(c, net)) {
         CK(cudaMemcpyAsync(d_work, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
@@ -749,9 +780,8 @@ int cloth_reset_modes(cloth_ctx* c, void* stream)
 int cloth_net_workspace_size(const cloth_ctx* c, int32_t precision, size_t* bytes)
 {
     if (!c || !bytes || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
-    size_t n = precision == CLOTH_NET_BF16 ? tc_tiles(c).size() : 0;
-    if (precision != CLOTH_NET_BF16)   // room for the list of any FP32 tile shape
-        for (int v = 0; v < net_comp_variants(); ++v) n = std::max(n, comp_tiles(c, v).size());
+    size_t n = 0;   // room for the list of any tile shape of the precision
+    for (int v = 0; v < tile_choices(precision); ++v) n = std::max(n, shape_tiles(c, precision, v).size());
     *bytes = align_up(sizeof(int4) * n, kAlign);
     return CLOTH_OK;
 }
@@ -1039,40 +1069,38 @@ int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const in
     return CLOTH_OK;
 }
 
-int cloth_net_tile_choices(int32_t* cols, int32_t capacity, int32_t* count)
+int cloth_net_tile_choices(int32_t precision, int32_t* rows, int32_t* cols, int32_t* kinds, int32_t capacity,
+                           int32_t* count)
 {
-    if (!count || capacity < 0 || (capacity > 0 && !cols)) return CLOTH_EINVAL;
-    *count = net_comp_variants();
-    for (int v = 0; v < net_comp_variants() && v < capacity; ++v) cols[v] = net_comp_variant_cols(v);
+    if (!count || capacity < 0 || (capacity > 0 && (!rows || !cols || !kinds))) return CLOTH_EINVAL;
+    if (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16) return CLOTH_EINVAL;
+    *count = tile_choices(precision);
+    for (int v = 0; v < *count && v < capacity; ++v) tile_shape(precision, v, &rows[v], &cols[v], &kinds[v]);
     return CLOTH_OK;
 }
 
-int cloth_set_net_tile(cloth_ctx* c, int32_t tile_cols)
+int cloth_set_net_tile(cloth_ctx* c, int32_t precision, int32_t choice)
 {
-    if (!c) return CLOTH_EINVAL;
-    for (int v = 0; v < net_comp_variants(); ++v)
-        if (net_comp_variant_cols(v) == tile_cols) {
-            if (v != c->comp_variant) {
-                drop_graphs(c);   // the captured network steps use the old shape
-                c->comp_variant = v;
-            }
-            return CLOTH_OK;
-        }
-    return CLOTH_EINVAL;
+    if (!c || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
+    if (choice < 0 || choice >= tile_choices(precision)) return CLOTH_EINVAL;
+    if (choice != tile_variant(c, precision)) {
+        drop_graphs(c);   // the captured network steps use the old shape
+        tile_variant(c, precision) = choice;
+    }
+    return CLOTH_OK;
 }
 
-int cloth_get_net_tile(const cloth_ctx* c, int32_t* tile_cols)
+int cloth_get_net_tile(const cloth_ctx* c, int32_t precision, int32_t* choice)
 {
-    if (!c || !tile_cols) return CLOTH_EINVAL;
-    *tile_cols = net_comp_variant_cols(c->comp_variant);
+    if (!c || !choice || (precision != CLOTH_NET_FP32 && precision != CLOTH_NET_BF16)) return CLOTH_EINVAL;
+    *choice = tile_variant(c, precision);
     return CLOTH_OK;
 }
 
 int cloth_tune_net(cloth_ctx* c, const cloth_net* net, int32_t warmup, int32_t steps, float* us_out,
-                   int32_t* best_cols, void* d_work, size_t bytes, void* stream)
+                   int32_t* best, void* d_work, size_t bytes, void* stream)
 {
-    if (!c || !net || !us_out || !best_cols || !d_work || warmup < 0 || steps < 1) return CLOTH_EINVAL;
-    if (net->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;   // the tensor-core step has one shape
+    if (!c || !net || !us_out || !best || !d_work || warmup < 0 || steps < 1) return CLOTH_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_work) % kAlign) return CLOTH_EINVAL;
     size_t need = 0;
     int rc = cloth_net_workspace_size(c, net->precision, &need);
@@ -1087,9 +1115,10 @@ int cloth_tune_net(cloth_ctx* c, const cloth_net* net, int32_t warmup, int32_t s
     // so the state the caller sees does not move
     const float* src = c->d_state(c->cur);
     float* dst = c->d_state(c->cur ^ 1);
-    const int nv = net_comp_variants();
+    const int nv = tile_choices(net->precision);
+    int& var = tile_variant(c, net->precision);
     for (int v = 0; v < nv && rc == CLOTH_OK && ce == cudaSuccess; ++v) {
-        c->comp_variant = v;
+        var = v;
         int n_tiles = 0;
         rc = net_tile_list(c, net, d_work, bytes, &n_tiles, s);
         const int4* tl = static_cast<const int4*>(d_work);
@@ -1106,13 +1135,13 @@ int cloth_tune_net(cloth_ctx* c, const cloth_net* net, int32_t warmup, int32_t s
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (ce != cudaSuccess) { c->comp_variant = 0; return cuda_fail(ce); }
-    if (rc) { c->comp_variant = 0; return rc; }
+    if (ce != cudaSuccess) { var = 0; return cuda_fail(ce); }
+    if (rc) { var = 0; return rc; }
     int b = 0;
     for (int v = 1; v < nv; ++v)
         if (us_out[v] < us_out[b]) b = v;
-    c->comp_variant = b;
-    *best_cols = net_comp_variant_cols(b);
+    var = b;
+    *best = b;
     return CLOTH_OK;
 }
 

@@ -81,16 +81,24 @@ __device__ inline float trunk_composite(const float* __restrict__ w, int n, int 
     return s;
 }
 
-// Tensor-core (tcgen05, BF16) fused cell / network step (net_tc.cu).
+// Tensor-core (tcgen05, BF16) fused cell / network step (net_tc.cu): tiles
+// of net_tc_variant_rows(v) x net_tc_tile_cols() output nodes for one of
+// net_tc_variants() BF16 tile shapes v (0: the default), and the FP32 step
+// as three BF16 products per term (hi hi + hi lo + lo hi, "split") on tiles
+// of net_tc_split_rows(k) rows for one of net_tc_split_variants() shapes k;
+// launch_net_tc_step takes v, or k when `split`.
 cudaError_t net_tc_init();
 int net_tc_pack_bytes();
 int net_tc_edge_offset();   // bytes from the pack's start to the FP32 edge and corner terms
-int net_tc_tile_rows();
 int net_tc_tile_cols();
+int net_tc_variants();
+int net_tc_variant_rows(int v);
+int net_tc_split_variants();
+int net_tc_split_rows(int k);
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s);
-cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDesc* desc, const int4* tiles, int n_tiles,
-                               const float* src, float* dst, const uint32_t* pinmask, int32_t* status, int grid,
-                               cudaStream_t s, const int32_t* mode = nullptr);
+cudaError_t launch_net_tc_step(int variant, bool split, const void* wpack, const float* w, const ClothDesc* desc,
+                               const int4* tiles, int n_tiles, const float* src, float* dst, const uint32_t* pinmask,
+                               int32_t* status, int grid, cudaStream_t s, const int32_t* mode = nullptr);
 cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
                                   int32_t* status, int grid, cudaStream_t s);
 // FP32 fused network step with the composite trunk (net_comp.cu): tiles of

@@ -60,18 +60,13 @@
 namespace cloth {
 namespace {
 
-constexpr int R = 14, WO = 26, PT = WO + 6;   // output rows, output columns, region pitch
-constexpr int N0 = (R + 6) * PT;                // input-region nodes of a tile (origin y0 - 3, x0 - 3)
-constexpr int N2 = (R + 2) * PT;                // cell region (origin y0 - 1, x0 - 1)
-constexpr int C2 = (N2 + 127) / 128;            // chunks of the cell region
-constexpr int N0BUF = (C2 * 128 + 4 * PT + 4 + 1 + 15) / 16 * 16;   // input rows the MMAs read
+constexpr int WO = 26, PT = WO + 6;              // output columns, region pitch
 constexpr int NWORK = 512;                       // 16 worker warps; warps w, w + 4, w + 8, w + 12 share TMEM lanes
 constexpr int NHELP = 96;                        // 3 helper warps: stage the next tile's input
 constexpr int NTH = NWORK + 32 + NHELP;          // + 1 warp that issues the MMAs + the helpers
 constexpr int kNC = 96;                          // MMA N: t [0, 32), q [32, 59), 0 [59, 64), xi [64, 96)
 constexpr int kPairs = 13;                       // 25 taps in K = 16 pairs (the last pair's second tap is 0)
 constexpr uint32_t kWaitLimit = 1u << 24;
-static_assert(N0BUF >= N0 && N0BUF >= C2 * 128 + 4 * PT + 4 + 1, "input buffer");
 
 // composite tap c = 5 cy + cx reads the input-region row j2 + cy * PT + cx
 // of cell-region node j2
@@ -96,49 +91,72 @@ constexpr int kKD = 2 * 5 * 3 * kNC;
 constexpr int kNDN = 16, kNDK = 64;
 constexpr int kOffBnd = kBc + (kKE + kKC + kKD) * 4;
 constexpr int kBnd = kNDK * kNDN * 2;
-constexpr int kPack = kOffBnd + kBnd;
-static_assert(kPack % 16 == 0, "pack");
+// The three-term split of the FP32 step: B = Bhi + Blo with Bhi the BF16 B
+// above and Blo = BF16(B - Bhi) in the same layout, and the defects KD2 =
+// B - (Bhi + Blo) in KD's layout.
+constexpr int kOffBlo = kOffBnd + kBnd;
+constexpr int kOffKD2 = kOffBlo + kBc;
+constexpr int kPack = kOffKD2 + kKD * 4;
+static_assert(kPack % 16 == 0 && kOffBlo % 16 == 0, "pack");
 
-// FP32 u, v of the output nodes and their 1-node halo, for the update
-constexpr int UH = R + 2, UW = WO + 2;
-// q is kept for the valid cell-region positions only: (R+2) x (WO+2), one
-// plane per value
-constexpr int NQ = (R + 2) * (WO + 2);
-
-// shared memory map (bytes)
-constexpr int oBc = 0;
-constexpr int oIn = oBc + kBc;                      // input [2 tiles][N0BUF][8] bf16
-constexpr int oBnd = oIn + 2 * N0BUF * 16;          // B of the N + D MMA
-constexpr int oAnd = oBnd + kBnd;                   // A of the N + D MMA [2 accumulators][8][128][8] bf16
-constexpr int kAnd = (kNDK / 8) * 128 * 16;         // bytes of one
-constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);  // edge nodes of a cell region: x = 0, x = W-1, y = 0, y = H-1
-constexpr int kCorr = kSlots * kNC;                 // floats of one tile's edge table
-constexpr int oCorr = oAnd + 2 * kAnd;              // the edge nodes' corrections [kSlots][96] float
-constexpr int oQ = oCorr + kCorr * 4;               // q [27][NQ] float
-constexpr int kUFloats = 6 * UH * UW;
-constexpr int oU = oQ + NQ * 27 * 4;                // u, v [2 tiles][6][UH][UW] float
-constexpr int oPar = oU + 2 * kUFloats * 4;         // bL[3] outs[3] ins[6]
-constexpr int oDesc = oPar + 16 * 4;                // the two tiles' cloth descriptors
-constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
-constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;   // mbarriers of the two accumulators; TMEM address
-// accumulator b full (MMAs done) at b, free (16 warps read it and wrote
-// their part of the N + D operand) at 2 + b, the tile's N + D done at 4, the
-// tear-down drain at 5
+constexpr int UW = WO + 2;
+constexpr int kAnd = (kNDK / 8) * 128 * 16;      // bytes of one N + D operand [8][128][8] bf16
+// mbarriers: accumulator b full (MMAs done) at b, free (16 warps read it and
+// wrote their part of the N + D operand) at 2 + b, the tile's N + D done at
+// 4, the tear-down drain at 5
 constexpr int kNumBars = 6;
-constexpr int oTmemSlot = oBar + 8 * kNumBars;
-constexpr int kSmem = oTmemSlot + 16;
-static_assert(kSmem <= 232448, "shared memory");
-static_assert(oIn % 16 == 0 && oBnd % 16 == 0 && oAnd % 16 == 0 && oCorr % 16 == 0 && oQ % 16 == 0 && oU % 16 == 0 &&
-                  oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0 && kOffBnd % 16 == 0,
-              "alignment");
-
 // TMEM columns: accumulator b at [96 b, +96), N + D of chunk c at
 // [192 + 16 c, +16)
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kTmemND = 2 * kNC;
-static_assert(kTmemND + C2 * kNDN <= kTmemCols, "tensor memory columns");
-static_assert(C2 * 4 == NWORK / 32 && N2 <= C2 * 128 && PT == 32,
-              "the final pass gives each worker warp one region row: 4 chunks x 4 lane quarters");
+
+// A tile shape: C2 chunks of 128 cell-region nodes = C2 * 4 rows of PT, so
+// R = 4 C2 - 2 output rows of WO columns.  SPLIT: the FP32 step, each BF16
+// operand as a high and a low part (three MMAs per product: hi hi, hi lo,
+// lo hi), N + D and tanh in FP32 on the CUDA cores.
+template <int C2V, bool SPLITV>
+struct TcShape {
+    static constexpr int C2 = C2V;
+    static constexpr bool SPLIT = SPLITV;
+    static constexpr int R = 4 * C2 - 2;                  // output rows
+    static constexpr int N0 = (R + 6) * PT;               // input-region nodes of a tile (origin y0 - 3, x0 - 3)
+    static constexpr int N2 = (R + 2) * PT;               // cell region (origin y0 - 1, x0 - 1)
+    static constexpr int N0BUF = (C2 * 128 + 4 * PT + 4 + 1 + 15) / 16 * 16;   // input rows the MMAs read
+    static constexpr int kParts = SPLIT ? 2 : 1;          // BF16 parts of each operand
+    // FP32 u, v of the output nodes and their 1-node halo, for the update
+    static constexpr int UH = R + 2;
+    // q is kept for the valid cell-region positions only: (R+2) x (WO+2),
+    // one plane per value
+    static constexpr int NQ = (R + 2) * (WO + 2);
+    static constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);   // edge nodes: x = 0, x = W-1, y = 0, y = H-1
+    static constexpr int kCorr = kSlots * kNC;            // floats of one tile's edge table
+    static constexpr int kUFloats = 6 * UH * UW;
+    // shared memory map (bytes)
+    static constexpr int oBc = 0;                         // B [part][pair][khalf][96][8] bf16
+    static constexpr int oIn = oBc + kParts * kBc;        // input [2 tiles][part][N0BUF][8] bf16
+    static constexpr int oBnd = oIn + 2 * kParts * N0BUF * 16;   // B of the N + D MMA (BF16 only)
+    static constexpr int oAnd = oBnd + (SPLIT ? 0 : kBnd);       // A of the N + D MMA [2 accumulators] (BF16 only)
+    static constexpr int oCorr = oAnd + (SPLIT ? 0 : 2 * kAnd);  // the edge nodes' corrections [kSlots][96] float
+    static constexpr int oQ = oCorr + kCorr * 4;          // q [27][NQ] float
+    // SPLIT: the N + D partial sums of the 4 channel groups [4][3][C2 * 128] float
+    static constexpr int oND = oQ + NQ * 27 * 4;
+    static constexpr int kNDp = SPLIT ? 4 * 3 * C2 * 128 : 0;
+    static constexpr int oU = oND + kNDp * 4;             // u, v [2 tiles][6][UH][UW] float
+    static constexpr int oPar = oU + 2 * kUFloats * 4;    // bL[3] outs[3] ins[6] (SPLIT: + WN[3][32], WD[3][32])
+    static constexpr int kParFloats = SPLIT ? 16 + 6 * 32 : 16;
+    static constexpr int oDesc = oPar + kParFloats * 4;   // the two tiles' cloth descriptors
+    static constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
+    static constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;  // mbarriers; TMEM address
+    static constexpr int oTmemSlot = oBar + 8 * kNumBars;
+    static constexpr int kSmem = oTmemSlot + 16;
+    static_assert(C2 >= 2 && C2 <= 4, "two chunks in flight; the final pass gives each worker warp one region row");
+    static_assert(N0BUF >= N0 && N0BUF >= C2 * 128 + 4 * PT + 4 + 1, "input buffer");
+    static_assert(kSmem <= 232448, "shared memory");
+    static_assert(oIn % 16 == 0 && oBnd % 16 == 0 && oAnd % 16 == 0 && oCorr % 16 == 0 && oQ % 16 == 0 &&
+                      oND % 16 == 0 && oU % 16 == 0 && oPar % 16 == 0 && oDesc % 16 == 0 && oBar % 8 == 0,
+                  "alignment");
+    static_assert(kTmemND + C2 * kNDN <= kTmemCols, "tensor memory columns");
+};
 
 struct TcArgs {
     const uint4* wpack;   // packed operands (kPack bytes)
@@ -181,9 +199,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool STEP>
+template <bool STEP, int C2V, bool SPLIT>
 __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 {
+    using S = TcShape<C2V, SPLIT>;
+    constexpr int C2 = S::C2, R = S::R, N0 = S::N0, N2 = S::N2, N0BUF = S::N0BUF, kParts = S::kParts;
+    constexpr int UH = S::UH, NQ = S::NQ, kUFloats = S::kUFloats;
+    constexpr int oBc = S::oBc, oIn = S::oIn, oBnd = S::oBnd, oAnd = S::oAnd, oCorr = S::oCorr, oQ = S::oQ;
+    constexpr int oND = S::oND, oU = S::oU, oPar = S::oPar, oDesc = S::oDesc, oPin = S::oPin, oBar = S::oBar;
+    constexpr int oTmemSlot = S::oTmemSlot;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = tid < NWORK, issuer = tid == NWORK, helper = tid >= NWORK + 32;
@@ -202,25 +226,35 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     float* sBL = sPar;
     float* sOut = sBL + 3;
     float* sIns = sOut + 3;
+    float* sNDW = sPar + 16;   // SPLIT: WN [3][32], then WD [3][32]
+    float* sND = reinterpret_cast<float*>(sm + oND);   // SPLIT: N + D partial sums [channel group 4][3][C2 * 128]
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
     uint8_t* sPin = sm + oPin;
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
     auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
     auto bar_free = [&](int b) { return sbase + oBar + 8u * (uint32_t)(2 + b); };
     const uint32_t bar_nd = sbase + oBar + 8u * 4u, bar_drain = sbase + oBar + 8u * 5u;
-    auto sIn = [&](int buf) { return reinterpret_cast<uint4*>(sm + oIn) + buf * N0BUF; };
+    // input buffer of tile buffer `buf` (SPLIT: its high part; the low part follows at + N0BUF)
+    auto sIn = [&](int buf, int part = 0) { return reinterpret_cast<uint4*>(sm + oIn) + (buf * kParts + part) * N0BUF; };
 
     // ---- one-time set-up: operands, barriers, tensor memory
     for (int e = tid; e < kBc / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBc)[e] = A.wpack[e];
-    for (int e = tid; e < kBnd / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBnd)[e] = A.wpack[kOffBnd / 16 + e];
+    if constexpr (SPLIT) {
+        for (int e = tid; e < kBc / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBc + kBc)[e] = A.wpack[kOffBlo / 16 + e];
+        for (int e = tid; e < 6 * kC; e += NTH) sNDW[e] = A.w[(e < 3 * kC ? kOffWN : kOffWD) + e % (3 * kC)];
+    } else {
+        for (int e = tid; e < kBnd / 16; e += NTH) reinterpret_cast<uint4*>(sm + oBnd)[e] = A.wpack[kOffBnd / 16 + e];
+    }
     if (tid < 3) {
         sBL[tid] = A.w[kOffBL + tid];
         sOut[tid] = A.w[kOffOuts + tid];
     }
     if (tid < 6) sIns[tid] = A.w[kOffIns + tid];
     // input rows N0 .. N0BUF are read only by junk cell-region positions; keep them zero
-    for (int e = tid; e < 2 * (N0BUF - N0); e += NTH)
-        sIn(e / (N0BUF - N0))[N0 + e % (N0BUF - N0)] = make_uint4(0, 0, 0, 0);
+    for (int e = tid; e < 2 * kParts * (N0BUF - N0); e += NTH) {
+        const int bp = e / (N0BUF - N0);
+        sIn(bp / kParts, bp % kParts)[N0 + e % (N0BUF - N0)] = make_uint4(0, 0, 0, 0);
+    }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(bar(b), 1);
@@ -273,7 +307,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     };
     auto issue_chunk = [&](int c2, int ib) {   // chunk c2 of input buffer ib into accumulator c2 & 1
         const uint32_t d = tmem + (uint32_t)kNC * (uint32_t)(c2 & 1);
-        const uint32_t in = sbase + oIn + (uint32_t)(ib * N0BUF * 16);
+        const uint32_t in = sbase + oIn + (uint32_t)(ib * kParts * N0BUF * 16);
         const uint64_t dA = tc::sdesc(in, 16, 128), dAw = tc::sdesc(in, (PT - 4) * 16, 128);
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
@@ -281,6 +315,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             const bool wrap = p < kPairs - 1 && ta % 5 == 4;
             const uint64_t ad = (wrap ? dAw : dA) + (uint64_t)(c2 * 128 + ctap_off(ta));
             tc::mma_bf16(d, ad, dBc + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), p > 0);
+            if constexpr (SPLIT) {   // + A_hi B_lo + A_lo B_hi (the low parts sit kBc and N0BUF rows further)
+                tc::mma_bf16(d, ad, dBc + (uint64_t)(kBc >> 4) + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), true);
+                tc::mma_bf16(d, ad + (uint64_t)N0BUF, dBc + (uint64_t)(p * 2 * kNC), tc::idesc_bf16(128, kNC), true);
+            }
         }
         tc::mma_commit(bar(c2 & 1));
     };
@@ -352,7 +390,15 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
 #pragma unroll
         for (int c = 0; c < 6; ++c) v[c] = sIns[c] * rw.v[c];
         v[6] = v[7] = 0.f;
-        sIn(buf)[j0] = pack8(v);
+        if constexpr (SPLIT) {   // v = hi + lo, both BF16
+            float lo[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) lo[c] = v[c] - __bfloat162float(__float2bfloat16_rn(v[c]));
+            sIn(buf, 0)[j0] = pack8(v);
+            sIn(buf, 1)[j0] = pack8(lo);
+        } else {
+            sIn(buf)[j0] = pack8(v);
+        }
         const int uy = iy - 2, ux = ix - 2;
         if (uy >= 0 && uy < UH && ux >= 0 && ux < UW) {
             float* sUb = sU + buf * kUFloats;
@@ -393,8 +439,14 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             const uint4 r = in[row];
             if (n < 64) { z[0] = bf_lo(r.x); z[1] = bf_hi(r.x); z[2] = bf_lo(r.y); }
             else { z[0] = bf_hi(r.y); z[1] = bf_lo(r.z); z[2] = bf_hi(r.z); }
+            if constexpr (SPLIT) {   // + the low part: the FP32 value the MMAs see
+                const uint4 l = in[row + N0BUF];
+                if (n < 64) { z[0] += bf_lo(l.x); z[1] += bf_hi(l.x); z[2] += bf_lo(l.y); }
+                else { z[0] += bf_hi(l.y); z[1] += bf_lo(l.z); z[2] += bf_hi(l.z); }
+            }
         };
-        const float* gKD = reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc) + kKE + kKC;
+        const float* gKD = SPLIT ? reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kOffKD2)
+                                 : reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc) + kKE + kKC;
 #pragma unroll 1
         for (int ed = 0; ed < 4; ++ed) {
             if (!has[ed]) continue;
@@ -488,7 +540,20 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             for (int k = 0; k < 8; ++k)
                 if (k < 3 || cg < 3) qr[k * NQ] = valid ? q[k] : 0.f;
         }
-        {
+        if constexpr (SPLIT) {
+            // s = tanh(t) in FP32 (the 1e-4 tolerance rules out tanh.approx)
+            // and this channel group's share of N + D = WN s + WD (xi . s)
+            float nd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float sv = tanhf(t[c]), xs = xi[c] * sv;
+#pragma unroll
+                for (int co = 0; co < 3; ++co)
+                    nd[co] = fmaf(sNDW[3 * kC + co * kC + 8 * cg + c], xs, fmaf(sNDW[co * kC + 8 * cg + c], sv, nd[co]));
+            }
+#pragma unroll
+            for (int co = 0; co < 3; ++co) sND[(cg * 3 + co) * (C2 * 128) + j2] = nd[co];
+        } else {
             // every row of the operand is written (rows that are no output
             // node give N + D nobody reads; their inputs are finite)
             float sv[8], xs[8];
@@ -500,8 +565,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             uint4* a = reinterpret_cast<uint4*>(sm + oAnd + b * kAnd) + quarter * 32 + lane;
             a[cg * 128] = pack8(sv);
             a[(4 + cg) * 128] = pack8(xs);
+            tc::fence_async_smem();   // the operand, for the tensor cores
         }
-        tc::fence_async_smem();   // the operand, for the tensor cores
         tc::fence_before();
         (void)out_node;
     };
@@ -516,11 +581,19 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         const int cc = warp >> 2;
         const int j2 = cc * 128 + quarter * 32 + lane;   // ry2 = j2 / PT, rx2 = lane (PT = 32)
         const int oy = j2 / PT - 1, ox = j2 % PT - 1;
-        const bool ok = tc::mbar_wait(bar_nd, ph_nd, kWaitLimit);
-        ph_nd ^= 1u;
-        tc::fence_after();
-        float nd[4];
-        {
+        float nd[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (SPLIT) {   // the 4 channel groups' shares, in a fixed order
+            if (j2 < N2) {
+#pragma unroll
+                for (int co = 0; co < 3; ++co) {
+                    const float* p = sND + co * (C2 * 128) + j2;
+                    nd[co] = ((p[0] + p[3 * C2 * 128]) + p[6 * C2 * 128]) + p[9 * C2 * 128];
+                }
+            }
+        } else {
+            const bool ok = tc::mbar_wait(bar_nd, ph_nd, kWaitLimit);
+            ph_nd ^= 1u;
+            tc::fence_after();
             uint32_t r[4];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -529,9 +602,9 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             tc::tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 4; ++i) nd[i] = __uint_as_float(r[i]);
+            tc::fence_before();
+            if (!ok) return false;
         }
-        tc::fence_before();
-        if (!ok) return false;
         const int o = oy * WO + ox, y = g.y0 + oy, x = g.x0 + ox;
         if (oy >= 0 && oy < R && ox >= 0 && ox < WO && y < g.H && x < g.W) {
             float acc[3];
@@ -667,9 +740,9 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 if (issuer && ok) {
                     ok = wait_free(b);
                     if (ok) {
-                        issue_nd(c2);
+                        if constexpr (!SPLIT) issue_nd(c2);
                         if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
-                        if (c2 == C2 - 1) tc::mma_commit(bar_nd);
+                        if (!SPLIT && c2 == C2 - 1) tc::mma_commit(bar_nd);
                     }
                 }
             }
@@ -724,9 +797,34 @@ __device__ float composite_tap(const float* __restrict__ w, int n, int e, int cy
 __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict__ out)
 {
     constexpr int nB = kPairs * 2 * kNC * 8;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nB + kKE + kKC + kKD + kNDK * kNDN) return;
+    constexpr int nFirst = nB + kKE + kKC + kKD + kNDK * kNDN;   // up to the three-term split's tables
+    const int r0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r0 >= nFirst + nB + kKD) return;
     auto tap = [](int y, int x) { return 3 * y + x; };
+    if (r0 >= nFirst + nB) {   // KD2: the composite tap less Bhi + Blo, in KD's layout
+        const int q3 = r0 - nFirst - nB;
+        const int n = q3 % kNC, ch = (q3 / kNC) % 3, s5 = (q3 / (3 * kNC)) % 5, dir = q3 / (15 * kNC);
+        float d = 0.f;
+        if (n < 59 || n >= 64) {
+            const float v = composite_tap(w, n, n < 64 ? ch : 3 + ch, dir == 0 ? s5 : 2, dir == 0 ? 2 : s5);
+            const float hi = __bfloat162float(__float2bfloat16_rn(v));
+            d = v - (hi + __bfloat162float(__float2bfloat16_rn(v - hi)));
+        }
+        reinterpret_cast<float*>(out + kOffKD2)[q3] = d;
+        return;
+    }
+    if (r0 >= nFirst) {   // Blo: BF16(B - Bhi), in B's layout
+        const int r = r0 - nFirst;
+        const int e = r % 8, n = (r / 8) % kNC, kh = (r / (8 * kNC)) % 2, p = r / (16 * kNC);
+        const int c = 2 * p + kh, cy = c / 5, cx = c % 5;
+        float v = 0.f;
+        const bool u_col = n < 59 && e < 3, v_col = n >= 64 && e >= 3 && e < 6;
+        if (c < 25 && (u_col || v_col)) v = composite_tap(w, n, e, cy, cx);
+        const float hi = __bfloat162float(__float2bfloat16_rn(v));
+        reinterpret_cast<__nv_bfloat16*>(out + kOffBlo)[r] = __float2bfloat16_rn(v - hi);
+        return;
+    }
+    const int r = r0;
     if (r >= nB + kKE + kKC + kKD) {   // B of N + D: [k / 8][n][k % 8]
         const int e2 = r - (nB + kKE + kKC + kKD);
         const int e = e2 % 8, n = (e2 / 8) % kNDN, k = (e2 / (8 * kNDN)) * 8 + e;
@@ -794,26 +892,50 @@ __global__ void pack_tc_kernel(const float* __restrict__ w, uint8_t* __restrict_
 
 int net_tc_pack_bytes() { return kPack; }
 int net_tc_edge_offset() { return kBc; }
-int net_tc_tile_rows() { return R; }
 int net_tc_tile_cols() { return WO; }
+// BF16 tile shapes v = 0, 1, 2: 4, 3 or 2 chunks (14, 10 or 6 output rows);
+// the FP32 three-term shapes k = 0, 1: 3 or 2 chunks (10 or 6 rows; 4 chunks
+// of the split operands do not fit in shared memory)
+int net_tc_variants() { return 3; }
+int net_tc_variant_rows(int v) { return 4 * (4 - v) - 2; }
+int net_tc_split_variants() { return 2; }
+int net_tc_split_rows(int k) { return 4 * (3 - k) - 2; }
+
+namespace {
+template <bool STEP, int C2, bool SPLIT>
+cudaError_t set_smem()
+{
+    return cudaFuncSetAttribute(net_tc_kernel<STEP, C2, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TcShape<C2, SPLIT>::kSmem);
+}
+template <int C2, bool SPLIT>
+void launch_step(const TcArgs& a, int grid, cudaStream_t s)
+{
+    net_tc_kernel<true, C2, SPLIT><<<grid, NTH, TcShape<C2, SPLIT>::kSmem, s>>>(a);
+}
+}  // namespace
 
 cudaError_t net_tc_init()
 {
-    cudaError_t e = cudaFuncSetAttribute(net_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(net_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = set_smem<true, 4, false>();
+    if (e == cudaSuccess) e = set_smem<true, 3, false>();
+    if (e == cudaSuccess) e = set_smem<true, 2, false>();
+    if (e == cudaSuccess) e = set_smem<true, 3, true>();
+    if (e == cudaSuccess) e = set_smem<true, 2, true>();
+    if (e == cudaSuccess) e = set_smem<false, 4, false>();
     return e;
 }
 
 cudaError_t launch_pack_bf16(const float* w, void* wpack, cudaStream_t s)
 {
-    constexpr int n = kPairs * 2 * kNC * 8 + kKE + kKC + kKD + kNDK * kNDN;
+    constexpr int n = 2 * kPairs * 2 * kNC * 8 + kKE + kKC + 2 * kKD + kNDK * kNDN;
     pack_tc_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, static_cast<uint8_t*>(wpack));
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDesc* desc, const int4* tiles, int n_tiles,
-                               const float* src, float* dst, const uint32_t* pinmask, int32_t* status, int grid,
-                               cudaStream_t s, const int32_t* mode)
+cudaError_t launch_net_tc_step(int variant, bool split, const void* wpack, const float* w, const ClothDesc* desc,
+                               const int4* tiles, int n_tiles, const float* src, float* dst, const uint32_t* pinmask,
+                               int32_t* status, int grid, cudaStream_t s, const int32_t* mode)
 {
     TcArgs a{};
     a.wpack = static_cast<const uint4*>(wpack);
@@ -826,13 +948,19 @@ cudaError_t launch_net_tc_step(const void* wpack, const float* w, const ClothDes
     a.dst = dst;
     a.pinmask = pinmask;
     a.mode = mode;
-    net_tc_kernel<true><<<grid, NTH, kSmem, s>>>(a);
+    if (split) {
+        if (variant == 1) launch_step<2, true>(a, grid, s);
+        else launch_step<3, true>(a, grid, s);
+    } else if (variant == 1) launch_step<3, false>(a, grid, s);
+    else if (variant == 2) launch_step<2, false>(a, grid, s);
+    else launch_step<4, false>(a, grid, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float* z, float* out, int N, int H, int W,
                                   int32_t* status, int grid, cudaStream_t s)
 {
+    using S = TcShape<4, false>;
     TcArgs a{};
     a.wpack = static_cast<const uint4*>(wpack);
     a.w = w;
@@ -840,10 +968,10 @@ cudaError_t launch_net_tc_forward(const void* wpack, const float* w, const float
     a.z = z;
     a.a = out;
     a.N = N; a.H = H; a.W = W;
-    a.tiles_y = (H + R - 1) / R;
+    a.tiles_y = (H + S::R - 1) / S::R;
     a.tiles_x = (W + WO - 1) / WO;
     const int n_tiles = N * a.tiles_y * a.tiles_x;
-    net_tc_kernel<false><<<grid < n_tiles ? grid : n_tiles, NTH, kSmem, s>>>(a);
+    net_tc_kernel<false, 4, false><<<grid < n_tiles ? grid : n_tiles, NTH, S::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

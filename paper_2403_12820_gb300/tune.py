@@ -128,43 +128,47 @@ def autotune(cb, cache_path: str | None = None, candidates=DEFAULT_CANDIDATES, w
     return dict(rec, key=key, cached=False)
 
 
-def net_tile_choices() -> list[int]:
-    """Tile widths of the FP32 network step (cloth_net_tile_choices; the first
-    is the default)."""
+def net_tile_choices(precision: int) -> list[dict]:
+    """Tile shapes of the network step for networks of `precision`
+    (cloth_net_tile_choices): per choice its output rows, columns and kind
+    ("cuda" cores or "tensor" cores); the first is the default."""
     import ctypes
 
     from . import _lib
-    cols = (ctypes.c_int32 * 16)()
+    rows, cols, kinds = (ctypes.c_int32 * 16)(), (ctypes.c_int32 * 16)(), (ctypes.c_int32 * 16)()
     n = ctypes.c_int32()
-    _lib.call("cloth_net_tile_choices", cols, 16, ctypes.byref(n))
-    return [int(cols[i]) for i in range(min(16, n.value))]
+    _lib.call("cloth_net_tile_choices", int(precision), rows, cols, kinds, 16, ctypes.byref(n))
+    return [{"rows": int(rows[i]), "cols": int(cols[i]), "kind": "tensor" if kinds[i] else "cuda"}
+            for i in range(min(16, n.value))]
 
 
 def autotune_net(cb, net, cache_path: str | None = None, warmup: int = 3, steps: int = 10,
                  retune: bool = False) -> dict:
-    """Pick the FP32 network step's tile shape for the ClothBatch `cb` and the
-    FP32 Net `net` and apply it, as autotune does for the plain step: from
-    the cache when it holds this batch's key, else timed by libcloth
-    (cloth_tune_net).  Returns the record: tile_cols, us_per_step, the timed
-    choices, and whether it came from the cache."""
+    """Pick the network step's tile shape for the ClothBatch `cb` and the Net
+    `net` (in its precision) and apply it, as autotune does for the plain
+    step: from the cache when it holds this batch's key, else timed by
+    libcloth (cloth_tune_net).  Returns the record: the choice index, its
+    shape, us_per_step, the timed choices, and whether it came from the
+    cache."""
     import torch
 
     props = torch.cuda.get_device_properties(cb.device)
-    key = batch_key("net_comp", props.name, props.multi_processor_count, [(s["rows"], s["cols"]) for s in cb.specs])
+    key = batch_key(f"net_step_p{int(net.precision)}", props.name, props.multi_processor_count,
+                    [(s["rows"], s["cols"]) for s in cb.specs])
     cache = LaunchCache(cache_path) if cache_path else None
-    choices = net_tile_choices()
+    choices = net_tile_choices(net.precision)
     if cache is not None and not retune:
         rec = cache.data.get(key)
         if rec is not None:
-            if int(rec["tile_cols"]) not in choices:
-                raise ValueError(f"cached tile width {rec['tile_cols']} is not a choice")
-            cb.set_net_tile(int(rec["tile_cols"]))
+            if not 0 <= int(rec["choice"]) < len(choices) or choices[int(rec["choice"])] != rec["shape"]:
+                raise ValueError(f"cached tile shape {rec['shape']} is not a choice")
+            cb.set_net_tile(net.precision, int(rec["choice"]))
             return dict(rec, key=key, cached=True)
     best, us = cb.tune_net(net, warmup=warmup, steps=steps)
-    if best != choices[pick(choices, us)]:
+    if best != pick(list(range(len(choices))), us):
         raise RuntimeError("libcloth applied a different tile shape than the fastest timed")
-    rec = {"tile_cols": best, "us_per_step": us[choices.index(best)],
-           "candidates": [[c, t] for c, t in zip(choices, us)], "warmup": int(warmup), "steps": int(steps)}
+    rec = {"choice": best, "shape": choices[best], "us_per_step": us[best],
+           "candidates": [[ch, t] for ch, t in zip(choices, us)], "warmup": int(warmup), "steps": int(steps)}
     if cache is not None:
         cache.put(key, rec)
     return dict(rec, key=key, cached=False)

@@ -11,10 +11,12 @@ relative, far below the tolerance even where a is small (the derivative
 branch alone on a 1 x 1 cloth gives |a| near 1e-3 m/s^2 beside |v| near
 0.03 m/s).  Only v' is read, so the large step changes nothing else.
 
-Kernels: the tensor-core step (BF16 operands, FP32 accumulation), the FP32
-CUDA-core step, and the literal-cell step.  Tolerances, normwise per cloth
-(max |a_gpu - a_ref| / max |a_ref|): 2e-2 for BF16, 1e-4 for FP32 and the
-literal cell.  Besides the whole cell, weight blobs with the linear branch
+Kernels: the tensor-core step (BF16 operands, FP32 accumulation) in its
+three tile shapes (14, 10 and 6 output rows), the FP32 CUDA-core step, the
+FP32 tensor-core step in its two shapes (10 and 6 rows; each product as three
+BF16 products of high and low parts), and the literal-cell step.  Tolerances, normwise per cloth (max
+|a_gpu - a_ref| / max |a_ref|): 2e-2 for BF16, 1e-4 for FP32 and the literal
+cell.  Besides the whole cell, weight blobs with the linear branch
 zeroed (a = N + D) and with only the derivative branch (a = D) keep the
 smaller branches from hiding behind the linear one.  Shapes: single nodes,
 single rows and columns, exact and ragged tiles of both step kernels, and a
@@ -33,7 +35,10 @@ from paper_2403_12820_gb300.net import BF16, FP32, Net
 pytestmark = pytest.mark.gpu
 
 DT = 1.0
-TOL = {"bf16": 2e-2, "fp32": 1e-4, "pcell": 1e-4}
+# kind -> (precision, tile choice of tune.net_tile_choices(precision))
+NET_KINDS = {"bf16": (BF16, 0), "bf16_r10": (BF16, 1), "bf16_r6": (BF16, 2), "fp32": (FP32, 2), "fp32tc": (FP32, 0),
+             "fp32tc_r6": (FP32, 1)}
+TOL = {"bf16": 2e-2, "bf16_r10": 2e-2, "bf16_r6": 2e-2, "fp32": 1e-4, "fp32tc": 1e-4, "fp32tc_r6": 1e-4, "pcell": 1e-4}
 
 # blob offsets: W1, W2, WL, bL, P, WN, WD, in_scale, out_scale
 O_WL, O_BL, O_P, O_WN, O_WD = 10944, 11808, 11811, 12835, 12931
@@ -72,7 +77,9 @@ def one_step(kind, w, specs, xs, vs):
     if kind == "pcell":
         cb.step_pcell(w, 1)
     else:
-        net = Net(w, BF16 if kind == "bf16" else FP32)
+        prec, choice = NET_KINDS[kind]
+        net = Net(w, prec)
+        cb.set_net_tile(prec, choice)
         cb.step_net(net, 1)
     _, v1 = cb.get_state()
     got = [t.cpu().numpy().astype(np.float64) for t in cb.split(v1)]
@@ -88,17 +95,24 @@ def gpu_accel(spec, x, v, v1):
 
 
 SHAPES = {
-    # the step kernels' tiles: 14 x 26 (tensor cores), 14 x 14 (FP32), 32 x 16 (literal cell)
+    # the step kernels' tiles: R x 26 (tensor cores, R = 14, 10, 6), 14 x 14 (FP32 CUDA cores),
+    # 32 x 16 (literal cell)
     "bf16": [(1, 1), (1, 2), (3, 1), (2, 3), (14, 26), (15, 27), (28, 52), (5, 5), (30, 61), (13, 40)],
+    "bf16_r10": [(1, 1), (1, 3), (4, 1), (10, 26), (11, 27), (20, 52), (9, 25), (31, 40)],
+    "bf16_r6": [(1, 1), (2, 1), (1, 5), (6, 26), (7, 27), (12, 52), (5, 25), (19, 33)],
     "fp32": [(1, 1), (1, 2), (3, 1), (2, 3), (14, 14), (15, 29), (30, 16), (5, 5), (28, 28), (17, 43)],
+    "fp32tc": [(1, 1), (1, 2), (3, 1), (2, 3), (10, 26), (11, 27), (20, 52), (5, 5), (31, 61), (13, 40)],
+    "fp32tc_r6": [(1, 1), (1, 2), (3, 1), (2, 3), (6, 26), (7, 27), (12, 52), (5, 5), (19, 61), (13, 40)],
     "pcell": [(1, 1), (1, 2), (3, 1), (2, 3), (32, 16), (33, 17), (8, 32), (5, 5), (64, 48), (37, 21)],
 }
-BRANCHES = {"bf16": ["all", "ND", "D"], "fp32": ["all", "ND", "D"], "pcell": ["all", "mixed"]}
+BRANCHES = {"bf16": ["all", "ND", "D"], "bf16_r10": ["all"], "bf16_r6": ["all"], "fp32": ["all", "ND", "D"],
+            "fp32tc": ["all", "ND", "D"], "fp32tc_r6": ["all", "ND", "D"], "pcell": ["all", "mixed"]}
+SEED = {"bf16": 301, "bf16_r10": 306, "bf16_r6": 307, "fp32": 302, "fp32tc": 308, "fp32tc_r6": 309, "pcell": 303}
 
 
-@pytest.mark.parametrize("kind,branches", [(k, b) for k in ("bf16", "fp32", "pcell") for b in BRANCHES[k]])
+@pytest.mark.parametrize("kind,branches", [(k, b) for k in SHAPES for b in BRANCHES[k]])
 def test_step_acceleration_matches_oracle_on_ragged_shapes(kind, branches):
-    rng = np.random.default_rng({"bf16": 301, "fp32": 302, "pcell": 303}[kind] + 7 * len(branches))
+    rng = np.random.default_rng(SEED[kind] + 7 * len(branches))
     specs, xs, vs = [], [], []
     for (r, c) in SHAPES[kind]:
         sp = wl.cloth_spec(r, c, p=rng.normal(0, 0.5), dt=DT)
@@ -114,7 +128,7 @@ def test_step_acceleration_matches_oracle_on_ragged_shapes(kind, branches):
         assert err <= TOL[kind], (kind, branches, SHAPES[kind][b], err)
 
 
-@pytest.mark.parametrize("kind", ["bf16", "fp32", "pcell"])
+@pytest.mark.parametrize("kind", ["bf16", "fp32", "fp32tc", "pcell"])
 def test_step_acceleration_maximum_size_cloth_sampled(kind):
     """One 2048 x 2048 cloth, one step: at sampled nodes (corners, edges,
     random) the kernel's a equals the oracle's cell on the window of the
@@ -123,7 +137,7 @@ def test_step_acceleration_maximum_size_cloth_sampled(kind):
     stencil; pressure needs 1)."""
     n = 2048
     rad = 2 if kind == "pcell" else 3
-    rng = np.random.default_rng({"bf16": 311, "fp32": 312, "pcell": 313}[kind])
+    rng = np.random.default_rng({"bf16": 311, "fp32": 312, "fp32tc": 316, "pcell": 313}[kind])
     sp = wl.cloth_spec(n, n, p=0.3, dt=DT)
     x, v = wl.noisy_flat_state(sp, 1e-3, rng)
     v = (v + rng.normal(0, 0.05, v.shape)).astype(np.float32)

@@ -136,60 +136,85 @@ def test_tune_rejects_bad_candidates_before_running():
 
 
 def test_net_tile_choices_are_the_library_shapes():
-    """The FP32 network step's tile widths (host query, no GPU): the default
-    first, each distinct."""
-    ch = tune.net_tile_choices()
-    assert ch[0] == 14 and len(set(ch)) == len(ch) >= 2
+    """The network step's tile shapes per precision (host query, no GPU):
+    FP32 has the tensor-core three-term shapes of 10 and 6 rows (the default
+    first) and then the CUDA-core shapes of 14 rows; BF16 has tensor-core
+    shapes of 14, 10 and 6 rows; every shape distinct."""
+    from paper_2403_12820_gb300.net import BF16, FP32
+    f = tune.net_tile_choices(FP32)
+    assert f[:2] == [{"rows": r, "cols": 26, "kind": "tensor"} for r in (10, 6)]
+    assert f[2] == {"rows": 14, "cols": 14, "kind": "cuda"}
+    assert [c["kind"] for c in f[2:]] == ["cuda"] * (len(f) - 2) and len(f) >= 4
+    b = tune.net_tile_choices(BF16)
+    assert b == [{"rows": r, "cols": 26, "kind": "tensor"} for r in (14, 10, 6)]
+    for ch in (f, b):
+        assert len({(c["rows"], c["cols"], c["kind"]) for c in ch}) == len(ch)
+    with pytest.raises(Exception):
+        tune.net_tile_choices(7)
 
 
-@pytest.mark.gpu
-def test_fp32_step_is_bitwise_the_same_in_every_tile_shape_and_the_tuner_picks_the_fastest(tmp_path):
-    """Each node's arithmetic in the FP32 network step does not depend on the
-    tiling, so every tile shape gives the same state bit for bit (an uneven
-    batch: single nodes, thin strips, sizes off every tile width, pins,
-    pressure, a sphere); cloth_tune_net leaves the state, applies the
-    fastest shape, and the cache brings it back without timing."""
-    import torch
-
+def _uneven_batch(seed):
+    """An uneven batch: single nodes, thin strips, sizes off every tile
+    shape, pins, pressure, a sphere."""
     from paper_2403_12820_gb300 import workloads as wl
-    from paper_2403_12820_gb300.cloth import ClothBatch, pack
-    from paper_2403_12820_gb300.net import BF16, FP32, Net
-    rng = np.random.default_rng(401)
+    rng = np.random.default_rng(seed)
     specs, pins, xs, vs = [], [], [], []
     for (r, c) in [(1, 1), (1, 7), (5, 3), (14, 14), (15, 31), (29, 61), (40, 13), (70, 33)]:
         sph = {"center": (0.1, 0.1, -0.05), "radius": 0.06} if r == 29 else None
         sp = wl.cloth_spec(r, c, p=rng.normal(0, 0.5), sphere=sph)
         x, v = wl.sag_state(sp, rng, amp=0.02, vamp=0.1)
         specs.append(sp); xs.append(x); vs.append(v); pins.append([0] if r * c > 1 else [])
+    return specs, pins, xs, vs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec_name", ["fp32", "bf16"])
+def test_network_step_per_tile_shape_and_the_tuner_picks_the_fastest(tmp_path, prec_name):
+    """Each node's arithmetic does not depend on the tiling, so the shapes of
+    one kind give the same state bit for bit; the FP32 tensor-core shape
+    (three BF16 products per term) agrees with the CUDA-core ones within the
+    FP32 tolerance on the velocity change; cloth_tune_net leaves the state,
+    applies the fastest shape, and the cache brings it back without timing."""
+    import torch
+
+    from paper_2403_12820_gb300 import workloads as wl
+    from paper_2403_12820_gb300.cloth import ClothBatch, pack
+    from paper_2403_12820_gb300.net import BF16, FP32, Net
+    prec = FP32 if prec_name == "fp32" else BF16
+    specs, pins, xs, vs = _uneven_batch(401)
     w = wl.kaiming_blob(402, in_scale=(50.0,) * 3 + (1.0,) * 3, out_scale=(9.81,) * 3, bias_sigma=0.1)
-    net = Net(w, FP32)
+    net = Net(w, prec)
     x0, v0 = pack(xs).cuda(), pack(vs).cuda()
+    choices = tune.net_tile_choices(prec)
     outs = []
-    for cols in tune.net_tile_choices():
+    for i, ch in enumerate(choices):
         cb = ClothBatch(specs, pins)
-        cb.set_net_tile(cols)
-        assert cb.get_net_tile() == cols
+        cb.set_net_tile(prec, i)
+        assert cb.get_net_tile(prec) == i
         cb.set_state(x0, v0)
-        cb.step_net(net, 7)
-        outs.append(cb.get_state())
+        cb.step_net(net, 1)
+        outs.append((ch["kind"], cb.get_state()))
         assert cb.status() == 0
         cb.close()
-    for x, v in outs[1:]:
-        assert torch.equal(x, outs[0][0]) and torch.equal(v, outs[0][1])
+    ref = [o for k, o in outs if k == outs[0][0]]
+    for x, v in ref[1:]:
+        assert torch.equal(x, ref[0][0]) and torch.equal(v, ref[0][1])
+    for k, (x, v) in outs:
+        if k != outs[0][0]:   # the other kind: the velocity change dt * a within the FP32 tolerance
+            dv0, dv = (ref[0][1] - v0).double(), (v - v0).double()
+            assert float(torch.linalg.norm(dv - dv0) / torch.linalg.norm(dv0)) <= 1e-4
     cb = ClothBatch(specs, pins)
     cb.set_state(x0, v0)
     with pytest.raises(Exception):
-        cb.set_net_tile(13)
+        cb.set_net_tile(prec, len(choices))
     path = str(tmp_path / "net_tiles.json")
     rec = tune.autotune_net(cb, net, cache_path=path, warmup=1, steps=3)
-    assert not rec["cached"] and rec["tile_cols"] in tune.net_tile_choices()
-    assert rec["tile_cols"] == min(rec["candidates"], key=lambda ct: ct[1])[0]
-    assert cb.get_net_tile() == rec["tile_cols"]
+    assert not rec["cached"] and rec["shape"] == choices[rec["choice"]]
+    assert rec["choice"] == min(range(len(choices)), key=lambda i: rec["candidates"][i][1])
+    assert cb.get_net_tile(prec) == rec["choice"]
     x, v = cb.get_state()
     assert torch.equal(x, x0) and torch.equal(v, v0)          # tuning does not move the state
-    cb.set_net_tile(tune.net_tile_choices()[0])
+    cb.set_net_tile(prec, 0 if rec["choice"] else 1)
     again = tune.autotune_net(cb, net, cache_path=path)
-    assert again["cached"] and cb.get_net_tile() == rec["tile_cols"]
-    with pytest.raises(Exception):
-        cb.tune_net(Net(w, BF16))                               # one shape on the tensor cores
+    assert again["cached"] and cb.get_net_tile(prec) == rec["choice"]
     cb.close()
