@@ -57,6 +57,10 @@ def parse_args(argv=None):
     p.add_argument("--no-larger-step", action="store_true")
     p.add_argument("--train-iters", type=int, default=20)
     p.add_argument("--de-generations", type=int, default=6)
+    p.add_argument("--bf16-tile", type=int, default=0,
+                   help="cnn_step section: tile choice of the BF16 network step (tune.net_tile_choices)")
+    p.add_argument("--fp32-tile", type=int, default=0,
+                   help="cnn_step section: tile choice of the FP32 network step (tune.net_tile_choices)")
     p.add_argument("--only", choices=["cnn", "cnn_step", "mixed", "pcell", "larger_step", "train", "single_cloth"],
                    default=None,
                    help="run one section alone and print its JSON (for profiling; not a bench line)")
@@ -581,8 +585,9 @@ def run_cnn_step(args, dev):
     cb.rollout(100, graph_chunk=100)
     x0, v0 = cb.get_state()
     out = {"trained": trained}
-    for name, prec in (("bf16", BF16), ("f32", FP32)):
+    for name, prec, tile in (("bf16", BF16, args.bf16_tile), ("f32", FP32, args.fp32_tile)):
         net = Net(blob, prec, device=dev)
+        cb.set_net_tile(prec, tile)
         cb.set_state(x0, v0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -591,7 +596,7 @@ def run_cnn_step(args, dev):
         e1.record()
         torch.cuda.synchronize()
         out[name] = {"ms_per_step": e0.elapsed_time(e1) / max(1, args.cnn_steps), "steps": args.cnn_steps,
-                     "status_word": cb.status()}
+                     "tile_choice": tile, "status_word": cb.status()}
         net.close()
     cb.close()
     return out

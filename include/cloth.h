@@ -234,9 +234,10 @@ int cloth_set_launch(cloth_ctx* ctx, int32_t seg_rows, int32_t warps_per_sm, voi
 /* Launch-shape autotuner of the plain step.  For each of the n candidates
  * (seg_rows[i], warps_per_sm[i]), in cloth_set_launch's ranges (seg_rows
  * >= 4 or -1 for balanced ranges; warps_per_sm 1..64 or -1 for the
- * default), runs `warmup` untimed and then `steps` timed plain steps on
- * `stream`, timed with CUDA events, and writes the mean microseconds per
- * step to us_out[i] (host array of n).  The steps read the current state
+ * default), captures `steps` plain steps as one CUDA graph (as rollouts
+ * replay them), replays it warmup + 1 times untimed and twice timed with
+ * CUDA events on `stream`, and writes the mean microseconds per step to
+ * us_out[i] (host array of n).  The steps read the current state
  * and write only the other state buffer: the state is unchanged.  The
  * fastest candidate is then applied as by cloth_set_launch and its index
  * written to *best (host).  CLOTH_EINVAL, before anything runs, for n < 1,

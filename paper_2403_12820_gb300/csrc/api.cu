@@ -1042,18 +1042,30 @@ int cloth_tune_launch(cloth_ctx* c, int32_t n, const int32_t* seg_rows, const in
     // so the state the caller sees does not move
     const float* src = c->d_state(c->cur);
     float* dst = c->d_state(c->cur ^ 1);
+    // each candidate's `steps` steps are timed as one CUDA graph, as rollouts
+    // replay them (eager launches rank the shapes differently)
     for (int i = 0; i < n && rc == CLOTH_OK && ce == cudaSuccess; ++i) {
         rc = apply(i);
-        for (int k = 0; k < warmup && rc == CLOTH_OK; ++k) rc = launch_plain(c, src, dst, nullptr, s);
         if (rc) break;
-        if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) break;
-        for (int k = 0; k < steps && rc == CLOTH_OK; ++k) rc = launch_plain(c, src, dst, nullptr, s);
-        if (rc) break;
-        if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) break;
-        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        if ((ce = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        for (int k = 0; k < steps && rc == CLOTH_OK; ++k) rc = launch_plain(c, src, dst, nullptr, c->cap);
+        const cudaError_t ec = cudaStreamEndCapture(c->cap, &g);
+        if (rc == CLOTH_OK && (ce = ec) == cudaSuccess) ce = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        for (int k = 0; k <= warmup && rc == CLOTH_OK && ce == cudaSuccess; ++k)   // at least one untimed replay
+            ce = cudaGraphLaunch(ge, s);
+        constexpr int kReplays = 2;   // timed
+        if (rc == CLOTH_OK && ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+        for (int k = 0; k < kReplays && rc == CLOTH_OK && ce == cudaSuccess; ++k) ce = cudaGraphLaunch(ge, s);
+        if (rc == CLOTH_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (rc == CLOTH_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
         float ms = 0.f;
-        if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
-        us_out[i] = ms * 1000.f / (float)steps;
+        if (rc == CLOTH_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (rc || ce != cudaSuccess) break;
+        us_out[i] = ms * 1000.f / (float)(kReplays * steps);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
