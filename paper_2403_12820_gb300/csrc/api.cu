@@ -542,12 +542,14 @@ int cloth_train_loss(cloth_ctx* c, cloth_net* net, int32_t S, const float* d_tar
         f.s = SAVED + kSavS * NHW;
         f.a = a;
         f.N = B; f.H = H; f.W = W;
+        f.status = c->d_status();
         return launch_net_forward_simt(f, s);
     };
     auto backward = [&](const float* z, const float* ga, float* gz) {
         cudaError_t e = forward(z, static_cast<float*>(d_work) + L.a);   // recompute the step's activations
         if (e != cudaSuccess) return e;
-        return launch_net_backward_simt(net->d_w(), z, SAVED, ga, gz, net->d_part(), d_grad_w, B, H, W, s);
+        return launch_net_backward_simt(net->d_w(), z, SAVED, ga, gz, net->d_part(), d_grad_w, B, H, W, c->d_status(),
+                                        s);
     };
     return train_loss_impl(c, S, d_targets, alpha, g_norm, d_loss, d_work, bytes, s, forward, backward,
                            d_grad_w != nullptr);

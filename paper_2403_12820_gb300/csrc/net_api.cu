@@ -141,6 +141,7 @@ int net_forward(cloth_net* n, const float* d_z, float* d_a, int32_t N, int32_t H
     f.s = d_saved + kSavS * NHW;
     f.a = d_a;
     f.N = N; f.H = H; f.W = W;
+    f.status = n->d_status();
     NCK(launch_net_forward_simt(f, s));
     return CLOTH_OK;
 }
@@ -151,7 +152,7 @@ int net_backward(cloth_net* n, const float* d_z, float* d_saved, const float* d_
     if (!n || !d_z || !d_saved || !d_grad_a || !d_grad_w || !dims_ok(N, H, W)) return CLOTH_EINVAL;
     if (n->precision != CLOTH_NET_FP32) return CLOTH_EUNSUPPORTED;
     NCK(launch_net_backward_simt(n->d_w(), d_z, d_saved, d_grad_a, d_grad_z, n->d_part(), d_grad_w, N, H, W,
-                                 static_cast<cudaStream_t>(stream)));
+                                 n->d_status(), static_cast<cudaStream_t>(stream)));
     return CLOTH_OK;
 }
 

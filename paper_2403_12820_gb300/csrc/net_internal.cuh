@@ -49,11 +49,18 @@ struct NetFwdArgs {
     float* s;           // [N][32][H][W] or nullptr
     float* a;           // [N][3][H][W]
     int N, H, W;
+    int32_t* status;    // status word for a timed-out tensor-core wait; null: the second
+                        // convolution runs on the CUDA cores
 };
 
 cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s);
 cudaError_t launch_net_backward_simt(const float* w, const float* z, float* saved, const float* ga, float* gz,
-                                     float* partials, float* gw, int N, int H, int W, cudaStream_t s);
+                                     float* partials, float* gw, int N, int H, int W, int32_t* status, cudaStream_t s);
+// The 32 -> 32 3x3 convolution W2 (*) (or its adjoint, `transposed`) on the
+// tensor cores at FP32 precision (conv_tc.cu): NCHW images of 32 channels.
+cudaError_t conv32_tc_init();
+cudaError_t launch_conv32_tc(const float* in, float* out, const float* w, bool transposed, int images, int H, int W,
+                             int32_t* status, cudaStream_t s);
 cudaError_t net_simt_init();
 int net_last_cuda_error();
 // Record a CUDA failure of a network entry point for cloth_last_cuda_error.

@@ -446,7 +446,7 @@ cudaError_t net_simt_init()
     SET_SMEM((wgrad_kernel<kC, kC, 9, 4, View, View>), ((kC * TH * TW + kC * ((TH + 2) * (TW + 2) + 1)) * 4));
     SET_SMEM((wgrad_kernel<kC, kC, 1, 4, View, View>), ((kC * TH * TW + kC * (TH * TW + 1)) * 4));
 #undef SET_SMEM
-    return cudaSuccess;
+    return conv32_tc_init();
 }
 
 cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s)
@@ -457,8 +457,12 @@ cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s)
     // Eq. 6: phi1 = W1 (*) [zu; 0], xi1 = W1 (*) [0; zv] (images 2n + field)
     e = conv3x3<3, kC>(InZ{f.src, f.w, H, W}, WtW1{f.w}, OutView{f.t1, kC * HW, HW, W}, H, W, 2 * N, s);
     if (e != cudaSuccess) return e;
-    // phi = W2 (*) phi1, xi = W2 (*) xi1
-    e = conv3x3<kC, kC>(View{f.t1, kC * HW, HW, W, 1, 0}, WtW2{f.w}, OutView{f.t2, kC * HW, HW, W}, H, W, 2 * N, s);
+    // phi = W2 (*) phi1, xi = W2 (*) xi1: on the tensor cores where a status
+    // word can report a timed-out wait
+    if (f.status)
+        e = launch_conv32_tc(f.t1, f.t2, f.w, false, 2 * N, H, W, f.status, s);
+    else
+        e = conv3x3<kC, kC>(View{f.t1, kC * HW, HW, W, 1, 0}, WtW2{f.w}, OutView{f.t2, kC * HW, HW, W}, H, W, 2 * N, s);
     if (e != cudaSuccess) return e;
     // Eq. 7
     dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH, N);
@@ -467,7 +471,7 @@ cudaError_t launch_net_forward_simt(const NetFwdArgs& f, cudaStream_t s)
 }
 
 cudaError_t launch_net_backward_simt(const float* w, const float* z, float* saved, const float* ga, float* gz,
-                                     float* part, float* gw, int N, int H, int W, cudaStream_t s)
+                                     float* part, float* gw, int N, int H, int W, int32_t* status, cudaStream_t s)
 {
     const int64_t HW = (int64_t)H * W, NHW = (int64_t)N * HW;
     float* T1 = saved + kSavT1 * NHW;
@@ -496,9 +500,9 @@ cudaError_t launch_net_backward_simt(const float* w, const float* z, float* save
     if ((e = wgrad<kC, kC, 9, 4>(View{G2, kC * HW, HW, W, 1, 0}, View{T1, kC * HW, HW, W, 1, 0}, part, kOffW2, kC, H, W,
                                  2 * N, s)) != cudaSuccess)
         return e;
-    if ((e = conv3x3<kC, kC>(View{G2, kC * HW, HW, W, 1, 0}, WtW2T{w}, OutView{G1, kC * HW, HW, W}, H, W, 2 * N, s)) !=
-        cudaSuccess)
-        return e;
+    e = status ? launch_conv32_tc(G2, G1, w, true, 2 * N, H, W, status, s)
+               : conv3x3<kC, kC>(View{G2, kC * HW, HW, W, 1, 0}, WtW2T{w}, OutView{G1, kC * HW, HW, W}, H, W, 2 * N, s);
+    if (e != cudaSuccess) return e;
     // W1: per field, d W1[:, 3f:3f+3] from d phi1 / d xi1 and the scaled input
     for (int f = 0; f < 2; ++f) {
         if ((e = wgrad<kC, 3, 9, 4>(View{G1, kC * HW, HW, W, 2, f}, ZView{z, w, HW, W, f}, part, kOffW1 + 27 * f, 6, H, W,
