@@ -20,7 +20,8 @@ import tempfile
 # >= 4 cuts the strips into segments of that many rows (one warp per segment
 # by default), -1 gives balanced row shares; warps_per_sm -1 is the default.
 DEFAULT_CANDIDATES: tuple[tuple[int, int], ...] = (
-    (8, -1), (12, -1), (16, -1), (20, -1), (24, -1), (28, -1), (32, -1), (36, -1), (40, -1), (48, -1), (64, -1),
+    (8, -1), (12, -1), (16, -1), (20, -1), (24, -1), (28, -1), (30, -1), (32, -1), (34, -1), (36, -1), (40, -1),
+    (48, -1), (64, -1),
     (-1, -1), (-1, 8), (-1, 16),
 )
 MIN_SEG_ROWS = 4
