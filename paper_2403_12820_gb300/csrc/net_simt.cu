@@ -351,17 +351,33 @@ __global__ void __launch_bounds__(NT) branch_bwd_kernel(const float* __restrict_
 // Partial weight gradients: for the tiles t = blockIdx.x, + gridDim.x, ...
 // (tile = 32 x 8 nodes of image i), out[(a * BSTRIDE + b) * TAPS + tap] +=
 // sum_pixels A(i, a, y, x) B(i, b, y + dy, x + dx) with B zero outside the
-// image.  Thread (ab, b) owns a in [ab*ABLK, ab*ABLK+ABLK) and one b.
+// image.  Thread (pg, ab, b) owns a in [ab*ABLK, ab*ABLK+ABLK), one b, and the
+// tile rows pg, pg + PG, ...: shapes with few (a, b) pairs take several row
+// groups per block, whose sums are added in a fixed order at the end, so the
+// partials stay bitwise reproducible.
+template <int CA, int CB, int TAPS, int ABLK>
+struct WgradShape {
+    static constexpr int NG = (CA / ABLK) * CB;                       // threads of one row group
+    static constexpr int PG = NG >= 256 ? 1 : (256 / NG < TH ? 256 / NG : TH);
+    static constexpr int NTH = NG * PG < 32 ? 32 : NG * PG;
+    static constexpr int HB = TAPS == 9 ? 1 : 0;                      // halo of the B tile
+    static constexpr int kTile = CA * TH * TW + CB * ((TH + 2 * HB) * (TW + 2 * HB) + 1);
+    static constexpr int kRed = PG > 1 ? PG * CA * CB * TAPS : 0;
+    static constexpr int kSmem = (kTile > kRed ? kTile : kRed) * 4;
+};
+
 template <int CA, int CB, int TAPS, int ABLK, class AV, class BV>
 __global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, int bstride, int H, int W, int n_img)
 {
-    constexpr int HB = TAPS == 9 ? 1 : 0;   // halo of the B tile
+    using S = WgradShape<CA, CB, TAPS, ABLK>;
+    constexpr int HB = S::HB, PG = S::PG;
     extern __shared__ float4 smem4[];
     float* sA = reinterpret_cast<float*>(smem4);          // [CA][TH][TW]
     float* sB = sA + CA * TH * TW;                          // [CB][TH+2HB][TW+2HB] (+1 pad)
     constexpr int BW = TW + 2 * HB, BH = TH + 2 * HB, BPL = BH * BW + 1;
     const int tid = threadIdx.x;
-    const int ab = tid / CB, b = tid % CB;
+    const int pg = tid / S::NG, r = tid % S::NG, ab = r / CB, b = r % CB;
+    const bool active = pg < PG && ab < CA / ABLK;
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y * n_img;
     float acc[ABLK][TAPS];
@@ -383,8 +399,8 @@ __global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, 
             return (y >= 0 && y < H && x >= 0 && x < W) ? B(i, bb, y, x) : 0.f;
         }, [&](int e, float v) { sB[(e / (BH * BW)) * BPL + e % (BH * BW)] = v; });
         __syncthreads();
-        if (ab < CA / ABLK) {
-            for (int py = 0; py < TH; ++py)
+        if (active) {
+            for (int py = pg; py < TH; py += PG)
                 for (int px = 0; px < TW; ++px) {
                     float av[ABLK];
 #pragma unroll
@@ -399,23 +415,44 @@ __global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, 
                 }
         }
     }
-    if (ab < CA / ABLK) {
-        float* out = part + (int64_t)blockIdx.x * kParams + out_off;
+    float* out = part + (int64_t)blockIdx.x * kParams + out_off;
+    if constexpr (PG == 1) {
+        if (active) {
 #pragma unroll
-        for (int j = 0; j < ABLK; ++j)
+            for (int j = 0; j < ABLK; ++j)
 #pragma unroll
-            for (int t = 0; t < TAPS; ++t) out[((ab * ABLK + j) * bstride + b) * TAPS + t] = acc[j][t];
+                for (int t = 0; t < TAPS; ++t) out[((ab * ABLK + j) * bstride + b) * TAPS + t] = acc[j][t];
+        }
+    } else {
+        // the row groups' sums, added in the order pg = 0, 1, ...
+        float* red = reinterpret_cast<float*>(smem4);   // [PG][CA][CB][TAPS]
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < ABLK; ++j)
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) red[((pg * CA + ab * ABLK + j) * CB + b) * TAPS + t] = acc[j][t];
+        }
+        __syncthreads();
+        if (active && pg == 0) {
+#pragma unroll
+            for (int j = 0; j < ABLK; ++j)
+#pragma unroll
+                for (int t = 0; t < TAPS; ++t) {
+                    float sum = 0.f;
+                    for (int q = 0; q < PG; ++q) sum += red[((q * CA + ab * ABLK + j) * CB + b) * TAPS + t];
+                    out[((ab * ABLK + j) * bstride + b) * TAPS + t] = sum;
+                }
+        }
     }
 }
 
 template <int CA, int CB, int TAPS, int ABLK, class AV, class BV>
 cudaError_t wgrad(AV A, BV B, float* part, int out_off, int bstride, int H, int W, int n_img, cudaStream_t s)
 {
-    constexpr int NTH = (CA / ABLK) * CB;
-    constexpr int HB = TAPS == 9 ? 1 : 0;
-    constexpr int smem = (CA * TH * TW + CB * ((TH + 2 * HB) * (TW + 2 * HB) + 1)) * 4;
-    wgrad_kernel<CA, CB, TAPS, ABLK, AV, BV><<<kWgradBlocks, NTH < 32 ? 32 : NTH, smem, s>>>(A, B, part, out_off, bstride,
-                                                                                        H, W, n_img);
+    using S = WgradShape<CA, CB, TAPS, ABLK>;
+    wgrad_kernel<CA, CB, TAPS, ABLK, AV, BV><<<kWgradBlocks, S::NTH, S::kSmem, s>>>(A, B, part, out_off, bstride, H, W,
+                                                                                  n_img);
     return cudaGetLastError();
 }
 
@@ -443,8 +480,8 @@ cudaError_t net_simt_init()
     SET_SMEM((conv3x3_kernel<kC, 3, View, WtW1T, OutGz>), (conv_smem<kC, 3>()));
     SET_SMEM(branch_fwd_kernel, kBranchSmem);
     SET_SMEM(branch_bwd_kernel, kBranchSmem);
-    SET_SMEM((wgrad_kernel<kC, kC, 9, 4, View, View>), ((kC * TH * TW + kC * ((TH + 2) * (TW + 2) + 1)) * 4));
-    SET_SMEM((wgrad_kernel<kC, kC, 1, 4, View, View>), ((kC * TH * TW + kC * (TH * TW + 1)) * 4));
+    SET_SMEM((wgrad_kernel<kC, kC, 9, 4, View, View>), (WgradShape<kC, kC, 9, 4>::kSmem));
+    SET_SMEM((wgrad_kernel<kC, kC, 1, 4, View, View>), (WgradShape<kC, kC, 1, 4>::kSmem));
 #undef SET_SMEM
     return conv32_tc_init();
 }
