@@ -232,44 +232,63 @@ __global__ void __launch_bounds__(NT) branch_fwd_kernel(const float* __restrict_
         return (y >= 0 && y < H && x >= 0 && x < W) ? phi[i * HW + (int64_t)y * W + x] : 0.f;
     }, [&](int e, float v) { sPhi[e] = v; });
     __syncthreads();
-    const int tx = tid & 31, x = x0 + tx;
-    for (int half = 0; half < 2; ++half) {
-        const int ly = (tid >> 5) + 4 * half, y = y0 + ly;
-        if (x >= W || y >= H) continue;
-        float L[3] = {sB[0], sB[1], sB[2]};
-        for (int i = 0; i < kC; ++i)
+    // each thread's two nodes (rows ly and ly + 4) in one pass, so every
+    // weight read from shared memory serves both (each node's sums keep
+    // their order)
+    const int tx = tid & 31, x = x0 + tx, ly = tid >> 5;
+    const int ya = y0 + ly, yb = ya + 4;
+    if (x >= W || ya >= H) return;   // yb > ya: both out
+    const bool hb = yb < H;
+    const int64_t pa = (int64_t)ya * W + x, pb = hb ? (int64_t)yb * W + x : pa;
+    float La[3] = {sB[0], sB[1], sB[2]}, Lb[3] = {sB[0], sB[1], sB[2]};
+    for (int i = 0; i < kC; ++i)
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
+        for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const float v = sPhi[(i * (TH + 2) + ly + ky) * (TW + 2) + tx + kx];
+            for (int kx = 0; kx < 3; ++kx) {
+                const float va = sPhi[(i * (TH + 2) + ly + ky) * (TW + 2) + tx + kx];
+                const float vb = sPhi[(i * (TH + 2) + ly + 4 + ky) * (TW + 2) + tx + kx];
 #pragma unroll
-                    for (int o = 0; o < 3; ++o) L[o] = fmaf(sWL[(o * kC + i) * 9 + ky * 3 + kx], v, L[o]);
+                for (int o = 0; o < 3; ++o) {
+                    const float wl = sWL[(o * kC + i) * 9 + ky * 3 + kx];
+                    La[o] = fmaf(wl, va, La[o]);
+                    Lb[o] = fmaf(wl, vb, Lb[o]);
                 }
-        float pc[kC];
-#pragma unroll
-        for (int i = 0; i < kC; ++i) pc[i] = sPhi[(i * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
-        float Nn[3] = {0.f, 0.f, 0.f}, Dd[3] = {0.f, 0.f, 0.f};
-        const int64_t p = (int64_t)y * W + x;
-        for (int c = 0; c < kC; ++c) {
-            float t = 0.f;
-            const float4* pr = reinterpret_cast<const float4*>(sP + c * kC);
-#pragma unroll
-            for (int q = 0; q < kC / 4; ++q) {
-                const float4 pw = pr[q];
-                t = fmaf(pw.x, pc[4 * q], fmaf(pw.y, pc[4 * q + 1], fmaf(pw.z, pc[4 * q + 2], fmaf(pw.w, pc[4 * q + 3], t))));
             }
-            const float sv = tanhf(t);
-            const float xs = xi[c * HW + p] * sv;
-            if (s_out) s_out[((int64_t)n * kC + c) * HW + p] = sv;
+    float pca[kC], pcb[kC];
 #pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                Nn[o] = fmaf(sWN[o * kC + c], sv, Nn[o]);
-                Dd[o] = fmaf(sWD[o * kC + c], xs, Dd[o]);
-            }
+    for (int i = 0; i < kC; ++i) {
+        pca[i] = sPhi[(i * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
+        pcb[i] = sPhi[(i * (TH + 2) + ly + 5) * (TW + 2) + tx + 1];
+    }
+    float Na[3] = {0.f, 0.f, 0.f}, Da[3] = {0.f, 0.f, 0.f}, Nb[3] = {0.f, 0.f, 0.f}, Db[3] = {0.f, 0.f, 0.f};
+    for (int c = 0; c < kC; ++c) {
+        float ta = 0.f, tb = 0.f;
+        const float4* pr = reinterpret_cast<const float4*>(sP + c * kC);
+#pragma unroll
+        for (int q = 0; q < kC / 4; ++q) {
+            const float4 pw = pr[q];
+            ta = fmaf(pw.x, pca[4 * q], fmaf(pw.y, pca[4 * q + 1], fmaf(pw.z, pca[4 * q + 2], fmaf(pw.w, pca[4 * q + 3], ta))));
+            tb = fmaf(pw.x, pcb[4 * q], fmaf(pw.y, pcb[4 * q + 1], fmaf(pw.z, pcb[4 * q + 2], fmaf(pw.w, pcb[4 * q + 3], tb))));
+        }
+        const float sa = tanhf(ta), sb = tanhf(tb);
+        const float xsa = xi[c * HW + pa] * sa, xsb = xi[c * HW + pb] * sb;
+        if (s_out) {
+            s_out[((int64_t)n * kC + c) * HW + pa] = sa;
+            if (hb) s_out[((int64_t)n * kC + c) * HW + pb] = sb;
         }
 #pragma unroll
-        for (int o = 0; o < 3; ++o) a[((int64_t)n * 3 + o) * HW + p] = sB[3 + o] * (L[o] + Nn[o] + Dd[o]);
+        for (int o = 0; o < 3; ++o) {
+            Na[o] = fmaf(sWN[o * kC + c], sa, Na[o]);
+            Da[o] = fmaf(sWD[o * kC + c], xsa, Da[o]);
+            Nb[o] = fmaf(sWN[o * kC + c], sb, Nb[o]);
+            Db[o] = fmaf(sWD[o * kC + c], xsb, Db[o]);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        a[((int64_t)n * 3 + o) * HW + pa] = sB[3 + o] * (La[o] + Na[o] + Da[o]);
+        if (hb) a[((int64_t)n * 3 + o) * HW + pb] = sB[3 + o] * (Lb[o] + Nb[o] + Db[o]);
     }
 }
 
@@ -304,46 +323,67 @@ __global__ void __launch_bounds__(NT) branch_bwd_kernel(const float* __restrict_
     float* gxi = gphi + kC * HW;
     float* gt = saved + kSavGT * NHW + (int64_t)n * kC * HW;
     float* gy = saved + kSavGY * NHW + (int64_t)n * 3 * HW;
-    const int tx = tid & 31, x = x0 + tx;
-    for (int half = 0; half < 2; ++half) {
-        const int ly = (tid >> 5) + 4 * half, y = y0 + ly;
-        if (x >= W || y >= H) continue;
-        const int64_t p = (int64_t)y * W + x;
-        float g[3];
+    // each thread's two nodes (rows ly and ly + 4) in one pass, so every
+    // weight read from shared memory serves both (each node's sums keep
+    // their order)
+    const int tx = tid & 31, x = x0 + tx, ly = tid >> 5;
+    const int ya = y0 + ly, yb = ya + 4;
+    if (x >= W || ya >= H) return;   // yb > ya: both out
+    const bool hb = yb < H;
+    const int64_t pa = (int64_t)ya * W + x, pb = hb ? (int64_t)yb * W + x : pa;
+    float g0[3], g1[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        g0[o] = sGy[(o * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
+        g1[o] = sGy[(o * (TH + 2) + ly + 5) * (TW + 2) + tx + 1];
+        gy[o * HW + pa] = g0[o];
+        if (hb) gy[o * HW + pb] = g1[o];
+    }
+    float gtla[kC], gtlb[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+        const float sa = sv[c * HW + pa], xa = xi[c * HW + pa];
+        const float sb = sv[c * HW + pb], xb = xi[c * HW + pb];
+        float gxsa = 0.f, gsa = 0.f, gxsb = 0.f, gsb = 0.f;
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
-            g[o] = sGy[(o * (TH + 2) + ly + 1) * (TW + 2) + tx + 1];
-            gy[o * HW + p] = g[o];
+            gxsa = fmaf(sWD[o * kC + c], g0[o], gxsa);
+            gsa = fmaf(sWN[o * kC + c], g0[o], gsa);
+            gxsb = fmaf(sWD[o * kC + c], g1[o], gxsb);
+            gsb = fmaf(sWN[o * kC + c], g1[o], gsb);
         }
-        float gtl[kC];
+        gsa = fmaf(gxsa, xa, gsa);
+        gsb = fmaf(gxsb, xb, gsb);
+        gtla[c] = gsa * (1.f - sa * sa);
+        gtlb[c] = gsb * (1.f - sb * sb);
+        gxi[c * HW + pa] = gxsa * sa;
+        gt[c * HW + pa] = gtla[c];
+        if (hb) {
+            gxi[c * HW + pb] = gxsb * sb;
+            gt[c * HW + pb] = gtlb[c];
+        }
+    }
+    for (int i = 0; i < kC; ++i) {
+        float acca = 0.f, accb = 0.f;
+#pragma unroll
         for (int c = 0; c < kC; ++c) {
-            const float s = sv[c * HW + p], xv = xi[c * HW + p];
-            float gxs = 0.f, gs = 0.f;
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-                gxs = fmaf(sWD[o * kC + c], g[o], gxs);
-                gs = fmaf(sWN[o * kC + c], g[o], gs);
-            }
-            gs = fmaf(gxs, xv, gs);
-            gxi[c * HW + p] = gxs * s;
-            gtl[c] = gs * (1.f - s * s);
-            gt[c * HW + p] = gtl[c];
+            const float pw = sP[c * kC + i];
+            acca = fmaf(pw, gtla[c], acca);
+            accb = fmaf(pw, gtlb[c], accb);
         }
-        for (int i = 0; i < kC; ++i) {
-            float acc = 0.f;
+        // WL^T (*) d y: d phi_i(p) += sum_o,ky,kx WL[o][i][ky][kx] d y_o(p - (ky-1, kx-1))
 #pragma unroll
-            for (int c = 0; c < kC; ++c) acc = fmaf(sP[c * kC + i], gtl[c], acc);
-            // WL^T (*) d y: d phi_i(p) += sum_o,ky,kx WL[o][i][ky][kx] d y_o(p - (ky-1, kx-1))
+        for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
+            for (int kx = 0; kx < 3; ++kx)
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                    for (int o = 0; o < 3; ++o)
-                        acc = fmaf(sWL[(o * kC + i) * 9 + ky * 3 + kx],
-                                   sGy[(o * (TH + 2) + ly + 2 - ky) * (TW + 2) + tx + 2 - kx], acc);
-            gphi[i * HW + p] = acc;
-        }
+                for (int o = 0; o < 3; ++o) {
+                    const float wl = sWL[(o * kC + i) * 9 + ky * 3 + kx];
+                    acca = fmaf(wl, sGy[(o * (TH + 2) + ly + 2 - ky) * (TW + 2) + tx + 2 - kx], acca);
+                    accb = fmaf(wl, sGy[(o * (TH + 2) + ly + 6 - ky) * (TW + 2) + tx + 2 - kx], accb);
+                }
+        gphi[i * HW + pa] = acca;
+        if (hb) gphi[i * HW + pb] = accb;
     }
 }
 
