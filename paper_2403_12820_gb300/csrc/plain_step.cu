@@ -41,6 +41,17 @@ constexpr unsigned kFull = 0xffffffffu;
 using f2 = float2;
 
 __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start before the kernel ahead of it in the stream has
+// finished; it waits for that kernel (and its memory) before it touches the
+// state, and lets the next one launch at once.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait_then_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
@@ -156,6 +167,7 @@ __global__ void __launch_bounds__(128, CLOTH_PLAIN_MINB) plain_step_kernel(StepA
     const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const bool out_lane = lane >= 1 && lane <= 30;
 
+    pdl_wait_then_release();
     if (gwarp >= a.n_warps) return;
     for (int u = a.warp_first[gwarp]; u < a.warp_first[gwarp + 1]; ++u) {
         const WorkUnit wu = a.units[u];
@@ -501,6 +513,7 @@ __global__ void pin_fix_kernel(const ClothDesc* __restrict__ desc, const int2* _
                                const float* __restrict__ src, float* __restrict__ dst, const int32_t* __restrict__ mode,
                                int32_t* __restrict__ status)
 {
+    pdl_wait_then_release();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int2 p = pins[i];
@@ -529,6 +542,7 @@ __global__ void pin_fix_mask_kernel(const ClothDesc* __restrict__ desc, int B, c
                                     const float* __restrict__ src, float* __restrict__ dst,
                                     const int32_t* __restrict__ mode, int32_t* __restrict__ status)
 {
+    pdl_wait_then_release();
     const int b = blockIdx.y;
     if (b >= B || (mode && mode[b] != kModePlain)) return;
     const ClothDesc& D = desc[b];
@@ -564,23 +578,37 @@ int plain_step_blocks_per_sm_nodamp(int block)
     return n;
 }
 
+// Launch with programmatic stream serialisation: the kernel's launch overlaps
+// the tail of the kernel ahead of it (see pdl_wait_then_release).
+template <class... P, class... A>
+cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t s, A... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_plain_step(const StepArgs& a, bool forces_only, int grid, int block, cudaStream_t s)
 {
     if (forces_only) {
         plain_step_kernel<true><<<grid, block, 0, s>>>(a);
         return cudaGetLastError();
     }
-    plain_step_kernel<false><<<grid, block, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(plain_step_kernel<false>, dim3(grid), dim3(block), s, a);
     if (e != cudaSuccess) return e;
     if (a.n_pins > 0) {
-        pin_fix_kernel<<<(a.n_pins + 127) / 128, 128, 0, s>>>(a.desc, a.pin_list, a.n_pins, a.src, a.dst, a.mode,
-                                                             a.status);
-        e = cudaGetLastError();
+        e = launch_pdl(pin_fix_kernel, dim3((a.n_pins + 127) / 128), dim3(128), s, a.desc, a.pin_list, a.n_pins,
+                       a.src, a.dst, a.mode, a.status);
     } else if (a.n_pins < 0) {   // the pins did not fit the list: from the mask
-        pin_fix_mask_kernel<<<dim3(64, (unsigned)a.n_cloths), 128, 0, s>>>(a.desc, a.n_cloths, a.pinmask, a.src,
-                                                                          a.dst, a.mode, a.status);
-        e = cudaGetLastError();
+        e = launch_pdl(pin_fix_mask_kernel, dim3(64, (unsigned)a.n_cloths), dim3(128), s, a.desc, a.n_cloths,
+                       a.pinmask, a.src, a.dst, a.mode, a.status);
     }
     return e;
 }
