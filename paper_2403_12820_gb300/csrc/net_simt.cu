@@ -440,19 +440,38 @@ __global__ void wgrad_kernel(AV A, BV B, float* __restrict__ part, int out_off, 
         }, [&](int e, float v) { sB[(e / (BH * BW)) * BPL + e % (BH * BW)] = v; });
         __syncthreads();
         if (active) {
-            for (int py = pg; py < TH; py += PG)
+            for (int py = pg; py < TH; py += PG) {
+                // 3 x 3 taps: a window of B's columns px .. px + 2 slides along
+                // the row, one new column (3 loads) per node
+                float win[3][3];
+                if constexpr (TAPS == 9) {
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        win[dy][1] = sB[b * BPL + (py + dy) * BW + 0];
+                        win[dy][2] = sB[b * BPL + (py + dy) * BW + 1];
+                    }
+                }
                 for (int px = 0; px < TW; ++px) {
                     float av[ABLK];
 #pragma unroll
                     for (int j = 0; j < ABLK; ++j) av[j] = sA[((ab * ABLK + j) * TH + py) * TW + px];
+                    if constexpr (TAPS == 9) {
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            win[dy][0] = win[dy][1];
+                            win[dy][1] = win[dy][2];
+                            win[dy][2] = sB[b * BPL + (py + dy) * BW + px + 2];
+                        }
+                    }
 #pragma unroll
                     for (int t = 0; t < TAPS; ++t) {
                         const int dy = TAPS == 9 ? t / 3 : 0, dx = TAPS == 9 ? t % 3 : 0;
-                        const float bv = sB[b * BPL + (py + dy) * BW + px + dx];
+                        const float bv = TAPS == 9 ? win[dy][dx] : sB[b * BPL + py * BW + px];
 #pragma unroll
                         for (int j = 0; j < ABLK; ++j) acc[j][t] = fmaf(av[j], bv, acc[j][t]);
                     }
                 }
+            }
         }
     }
     float* out = part + (int64_t)blockIdx.x * kParams + out_off;
