@@ -100,6 +100,9 @@ constexpr int kPack = kOffKD2 + kKD * 4;
 static_assert(kPack % 16 == 0 && kOffBlo % 16 == 0, "pack");
 
 constexpr int UW = WO + 2;
+// an edge node's slot of the edge table: its 96 columns, padded so that the
+// slots of a warp's 32 edge nodes (a y-edge row) fall on different banks
+constexpr int kCorrW = kNC + 4;
 constexpr int kAnd = (kNDK / 8) * 128 * 16;      // bytes of one N + D operand [8][128][8] bf16
 // mbarriers: accumulator b full (MMAs done) at b, free (16 warps read it and
 // wrote their part of the N + D operand) at 2 + b, the tile's N + D done at
@@ -129,14 +132,14 @@ struct TcShape {
     // one plane per value
     static constexpr int NQ = (R + 2) * (WO + 2);
     static constexpr int kSlots = 2 * (R + 2) + 2 * (WO + 2);   // edge nodes: x = 0, x = W-1, y = 0, y = H-1
-    static constexpr int kCorr = kSlots * kNC;            // floats of one tile's edge table
+    static constexpr int kCorr = kSlots * kCorrW;         // floats of one tile's edge table
     static constexpr int kUFloats = 6 * UH * UW;
     // shared memory map (bytes)
     static constexpr int oBc = 0;                         // B [part][pair][khalf][96][8] bf16
     static constexpr int oIn = oBc + kParts * kBc;        // input [2 tiles][part][N0BUF][8] bf16
     static constexpr int oBnd = oIn + 2 * kParts * N0BUF * 16;   // B of the N + D MMA (BF16 only)
     static constexpr int oAnd = oBnd + (SPLIT ? 0 : kBnd);       // A of the N + D MMA [2 accumulators] (BF16 only)
-    static constexpr int oCorr = oAnd + (SPLIT ? 0 : 2 * kAnd);  // the edge nodes' corrections [kSlots][96] float
+    static constexpr int oCorr = oAnd + (SPLIT ? 0 : 2 * kAnd);  // the edge nodes' corrections [kSlots][kCorrW] float
     static constexpr int oQ = oCorr + kCorr * 4;          // q [27][NQ] float
     // SPLIT: the N + D partial sums of the 4 channel groups [4][3][C2 * 128] float
     static constexpr int oND = oQ + NQ * 27 * 4;
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                         if (yb ? y == g.H - 1 : y == 0)
                             acc = fmaf(kc[yb][0], z[0], fmaf(kc[yb][1], z[1], fmaf(kc[yb][2], z[2], acc)));
                 }
-                corr[(base[ed] + i) * kNC + n] = acc;
+                corr[(base[ed] + i) * kCorrW + n] = acc;
             }
         }
     };
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         tc::tmem_wait_ld();
         if (valid && (x == 0 || y == 0 || x == g.W - 1 || y == g.H - 1)) {
             auto add = [&](int slot) {
-                const float4* c = reinterpret_cast<const float4*>(corr + slot * kNC + 8 * cg);
+                const float4* c = reinterpret_cast<const float4*>(corr + slot * kCorrW + 8 * cg);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const float4 a = c[j], e = c[8 + j], d = c[16 + j];
