@@ -505,6 +505,7 @@ def run_cnn(args, dev):
             left -= k
         return total
 
+    tuned = {}
     for name, prec in (("bf16", BF16), ("f32", FP32)):
         net = Net(blob, prec, device=dev)
         cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
@@ -512,6 +513,7 @@ def run_cnn(args, dev):
         # the step's tile shape from the launch tuner (the state does not move)
         from paper_2403_12820_gb300 import tune
         rec = tune.autotune_net(cn, net, warmup=3, steps=20)
+        tuned[name] = rec["choice"]
         shape = lambda ch: f"{ch['rows']}x{ch['cols']} {ch['kind']}"
         tile = {"shape": shape(rec["shape"]), "candidates_us": {shape(ch): round(t, 2) for ch, t in rec["candidates"]}}
         cn.step_net(net, 3)
@@ -549,6 +551,7 @@ def run_cnn(args, dev):
     w = (cfg["specs"][0]["cols"] - 1) * h
     net = Net(blob, BF16, device=dev)
     cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
+    cn.set_net_tile(BF16, tuned["bf16"])   # the shape the tuner picked for these cloths
     cn.set_net_stride(4)
     cn.set_state(x0, v0)
     cn.step_net(net, 3)
@@ -624,6 +627,9 @@ def run_mixed(args, dev):
     nodes = cb.total_nodes
     blob, trained = network_blob(h)
     net = Net(blob, BF16, device=dev)
+    from paper_2403_12820_gb300 import tune
+    cb.set_state(x0, v0)
+    tile_rec = tune.autotune_net(cb, net, warmup=2, steps=10)   # the network step's tile shape
     stream = torch.cuda.current_stream()
     steps = max(100, args.mixed_steps // 100 * 100)
     side = min(steps, 1000)
@@ -673,7 +679,9 @@ def run_mixed(args, dev):
            "network_unchecked": unchecked, "plain_same_cloths": plain, "ratio_to_plain": checked / plain,
            "side_rollout_steps": side, "status_word": status,
            "coulomb_contact": {"network_unchecked": friction_net, "plain": friction_plain, "friction": 0.3},
-           "gpu_launches_per_10_steps": 10 + 1 + 3 + 1}   # 10 network + 1 plain + residual, merge, latch + memset
+           "gpu_launches_per_10_steps": 10 + 1 + 3 + 1,   # 10 network + 1 plain + residual, merge, latch + memset
+           "tile": {"rows": tile_rec["shape"]["rows"], "cols": tile_rec["shape"]["cols"],
+                    "candidates_us": [round(t, 2) for _, t in tile_rec["candidates"]]}}
     net.close()
     cb.close()
     return out
@@ -775,6 +783,8 @@ def run_larger_step(args, dev, plain_rate: float | None):
     cn = ClothBatch(cfg["specs"], cfg["pins"], device=dev)
     cn.set_net_stride(k)
     cn.set_state(x0, v0)
+    from paper_2403_12820_gb300 import tune
+    net_tile = tune.autotune_net(cn, net, warmup=2, steps=10)["shape"]   # the state does not move
     cn.step_net(net, 3)
     t_net = timed(lambda n: cn.step_net(net, n), 50)
     net_rate = nodes * 50 / t_net
@@ -788,7 +798,8 @@ def run_larger_step(args, dev, plain_rate: float | None):
                         "max_cloth_error_rel_width": float(err.max().item()), "status_word": cb.status()},
            "bf16_network": {"value": net_rate, "unit": "node-steps/s (network steps of 10 dt)",
                             "ms_per_step": t_net / 50 * 1e3, "plain_equivalent_node_steps_per_s": k * net_rate,
-                            "ratio_to_explicit": _ratio(k * net_rate, plain_rate), "status_word": cn.status()},
+                            "ratio_to_explicit": _ratio(k * net_rate, plain_rate), "status_word": cn.status(),
+                            "tile": net_tile},
            "explicit_plain": plain_rate,
            "explicit_plain_moving_pins": {"value": moving_rate, "unit": "node-steps/s",
                                           "pin_velocity_m_s": [0.05, 0.0, 0.0]}}
