@@ -88,6 +88,19 @@ __device__ inline float trunk_composite(const float* __restrict__ w, int n, int 
     return s;
 }
 
+// tanh from the identity tanh(x) = 1 - 2 / (e^(2x) + 1), with the hardware
+// base-2 exponential (e^(2x) = 2^(2x log2 e)) and reciprocal: an absolute
+// error of about 1e-6 (both approximations are within a few units of the
+// last place), against the FP32 step's 1e-4 tolerance on the acceleration.
+// Large |x| saturate cleanly: e^(2x) = inf gives 1, e^(2x) = 0 gives -1.
+__device__ __forceinline__ float tanh_exp(float x)
+{
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.8853900817779268f));   // 2 log2(e)
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
+    return fmaf(-2.f, r, 1.f);
+}
+
 // Tensor-core (tcgen05, BF16) fused cell / network step (net_tc.cu): tiles
 // of net_tc_variant_rows(v) x net_tc_tile_cols() output nodes for one of
 // net_tc_variants() BF16 tile shapes v (0: the default), and the FP32 step

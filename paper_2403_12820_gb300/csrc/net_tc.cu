@@ -188,18 +188,6 @@ __device__ __forceinline__ uint4 pack8(const float* v)
 {
     return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
-// tanh from the identity tanh(x) = 1 - 2 / (e^(2x) + 1), with the hardware
-// base-2 exponential (e^(2x) = 2^(2x log2 e)) and reciprocal: an absolute
-// error of about 1e-6 (both approximations are within a few units of the
-// last place), against the FP32 step's 1e-4 tolerance on the acceleration.
-// Large |x| saturate cleanly: e^(2x) = inf gives 1, e^(2x) = 0 gives -1.
-__device__ __forceinline__ float tanh_exp(float x)
-{
-    float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.8853900817779268f));   // 2 log2(e)
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
-    return fmaf(-2.f, r, 1.f);
-}
 __device__ __forceinline__ float bf_lo(uint32_t x) { return __uint_as_float(x << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t x) { return __uint_as_float(x & 0xffff0000u); }
 
