@@ -148,7 +148,8 @@ struct TcShape {
     static constexpr int oPar = oU + 2 * kUFloats * 4;    // bL[3] outs[3] ins[6] (SPLIT: + WN[3][32], WD[3][32])
     static constexpr int kParFloats = SPLIT ? 16 + 6 * 32 : 16;
     static constexpr int oDesc = oPar + kParFloats * 4;   // the two tiles' cloth descriptors
-    static constexpr int oPin = oDesc + 2 * (int)sizeof(ClothDesc);   // pinned flags of the two tiles' output nodes
+    static constexpr int oTile = oDesc + 2 * (int)sizeof(ClothDesc);  // the two tiles' entries (cloth, y0, x0, -)
+    static constexpr int oPin = oTile + 2 * 16;           // pinned flags of the two tiles' output nodes
     static constexpr int oBar = oPin + (2 * R * WO + 15) / 16 * 16;  // mbarriers; TMEM address
     static constexpr int oTmemSlot = oBar + 8 * kNumBars;
     static constexpr int kSmem = oTmemSlot + 16;
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     constexpr int C2 = S::C2, R = S::R, N0 = S::N0, N2 = S::N2, N0BUF = S::N0BUF, kParts = S::kParts;
     constexpr int UH = S::UH, NQ = S::NQ, kUFloats = S::kUFloats;
     constexpr int oBc = S::oBc, oIn = S::oIn, oBnd = S::oBnd, oAnd = S::oAnd, oCorr = S::oCorr, oQ = S::oQ;
-    constexpr int oND = S::oND, oU = S::oU, oPar = S::oPar, oDesc = S::oDesc, oPin = S::oPin, oBar = S::oBar;
+    constexpr int oND = S::oND, oU = S::oU, oPar = S::oPar, oDesc = S::oDesc, oTile = S::oTile, oPin = S::oPin;
+    constexpr int oBar = S::oBar;
     constexpr int oTmemSlot = S::oTmemSlot;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     float* sNDW = sPar + 16;   // SPLIT: WN [3][32], then WD [3][32]
     float* sND = reinterpret_cast<float*>(sm + oND);   // SPLIT: N + D partial sums [channel group 4][3][C2 * 128]
     ClothDesc* sD = reinterpret_cast<ClothDesc*>(sm + oDesc);
+    int4* sTile = reinterpret_cast<int4*>(sm + oTile);
     uint8_t* sPin = sm + oPin;
     volatile uint32_t* sTmem = reinterpret_cast<uint32_t*>(sm + oTmemSlot);
     auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     tc::fence_after();
     const uint32_t tmem = *sTmem;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-    uint32_t ph[2] = {0, 0};
+    uint32_t ph = 0;      // bit b: the workers' phase of accumulator b's barrier
     uint32_t ph_nd = 0;   // the workers' phase of bar_nd (one completion per tile)
     bool timed_out = false;
     const int n_tiles = STEP ? A.n_tiles : A.N * A.tiles_y * A.tiles_x;
@@ -294,10 +297,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     // "free" barrier (the 16 worker warps read it and wrote their part of the
     // N + D operand) before it issues that chunk's N + D MMA and reuses the
     // accumulator
-    uint32_t pfree[2] = {0, 0};
+    uint32_t pfree = 0;   // bit b: the issuer's phase of accumulator b's free barrier
     auto wait_free = [&](int b) {
-        if (!tc::mbar_wait(bar_free(b), pfree[b], kWaitLimit)) return false;
-        pfree[b] ^= 1u;
+        if (!tc::mbar_wait(bar_free(b), (pfree >> b) & 1u, kWaitLimit)) return false;
+        pfree ^= 1u << b;
         tc::fence_after();
         return true;
     };
@@ -350,6 +353,22 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             g.src = A.z + (int64_t)g.n * 6 * A.H * A.W; g.cs = (int64_t)A.H * A.W; g.rs = A.W;
         }
         return g;
+    };
+    // the same from the copies in shared memory of tile buffer b (step mode:
+    // the tile's entry and its cloth's descriptor, staged with its input),
+    // so the workers start a tile without a dependent global load
+    auto geo_s = [&](int tile, int b) {
+        if constexpr (STEP) {
+            const int4 t = sTile[b];
+            const ClothDesc& d = sD[b];
+            Geo g{};
+            g.cloth = t.x; g.y0 = t.y; g.x0 = t.z; g.H = d.rows; g.W = d.cols;
+            g.src = A.src + d.plane_off; g.cs = d.plane_stride; g.rs = d.pitch;
+            g.pin = A.pinmask + d.pin_off; g.pin_wpr = d.pin_wpr;
+            return g;
+        } else {
+            return geo(tile);
+        }
     };
     // this CTA's tiles: every gridDim.x-th, skipping cloths not in network mode
     auto skip = [&](int t) {
@@ -412,8 +431,11 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         if (STEP && oy >= 0 && oy < R && ox >= 0 && ox < WO)
             sPin[buf * R * WO + oy * WO + ox] = (uint8_t)((rw.pin >> ((g.x0 + ox) & 31)) & 1u);
     };
-    auto stage = [&](const Geo& g, int buf) {   // the whole region at once
-        if (STEP && tid == 0) sD[buf] = A.desc[g.cloth];
+    auto stage = [&](const Geo& g, int tile, int buf) {   // the whole region at once
+        if (STEP && tid == 0) {
+            sD[buf] = A.desc[g.cloth];
+            sTile[buf] = A.tiles[tile];
+        }
         for (int j0 = tid; j0 < N0; j0 += NWORK) {
             Raw rw;
             stage_load(g, j0, rw);
@@ -435,8 +457,11 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         const int n = t % kNC, gi = t / kNC;
         if (n >= 59 && n < 64) return;   // padding columns: never read
         const int rxE = g.W - g.x0, ryN = g.H - g.y0;   // cell column of x = W-1, cell row of y = H-1
-        const bool has[4] = {g.x0 == 0, rxE >= 0 && rxE < WO + 2, g.y0 == 0, ryN >= 0 && ryN < R + 2};
-        constexpr int base[4] = {0, R + 2, 2 * (R + 2), 2 * (R + 2) + WO + 2};
+        // the edges present (bit ed), as a mask: no array indexed by the
+        // edge loop's counter, which would live in local memory
+        const uint32_t has = (uint32_t)(g.x0 == 0) | (uint32_t)(rxE >= 0 && rxE < WO + 2) << 1 |
+                             (uint32_t)(g.y0 == 0) << 2 | (uint32_t)(ryN >= 0 && ryN < R + 2) << 3;
+        if (has == 0) return;   // an interior tile: no edge terms
         // the three input slots of column n: u (n < 64) or v
         auto z3 = [&](int row, float (&z)[3]) {
             const uint4 r = in[row];
@@ -452,7 +477,8 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                                  : reinterpret_cast<const float*>(reinterpret_cast<const uint8_t*>(A.wpack) + kBc) + kKE + kKC;
 #pragma unroll 1
         for (int ed = 0; ed < 4; ++ed) {
-            if (!has[ed]) continue;
+            if (!((has >> ed) & 1u)) continue;
+            const int base = ed < 2 ? ed * (R + 2) : 2 * (R + 2) + (ed - 2) * (WO + 2);   // the edge's first slot
             // the rounding defect of a tap is added by the first edge (in the
             // order x = 0, x = W-1, y = 0, y = H-1) whose column or row holds
             // it: x = W-1 leaves its column to x = 0 on a one-column cloth,
@@ -498,7 +524,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                         if (yb ? y == g.H - 1 : y == 0)
                             acc = fmaf(kc[yb][0], z[0], fmaf(kc[yb][1], z[1], fmaf(kc[yb][2], z[2], acc)));
                 }
-                corr[(base[ed] + i) * kCorrW + n] = acc;
+                corr[(base + i) * kCorrW + n] = acc;
             }
         }
     };
@@ -678,7 +704,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         const Geo g = geo(tile);
         tn = skip(tile + (int)gridDim.x);
         if (worker) {
-            stage(g, 0);
+            stage(g, tile, 0);
             tc::fence_async_smem();
         }
         __syncthreads();
@@ -692,14 +718,14 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     while (tile < n_tiles && !timed_out) {
         const bool has_next = tn < n_tiles;
         const int tnn = has_next ? skip(tn + (int)gridDim.x) : n_tiles;
-        // the geometry each role needs: the workers this tile's and (for its
-        // edge terms) the next one's, the helpers the next one's
+        // the geometry each role needs: the workers this tile's (from shared
+        // memory) and, after the chunks, the next one's for its edge terms;
+        // the helpers the next one's from global memory
         Geo g{}, gn{};
         if (helper) {
             if (has_next) gn = geo(tn);
         } else if (worker) {
-            g = geo(tile);
-            if (has_next) gn = geo(tn);
+            g = geo_s(tile, buf);
         }
         bool ok = true;
         if (helper) {
@@ -707,9 +733,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             // tile's chunks run, all of a helper's input nodes in flight at once
             if (has_next) {
                 constexpr int kDescV = (int)(sizeof(ClothDesc) / sizeof(uint4));
-                static_assert(sizeof(ClothDesc) % sizeof(uint4) == 0 && kDescV <= NHELP, "descriptor copy");
+                static_assert(sizeof(ClothDesc) % sizeof(uint4) == 0 && kDescV < NHELP, "descriptor copy");
                 if (STEP && htid < kDescV)
                     reinterpret_cast<uint4*>(sD + (buf ^ 1))[htid] = reinterpret_cast<const uint4*>(A.desc + gn.cloth)[htid];
+                if (STEP && htid == kDescV) sTile[buf ^ 1] = A.tiles[tn];
                 constexpr int kBatch = kHelpParts;   // input nodes in flight per helper
 #pragma unroll 1
                 for (int k0 = 0; k0 < kHelpParts; k0 += kBatch) {
@@ -731,15 +758,19 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             // barrier; the issuer waits there, issues the chunk's N + D MMA and
             // then reuses the accumulator; after the last chunk's N + D it
             // commits to bar_nd, which the final pass waits for.
+            // BF16: unrolled, so the accumulator index and its barrier phases
+            // are compile-time (no local-memory array); the FP32 form, with
+            // more live registers, is faster rolled
+#pragma unroll(SPLIT ? 1 : C2)
             for (int c2 = 0; c2 < C2; ++c2) {
                 const int b = c2 & 1;
                 if (worker) {
-                    if (ok) ok = tc::mbar_wait(bar(b), ph[b], kWaitLimit);
+                    if (ok) ok = tc::mbar_wait(bar(b), (ph >> b) & 1u, kWaitLimit);
                     if (ok) epilogue(g, c2, b, sCorr(buf));
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bar_free(b));   // also after a timeout: the issuer's wait ends
                 }
-                ph[b] ^= 1u;
+                ph ^= 1u << b;
                 if (issuer && ok) {
                     ok = wait_free(b);
                     if (ok) {
@@ -759,7 +790,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
         if (worker) {
             if (!final_pass(g, buf)) ok = false;
-            if (has_next) edge_prep(gn, sIn(buf ^ 1), sCorr(buf ^ 1), tid, NWORK);   // this tile's epilogues are done
+            if (has_next) {   // this tile's epilogues are done; the helpers staged the next tile
+                gn = geo_s(tn, buf ^ 1);
+                edge_prep(gn, sIn(buf ^ 1), sCorr(buf ^ 1), tid, NWORK);
+            }
         }
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tile = tn;
