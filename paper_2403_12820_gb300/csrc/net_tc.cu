@@ -393,17 +393,22 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     auto stage_load = [&](const Geo& g, int j0, Raw& rw) {
         const int iy = j0 / PT, ix = j0 % PT;
         const int y = g.y0 - 3 + iy, x = g.x0 - 3 + ix;
+        const bool in = y >= 0 && y < g.H && x >= 0 && x < g.W;
+        // every load is issued, from an address inside the cloth (a node
+        // outside reads its nearest cloth node and counts as zero), so that
+        // all of a helper's loads are in flight together
+        const int yc = min(max(y, 0), g.H - 1), xc = min(max(x, 0), g.W - 1);
+        const float* p0 = g.src + (int64_t)yc * g.rs + (STEP ? col_pos(xc) : xc);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) rw.v[c] = 0.f;
+        for (int c = 0; c < 6; ++c) {
+            const float r = __ldg(p0 + c * g.cs);
+            rw.v[c] = in ? r : 0.f;
+        }
         rw.pin = 0;
-        if (y >= 0 && y < g.H && x >= 0 && x < g.W) {
-            const float* p0 = g.src + (int64_t)y * g.rs + (STEP ? col_pos(x) : x);
-#pragma unroll
-            for (int c = 0; c < 6; ++c) rw.v[c] = __ldg(p0 + c * g.cs);
-            if constexpr (STEP) {
-                const int oy = iy - 3, ox = ix - 3;
-                if (oy >= 0 && oy < R && ox >= 0 && ox < WO) rw.pin = __ldg(g.pin + (int64_t)y * g.pin_wpr + (x >> 5));
-            }
+        if constexpr (STEP) {
+            const int oy = iy - 3, ox = ix - 3;
+            const uint32_t pw = __ldg(g.pin + (int64_t)yc * g.pin_wpr + (xc >> 5));
+            if (in && oy >= 0 && oy < R && ox >= 0 && ox < WO) rw.pin = pw;
         }
     };
     auto stage_store = [&](const Geo& g, int buf, int j0, const Raw& rw) {
