@@ -27,8 +27,8 @@
 //      in_scale v, 0, 0 per node; zero outside the cloth) into one of two
 //      input buffers, and the raw FP32 u, v of the output nodes and their
 //      1-node halo into one of two FP32 tile buffers;
-//   2. per chunk of the (R+2)-row cell region (R = 14, WO = 26: exactly
-//      four chunks), 13 MMAs of K = 16, each pairing two of the 25 taps (the
+//   2. per chunk of the (R+2)-row cell region (R = 14, 10 or 6 with WO =
+//      26: exactly four, three or two chunks), 13 MMAs of K = 16, each pairing two of the 25 taps (the
 //      second core-matrix column of K sits LBO = the taps' row distance
 //      further), into one of two tensor-memory accumulators (chunk c+1 runs
 //      during the epilogue of chunk c);
@@ -44,8 +44,9 @@
 //      D); then (step mode) v <- C(v + dt (a + f_p / m)), u <- u + dt v,
 //      sphere contact, store.
 // Tiles are pipelined: the helper warps stage the input of tile t+1 (step
-// 1) while the chunks of tile t run, and the first two chunks of tile t+1
-// run during the final pass of tile t.  Between the chunks there is no CTA
+// 1, with its tile entry and cloth descriptor, from which the workers take
+// its geometry without a global load) while the chunks of tile t run, and
+// the first two chunks of tile t+1 run during the final pass of tile t.  Between the chunks there is no CTA
 // barrier: each worker warp arrives on an accumulator's "free" mbarrier once
 // it has read it, and the issuing thread waits there before it reuses the
 // accumulator; a tile has two CTA barriers (before and after its final
