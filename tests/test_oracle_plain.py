@@ -42,7 +42,7 @@ def test_spring_counts_closed_form(rows, cols):
 
 
 def test_spring_count_paper_100x100():
-    """Sec. 4.1 prints "around 60k springs" for 100 x 100 mass points."""
+    """Sec. 4.1 gives roughly 60 thousand springs for a 100 x 100 grid of mass points."""
     with open(os.path.join(GOLD, "spring_count_100x100.json")) as fh:
         gold = json.load(fh)
     total = sum(oracle.spring_counts(100, 100))
