@@ -107,8 +107,9 @@ constexpr int kCorrW = kNC + 4;
 constexpr int kAnd = (kNDK / 8) * 128 * 16;      // bytes of one N + D operand [8][128][8] bf16
 // mbarriers: accumulator b full (MMAs done) at b, free (16 warps read it and
 // wrote their part of the N + D operand) at 2 + b, the tile's N + D done at
-// 4, the tear-down drain at 5
-constexpr int kNumBars = 6;
+// 4, the tear-down drain at 5; in the FP32 form, accumulator b read (16 warps
+// loaded it into registers) at 6 + b
+constexpr int kNumBars = 8;
 // TMEM columns: accumulator b at [96 b, +96), N + D of chunk c at
 // [192 + 16 c, +16)
 constexpr uint32_t kTmemCols = 256;
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     auto bar = [&](int b) { return sbase + oBar + 8u * (uint32_t)b; };
     auto bar_free = [&](int b) { return sbase + oBar + 8u * (uint32_t)(2 + b); };
     const uint32_t bar_nd = sbase + oBar + 8u * 4u, bar_drain = sbase + oBar + 8u * 5u;
+    auto bar_read = [&](int b) { return sbase + oBar + 8u * (uint32_t)(6 + b); };
     // input buffer of tile buffer `buf` (SPLIT: its high part; the low part follows at + N0BUF)
     auto sIn = [&](int buf, int part = 0) { return reinterpret_cast<uint4*>(sm + oIn) + (buf * kParts + part) * N0BUF; };
 
@@ -269,6 +271,7 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         }
         tc::mbar_init(bar_nd, 1);
         tc::mbar_init(bar_drain, 1);
+        for (int b = 0; b < 2; ++b) tc::mbar_init(bar_read(b), NWORK / 32);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
@@ -302,6 +305,13 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
     auto wait_free = [&](int b) {
         if (!tc::mbar_wait(bar_free(b), (pfree >> b) & 1u, kWaitLimit)) return false;
         pfree ^= 1u << b;
+        tc::fence_after();
+        return true;
+    };
+    uint32_t pread = 0;   // bit b: the issuer's phase of accumulator b's read barrier (FP32 form)
+    auto wait_read = [&](int b) {
+        if (!tc::mbar_wait(bar_read(b), (pread >> b) & 1u, kWaitLimit)) return false;
+        pread ^= 1u << b;
         tc::fence_after();
         return true;
     };
@@ -553,6 +563,11 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
         tmem_ld8(col + 64, xi);
         tmem_ld8(col + 32, q);   // q_{8 cg} .. q_{8 cg + 7} (group 3: q_24..26 and padding)
         tc::tmem_wait_ld();
+        if constexpr (SPLIT) {   // the accumulator is in registers: the issuer may refill it now
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(bar_read(b));
+        }
         if (valid && (x == 0 || y == 0 || x == g.W - 1 || y == g.H - 1)) {
             auto add = [&](int slot) {
                 const float4* c = reinterpret_cast<const float4*>(corr + slot * kCorrW + 8 * cg);
@@ -772,17 +787,30 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
                 const int b = c2 & 1;
                 if (worker) {
                     if (ok) ok = tc::mbar_wait(bar(b), (ph >> b) & 1u, kWaitLimit);
-                    if (ok) epilogue(g, c2, b, sCorr(buf));
+                    if (ok) {
+                        epilogue(g, c2, b, sCorr(buf));   // FP32 form: arrives on bar_read(b) after its loads
+                    } else if (SPLIT) {
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(bar_read(b));   // after a timeout: the issuer's wait ends
+                    }
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bar_free(b));   // also after a timeout: the issuer's wait ends
                 }
                 ph ^= 1u << b;
                 if (issuer && ok) {
-                    ok = wait_free(b);
-                    if (ok) {
-                        if constexpr (!SPLIT) issue_nd(c2);
-                        if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
-                        if (!SPLIT && c2 == C2 - 1) tc::mma_commit(bar_nd);
+                    if constexpr (SPLIT) {
+                        // no N + D MMA: the accumulator is refilled as soon as
+                        // it is read, while the epilogue still runs (the free
+                        // barrier has no waiter in this form)
+                        ok = wait_read(b);
+                        if (ok && c2 + 2 < C2) issue_chunk(c2 + 2, buf);
+                    } else {
+                        ok = wait_free(b);
+                        if (ok) {
+                            issue_nd(c2);
+                            if (c2 + 2 < C2) issue_chunk(c2 + 2, buf);
+                            if (c2 == C2 - 1) tc::mma_commit(bar_nd);
+                        }
                     }
                 }
             }
