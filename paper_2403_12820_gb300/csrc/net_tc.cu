@@ -27,10 +27,10 @@
 //      in_scale v, 0, 0 per node; zero outside the cloth) into one of two
 //      input buffers, and the raw FP32 u, v of the output nodes and their
 //      1-node halo into one of two FP32 tile buffers;
-//   2. per chunk of the (R+2)-row cell region (R = 14, 10 or 6 with WO =
-//      26: exactly four, three or two chunks), 13 MMAs of K = 16, each pairing two of the 25 taps (the
-//      second core-matrix column of K sits LBO = the taps' row distance
-//      further), into one of two tensor-memory accumulators (chunk c+1 runs
+//   2. per chunk of the (R+2)-row cell region (R = 14, 10 or 6 with
+//      WO = 26: exactly four, three or two chunks), 13 MMAs of K = 16, each
+//      pairing two of the 25 taps (the second core-matrix column of K sits
+//      LBO = the taps' row distance further), into one of two tensor-memory accumulators (chunk c+1 runs
 //      during the epilogue of chunk c);
 //   3. epilogue per cell-region node: the edge corrections (computed per
 //      tile from the staged input, before its first epilogue), s = tanh(t)
@@ -46,13 +46,13 @@
 // Tiles are pipelined: the helper warps stage the input of tile t+1 (step
 // 1, with its tile entry and cloth descriptor, from which the workers take
 // its geometry without a global load) while the chunks of tile t run, and
-// the first two chunks of tile t+1 run during the final pass of tile t.  Between the chunks there is no CTA
-// barrier: each worker warp arrives on an accumulator's "free" mbarrier once
-// it has read it, and the issuing thread waits there before it reuses the
-// accumulator; a tile has two CTA barriers (before and after its final
-// pass).  Every wait on
-// the tensor cores is bounded; a timeout sets a status bit and the kernel
-// returns after releasing its tensor memory.
+// the first two chunks of tile t+1 run during the final pass of tile t.
+// Between the chunks there is no CTA barrier: each worker warp arrives on
+// an accumulator's "free" mbarrier once it has read it, and the issuing
+// thread waits there before it reuses the accumulator; a tile has two CTA
+// barriers (before and after its final pass).  Every wait on the tensor
+// cores is bounded; a timeout sets a status bit and the kernel returns after
+// releasing its tensor memory.
 #include <cuda_bf16.h>
 
 #include "net_internal.cuh"
@@ -778,7 +778,10 @@ __global__ void __launch_bounds__(NTH, 1) net_tc_kernel(TcArgs A)
             // its part of the N + D operand) on that accumulator's "free"
             // barrier; the issuer waits there, issues the chunk's N + D MMA and
             // then reuses the accumulator; after the last chunk's N + D it
-            // commits to bar_nd, which the final pass waits for.
+            // commits to bar_nd, which the final pass waits for.  The FP32
+            // form has no N + D MMA: the workers also arrive on the
+            // accumulator's "read" barrier right after loading it, and the
+            // issuer refills it from there.
             // BF16: unrolled, so the accumulator index and its barrier phases
             // are compile-time (no local-memory array); the FP32 form, with
             // more live registers, is faster rolled
